@@ -1,0 +1,248 @@
+"""FP64 CPU oracle for the B0 -> J/psi K pi four-dimensional amplitude fit.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's timed
+CPU baseline use it; the product path never imports it.  The arithmetic lives
+in ``amp4d_oracle.c`` (plain C, double precision, OpenMP over events); this
+module compiles it with gcc on first use and wraps it with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "amp4d_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = C.POINTER(C.c_double)
+_f = C.POINTER(C.c_float)
+_i = C.POINTER(C.c_int)
+_u32 = C.POINTER(C.c_uint32)
+
+
+def build(force=False):
+    """Compile the oracle shared library with gcc (no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            L.or_model_new.restype = C.c_void_p
+            L.or_model_new.argtypes = [_d, C.c_double, C.c_double, C.c_int, _i, _i, _i, _i, _i,
+                                       _d, _d, _d, _i]
+            L.or_model_free.argtypes = [C.c_void_p]
+            L.or_num_cols.argtypes = [C.c_void_p]
+            L.or_num_params.argtypes = [C.c_void_p]
+            L.or_columns.argtypes = [C.c_void_p, _i, _i]
+            L.or_wigner_d.restype = C.c_double
+            L.or_wigner_d.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double]
+            L.or_bw_poly.restype = C.c_double
+            L.or_bw_poly.argtypes = [C.c_int, C.c_double]
+            L.or_breakup.restype = C.c_double
+            L.or_breakup.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.or_lineshape.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, _d]
+            L.or_kinematics.argtypes = [C.c_void_p, _d, _d, _d, _d, C.c_int64, _d]
+            L.or_basis.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d]
+            L.or_density.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d]
+            L.or_norm.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, _d, C.c_int64, C.c_double,
+                                  _d, _d]
+            L.or_nll.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d, _d,
+                                 C.c_int64, C.c_double, _d, _d, _d]
+            L.or_gram.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, _d, C.c_int64, _d]
+            L.or_generate.restype = C.c_int64
+            L.or_generate.argtypes = [C.c_void_p, _d, C.c_uint64, C.c_int64, C.c_int64,
+                                      C.c_int64, _f, _f, _f, _f, _d]
+            L.or_philox4x32_10.argtypes = [_u32, _u32, _u32]
+            L.or_num_threads.restype = C.c_int
+            L.or_set_num_threads.argtypes = [C.c_int]
+            _lib = L
+    return _lib
+
+
+def _pd(a):
+    return a.ctypes.data_as(_d)
+
+
+def _pf(a):
+    return a.ctypes.data_as(_f)
+
+
+def _pi(a):
+    return a.ctypes.data_as(_i)
+
+
+def _f64(a):
+    """Coordinates enter the oracle in double; FP32 event arrays promote exactly."""
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    lib().or_set_num_threads(int(n))
+
+
+def wigner_d(j, mp, m, cosb):
+    """Wigner small-d d^j_{mp m}(beta) at cos(beta), by the general factorial sum."""
+    return lib().or_wigner_d(int(j), int(mp), int(m), float(cosb))
+
+
+def bw_poly(L, z):
+    """Blatt-Weisskopf barrier polynomial P_L(z)."""
+    return lib().or_bw_poly(int(L), float(z))
+
+
+def breakup(Mp, m1, m2):
+    """Two-body momentum of a parent of mass Mp decaying to m1, m2 (0 if closed)."""
+    return lib().or_breakup(float(Mp), float(m1), float(m2))
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(c.ctypes.data_as(_u32), k.ctypes.data_as(_u32), o.ctypes.data_as(_u32))
+    return o
+
+
+class Model:
+    """Oracle model built from a list of ``workloads.Resonance`` records."""
+
+    def __init__(self, res_list, float_names=(), masses=None, box=None):
+        import workloads as W
+        masses = W.PARTICLE_MASSES if masses is None else masses
+        box = (W.M_LO, W.M_HI) if box is None else box
+        self.res_list = list(res_list)
+        self.masses = tuple(masses)
+        self.box = tuple(box)
+        n = len(self.res_list)
+        ia = lambda xs: np.ascontiguousarray(xs, dtype=np.int32)
+        self._arrs = dict(
+            masses=_f64(masses),
+            chain=ia([r.chain for r in res_list]), J=ia([r.J for r in res_list]),
+            P=ia([r.P for r in res_list]), LB=ia([r.LB for r in res_list]),
+            LR=ia([r.LR for r in res_list]), M=_f64([r.M for r in res_list]),
+            G0=_f64([r.G0 for r in res_list]), r=_f64([r.r for r in res_list]),
+            flt=ia([1 if r.name in float_names else 0 for r in res_list]))
+        a = self._arrs
+        self.h = lib().or_model_new(_pd(a["masses"]), box[0], box[1], n, _pi(a["chain"]),
+                                    _pi(a["J"]), _pi(a["P"]), _pi(a["LB"]), _pi(a["LR"]),
+                                    _pd(a["M"]), _pd(a["G0"]), _pd(a["r"]), _pi(a["flt"]))
+        if not self.h:
+            raise ValueError("oracle: bad model")
+        self.n_cols = lib().or_num_cols(self.h)
+        self.n_params = lib().or_num_params(self.h)
+        res = np.zeros(self.n_cols, np.int32)
+        lam = np.zeros(self.n_cols, np.int32)
+        lib().or_columns(self.h, _pi(res), _pi(lam))
+        self.col_res, self.col_lam = res, lam
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().or_model_free(self.h)
+        except Exception:
+            pass
+
+    def lineshape(self, R, mrun, M=None, G0=None):
+        """(A, dA/dM, dA/dG0) of resonance R at running mass mrun."""
+        r = self.res_list[R]
+        o = np.zeros(6)
+        lib().or_lineshape(self.h, int(R), float(mrun), float(r.M if M is None else M),
+                           float(r.G0 if G0 is None else G0), _pd(o))
+        return complex(o[0], o[1]), complex(o[2], o[3]), complex(o[4], o[5])
+
+    def kinematics(self, pts):
+        m, cK, cpsi, phi = (_f64(a) for a in pts)
+        out = np.zeros((len(m), 24))
+        lib().or_kinematics(self.h, _pd(m), _pd(cK), _pd(cpsi), _pd(phi), len(m), _pd(out))
+        return out
+
+    def basis(self, params, pts):
+        """B[e, k, xi] complex (xi index 0 = +1, 1 = -1) and p q per point."""
+        m, cK, cpsi, phi = (_f64(a) for a in pts)
+        n = len(m)
+        out = np.zeros((n, self.n_cols, 2, 2))
+        pq = np.zeros(n)
+        pr = _f64(params)
+        lib().or_basis(self.h, _pd(pr), _pd(m), _pd(cK), _pd(cpsi), _pd(phi), n, _pd(out), _pd(pq))
+        return out[..., 0] + 1j * out[..., 1], pq
+
+    def density(self, params, pts):
+        """(S, p q) per point."""
+        m, cK, cpsi, phi = (_f64(a) for a in pts)
+        n = len(m)
+        S = np.zeros(n)
+        pq = np.zeros(n)
+        pr = _f64(params)
+        lib().or_density(self.h, _pd(pr), _pd(m), _pd(cK), _pd(cpsi), _pd(phi), n, _pd(S), _pd(pq))
+        return S, pq
+
+    def norm(self, params, pts, w=None, volume=None, grad=False):
+        import workloads as W
+        volume = W.BOX_VOLUME if volume is None else volume
+        m, cK, cpsi, phi = (_f64(a) for a in pts)
+        wf = _f64(w) if w is not None else None
+        I = C.c_double()
+        g = np.zeros(self.n_params) if grad else None
+        pr = _f64(params)
+        lib().or_norm(self.h, _pd(pr), _pd(m), _pd(cK), _pd(cpsi), _pd(phi),
+                      _pd(wf) if wf is not None else None, len(m), float(volume), C.byref(I),
+                      _pd(g) if grad else None)
+        return (I.value, g) if grad else I.value
+
+    def nll(self, params, events, norm_pts, w=None, volume=None, grad=False):
+        """(-2 ln L, gradient or None, aux = [sum ln S, sum ln pq, I], status)."""
+        import workloads as W
+        volume = W.BOX_VOLUME if volume is None else volume
+        ev = [_f64(a) for a in events]
+        nm = [_f64(a) for a in norm_pts]
+        wf = _f64(w) if w is not None else None
+        out = C.c_double()
+        g = np.zeros(self.n_params) if grad else None
+        aux = np.zeros(3)
+        pr = _f64(params)
+        rc = lib().or_nll(self.h, _pd(pr), *(_pd(a) for a in ev), len(ev[0]),
+                          *(_pd(a) for a in nm), _pd(wf) if wf is not None else None,
+                          len(nm[0]), float(volume), C.byref(out), _pd(g) if grad else None,
+                          _pd(aux))
+        return out.value, g, aux, rc
+
+    def gram(self, params, pts, w=None):
+        m, cK, cpsi, phi = (_f64(a) for a in pts)
+        D = 2 * self.n_cols
+        G = np.zeros((D, D))
+        wf = _f64(w) if w is not None else None
+        pr = _f64(params)
+        lib().or_gram(self.h, _pd(pr), _pd(m), _pd(cK), _pd(cpsi), _pd(phi),
+                      _pd(wf) if wf is not None else None, len(m), _pd(G))
+        return G
+
+    def generate(self, params, n, seed, n_scan=200_000, max_cand=None):
+        """Accept-reject pseudo-data distributed as S p q (FP32 SoA)."""
+        max_cand = max_cand or 4000 * n + (1 << 20)
+        outs = [np.zeros(n, np.float32) for _ in range(4)]
+        fmax = C.c_double()
+        pr = _f64(params)
+        used = lib().or_generate(self.h, _pd(pr), int(seed), int(n), int(n_scan), int(max_cand),
+                                 *(_pf(a) for a in outs), C.byref(fmax))
+        if used < 0:
+            raise RuntimeError("oracle generator: candidate budget exhausted")
+        return tuple(outs), used, fmax.value

@@ -1,0 +1,451 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, textbook closed forms, library special functions,
+conservation laws, exact angular integrals, brute-force quadrature, symmetry
+invariances of the likelihood and finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import legendre as npleg
+from scipy import integrate, special
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+# ---------------------------------------------------------------- Wigner d (Eq. 4, Eq. 10)
+def _legendre(J, x):
+    return npleg.legval(x, [0] * J + [1])
+
+
+def _legendre_deriv(J, x):
+    return npleg.legval(x, npleg.legder([0] * J + [1]))
+
+
+ANGLES = np.linspace(-0.999, 0.999, 37)
+
+
+@pytest.mark.parametrize("J", [0, 1, 2, 3, 4])
+def test_wigner_d_l0_is_legendre(J):
+    """d^J_{00} = P_J(cos), d^J_{+-1,0} = -+ sin P_J'(cos) / sqrt(J(J+1))."""
+    for c in ANGLES:
+        s = math.sqrt(1 - c * c)
+        assert O.wigner_d(J, 0, 0, c) == pytest.approx(_legendre(J, c), abs=1e-13)
+        if J >= 1:
+            ref = -s * _legendre_deriv(J, c) / math.sqrt(J * (J + 1))
+            assert O.wigner_d(J, 1, 0, c) == pytest.approx(ref, abs=1e-13)
+            assert O.wigner_d(J, -1, 0, c) == pytest.approx(-ref, abs=1e-13)
+            # d^J_{0 l} = (-1)^l d^J_{l 0}
+            assert O.wigner_d(J, 0, 1, c) == pytest.approx(-ref, abs=1e-13)
+            assert O.wigner_d(J, 0, -1, c) == pytest.approx(ref, abs=1e-13)
+
+
+def test_wigner_d1_closed_forms():
+    for c in ANGLES:
+        s = math.sqrt(1 - c * c)
+        ref = {(1, 1): (1 + c) / 2, (1, -1): (1 - c) / 2, (-1, 1): (1 - c) / 2,
+               (-1, -1): (1 + c) / 2, (0, 1): s / math.sqrt(2), (0, -1): -s / math.sqrt(2),
+               (1, 0): -s / math.sqrt(2), (-1, 0): s / math.sqrt(2), (0, 0): c}
+        for (mp, m), v in ref.items():
+            assert O.wigner_d(1, mp, m, c) == pytest.approx(v, abs=1e-14)
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 4])
+def test_wigner_d_unitarity(j):
+    rng = np.random.default_rng(j)
+    for c in rng.uniform(-1, 1, 7):
+        d = np.array([[O.wigner_d(j, mp, m, c) for m in range(-j, j + 1)]
+                      for mp in range(-j, j + 1)])
+        assert np.allclose(d.T @ d, np.eye(2 * j + 1), atol=1e-13)
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 4])
+def test_wigner_d_special_angles(j):
+    for mp in range(-j, j + 1):
+        for m in range(-j, j + 1):
+            assert O.wigner_d(j, mp, m, 1.0) == pytest.approx(1.0 if mp == m else 0.0, abs=1e-14)
+            ref = (-1) ** (j - m) if mp == -m else 0.0
+            assert O.wigner_d(j, mp, m, -1.0) == pytest.approx(ref, abs=1e-14)
+
+
+def test_wigner_d_orthogonality():
+    x, w = npleg.leggauss(12)
+    for lam in (0, 1):
+        for J in range(lam, 5):
+            for Jp in range(lam, 5):
+                v = sum(wi * O.wigner_d(J, lam, 0, xi) * O.wigner_d(Jp, lam, 0, xi)
+                        for xi, wi in zip(x, w))
+                assert v == pytest.approx(2 / (2 * J + 1) if J == Jp else 0.0, abs=1e-13)
+
+
+# ---------------------------------------------------------------- barrier factors, momenta
+@pytest.mark.parametrize("L", [0, 1, 2, 3, 4])
+def test_bw_poly_is_spherical_hankel(L):
+    """P_L(x^2) = x^(2L+2) (j_L(x)^2 + y_L(x)^2)."""
+    for x in (0.05, 0.3, 0.9, 1.7, 3.2):
+        ref = x ** (2 * L + 2) * (special.spherical_jn(L, x) ** 2 + special.spherical_yn(L, x) ** 2)
+        assert O.bw_poly(L, x * x) == pytest.approx(ref, rel=1e-12)
+
+
+def test_breakup_energy_conservation():
+    for Mp, m1, m2 in [(0.8955, W.M_K, W.M_PI), (2.1, W.M_K, W.M_PI), (W.M_B, 1.4, W.M_PSI),
+                       (4.43, W.M_PSI, W.M_PI), (W.M_B, 4.43, W.M_K)]:
+        q = O.breakup(Mp, m1, m2)
+        assert math.hypot(m1, q) + math.hypot(m2, q) == pytest.approx(Mp, rel=1e-14)
+    assert O.breakup(0.6, W.M_K, W.M_PI) == 0.0  # closed channel
+
+
+# ---------------------------------------------------------------- lineshape (Eq. 2, Eq. 3)
+def _all_model():
+    return O.Model(W.KSTAR_TABLE + [W.Z4430])
+
+
+def test_lineshape_at_pole():
+    """At m = M: p = p0, q = q0, F = 1, Gamma(M) = G0, so
+    A(M) = i (p0/m_B)^LB (q0/M)^LR / (M G0): peak phase +pi/2, height 1/(M G0)."""
+    mo = _all_model()
+    for R, r in enumerate(mo.res_list):
+        if r.chain == W.CHAIN_KSTAR:
+            p0 = O.breakup(W.M_B, r.M, W.M_PSI)
+            q0 = O.breakup(r.M, W.M_K, W.M_PI)
+        else:
+            p0 = O.breakup(W.M_B, r.M, W.M_K)
+            q0 = O.breakup(r.M, W.M_PSI, W.M_PI)
+        A, _, _ = mo.lineshape(R, r.M)
+        ref = 1j * (p0 / W.M_B) ** r.LB * (q0 / r.M) ** r.LR / (r.M * r.G0)
+        assert abs(A - ref) <= 1e-12 * abs(ref)
+
+
+def test_lineshape_vanishes_at_threshold():
+    """Near the K pi threshold A ~ q^L_R: A -> 0 as q -> 0 for L_R >= 1."""
+    mo = _all_model()
+    mth = W.M_K + W.M_PI
+    for R, r in enumerate(mo.res_list):
+        if r.chain != W.CHAIN_KSTAR:
+            continue
+        m1, m2 = mth + 1e-7, mth + 1e-11
+        q1, q2 = O.breakup(m1, W.M_K, W.M_PI), O.breakup(m2, W.M_K, W.M_PI)
+        a1 = abs(mo.lineshape(R, m1)[0])
+        a2 = abs(mo.lineshape(R, m2)[0])
+        assert a2 / a1 == pytest.approx((q2 / q1) ** r.LR, rel=1e-3)
+
+
+def test_lineshape_derivatives_match_finite_differences():
+    mo = _all_model()
+    for R, r in enumerate(mo.res_list):
+        mrun = r.M + 0.37 * r.G0 if r.chain == W.CHAIN_KSTAR else 4.3
+        A, dM, dG = mo.lineshape(R, mrun)
+        h = 1e-6
+        fdM = (mo.lineshape(R, mrun, M=r.M + h)[0] - mo.lineshape(R, mrun, M=r.M - h)[0]) / (2 * h)
+        fdG = (mo.lineshape(R, mrun, G0=r.G0 + h)[0] - mo.lineshape(R, mrun, G0=r.G0 - h)[0]) / (2 * h)
+        assert abs(dM - fdM) <= 1e-7 * max(abs(dM), 1e-12) + 1e-12
+        assert abs(dG - fdG) <= 1e-7 * max(abs(dG), 1e-12) + 1e-12
+
+
+# ---------------------------------------------------------------- kinematics
+def test_kstar_angles_round_trip():
+    mo = _all_model()
+    pts = W.uniform_points(2000, 11)
+    k = mo.kinematics(pts)
+    ok = k[:, 0] > 1e-6
+    assert np.allclose(k[ok, 9], pts[1][ok], atol=1e-11)
+    assert np.allclose(k[ok, 10], pts[2][ok], atol=1e-12)
+    assert np.allclose(k[ok, 11], np.cos(pts[3][ok].astype(np.float64)), atol=1e-11)
+    assert np.allclose(k[ok, 12], np.sin(pts[3][ok].astype(np.float64)), atol=1e-11)
+
+
+def test_dalitz_slope():
+    """At fixed m_Kpi, m^2_psi pi is linear in cos theta_K* with slope -2 p q m_B / m."""
+    mo = _all_model()
+    for m in (0.7, 0.9, 1.4, 2.0, 2.15):
+        c = np.linspace(-0.9, 0.9, 7)
+        pts = (np.full(7, m), c, np.zeros(7), np.zeros(7))
+        k = mo.kinematics(pts)
+        m2 = k[:, 2] ** 2
+        p, q = k[0, 0], k[0, 1]
+        slope = np.polyfit(c, m2, 1)[0]
+        assert slope == pytest.approx(-2 * p * q * W.M_B / m, rel=1e-10)
+        assert np.max(np.abs(np.polyfit(c, m2, 2)[0])) < 1e-9
+
+
+def test_cos_theta_z_invariant_mass_identity():
+    """In the Z frame: m_Kpi^2 = mK^2 + mpi^2 + 2 (E_K E_pi - |p_K||p_pi| cos theta_Z),
+    with E_K, E_pi, |p| fixed by m_psi pi (two-body relations in the Z frame)."""
+    mo = _all_model()
+    pts = W.uniform_points(500, 12)
+    k = mo.kinematics(pts)
+    mz = k[:, 2]
+    EK = (W.M_B ** 2 - mz ** 2 - W.M_K ** 2) / (2 * mz)
+    Epi = (mz ** 2 + W.M_PI ** 2 - W.M_PSI ** 2) / (2 * mz)
+    pK = np.sqrt(np.maximum(EK ** 2 - W.M_K ** 2, 0))
+    ppi = np.sqrt(np.maximum(Epi ** 2 - W.M_PI ** 2, 0))
+    m2 = W.M_K ** 2 + W.M_PI ** 2 + 2 * (EK * Epi - pK * ppi * k[:, 3])
+    ok = k[:, 0] > 1e-3
+    assert np.allclose(m2[ok], pts[0][ok].astype(np.float64) ** 2, rtol=1e-10)
+
+
+def test_z_frame_angles_are_unit():
+    mo = _all_model()
+    k = mo.kinematics(W.uniform_points(500, 13))
+    assert np.allclose(k[:, 5] ** 2 + k[:, 6] ** 2, 1, atol=1e-12)
+    assert np.allclose(k[:, 7] ** 2 + k[:, 8] ** 2, 1, atol=1e-12)
+    assert np.all(np.abs(k[:, 3]) <= 1 + 1e-12) and np.all(np.abs(k[:, 4]) <= 1 + 1e-12)
+
+
+# ---------------------------------------------------------------- exact angular integrals
+def _angular_rule(n_gl=6, n_phi=9):
+    x, w = npleg.leggauss(n_gl)
+    ph = -math.pi + 2 * math.pi * np.arange(n_phi) / n_phi
+    wp = np.full(n_phi, 2 * math.pi / n_phi)
+    cK, cpsi, phi = np.meshgrid(x, x, ph, indexing="ij")
+    wt = np.einsum("i,j,k->ijk", w, w, wp)
+    return cK.ravel(), cpsi.ravel(), phi.ravel(), wt.ravel()
+
+
+def _kstar_angular_closed_form(mo, c, m):
+    """int S dcK dcpsi dphi for a K*-only model: the phi integral removes
+    lambda != lambda', the cos theta_K* integral removes J != J'
+    (int d^J_{l0} d^J'_{l0} = 2/(2J+1) delta), and sum_xi int d^1_{l xi}^2 = 4/3."""
+    tot = 0.0
+    for lam in (-1, 0, 1):
+        byJ = {}
+        for k, (R, l) in enumerate(zip(mo.col_res, mo.col_lam)):
+            if l != lam:
+                continue
+            r = mo.res_list[R]
+            byJ.setdefault(r.J, 0j)
+            byJ[r.J] += c[k] * mo.lineshape(R, m)[0]
+        tot += sum(2 / (2 * J + 1) * abs(v) ** 2 for J, v in byJ.items())
+    return 2 * math.pi * 4 / 3 * tot
+
+
+def test_angular_closure_kstar_all_spins():
+    res = W.KSTAR_TABLE
+    mo = O.Model(res)
+    c = W.draw_couplings(res, 99)
+    p = W.couplings_to_params(c)
+    cK, cpsi, phi, wt = _angular_rule()
+    for m in (0.7, 0.9, 1.2, 1.43, 1.78, 2.05, 2.17):
+        S, _ = mo.density(p, (np.full(len(cK), m), cK, cpsi, phi))
+        assert np.dot(wt, S) == pytest.approx(_kstar_angular_closed_form(mo, c, m), rel=1e-12)
+
+
+def test_z_only_angular_integral_is_rotation_invariant():
+    """For a Z-only model at fixed (m, cK) the J/psi angles enter through a rotation of
+    the mu+ direction, so int S dcpsi dphi = 2 pi (4/3) sum_l' |H_l'|^2 |A_Z d^1_{0 l'}(theta_Z)|^2."""
+    res = [W.Z4430]
+    mo = O.Model(res)
+    c = np.array([0.7 - 0.2j, -0.3 + 0.5j])  # columns: lambda' = 0, lambda' = +-1
+    p = W.couplings_to_params(c)
+    x, w = npleg.leggauss(6)
+    ph = -math.pi + 2 * math.pi * np.arange(9) / 9
+    cpsi, phi = np.meshgrid(x, ph, indexing="ij")
+    wt = np.einsum("i,j->ij", w, np.full(9, 2 * math.pi / 9)).ravel()
+    cpsi, phi = cpsi.ravel(), phi.ravel()
+    for m, cK in [(0.9, 0.3), (1.4, -0.7), (1.9, 0.95), (2.1, -0.1)]:
+        n = len(cpsi)
+        pts = (np.full(n, m), np.full(n, cK), cpsi, phi)
+        S, _ = mo.density(p, pts)
+        kin = mo.kinematics(pts)
+        mz, cz = kin[0, 2], kin[0, 3]
+        A = mo.lineshape(0, mz)[0]
+        ref = 2 * math.pi * 4 / 3 * abs(A) ** 2 * (
+            abs(c[0]) ** 2 * O.wigner_d(1, 0, 0, cz) ** 2 +
+            abs(c[1]) ** 2 * (O.wigner_d(1, 0, 1, cz) ** 2 + O.wigner_d(1, 0, -1, cz) ** 2))
+        assert np.dot(wt, S) == pytest.approx(ref, rel=1e-12)
+
+
+# ---------------------------------------------------------------- normalisation
+M_END = W.M_B - W.M_PSI           # p = 0 beyond this
+M_TH = W.M_K + W.M_PI             # q = 0 below this
+
+
+def _m_rule(res, n=24):
+    """Composite Gauss-Legendre rule on [M_LO, M_END] with panels refined around each
+    pole, s = sqrt(m - M_TH) on the first panel and t = sqrt(M_END - m) on the last,
+    which make the square-root edges of p and q smooth."""
+    bps = {W.M_LO, M_END}
+    for r in res:
+        for k in (0.25, 0.5, 1, 2, 4, 8, 16):
+            for sgn in (-1, 1):
+                v = r.M + sgn * k * r.G0
+                if W.M_LO + 0.02 < v < M_END - 0.02:
+                    bps.add(v)
+    bps.add(W.M_LO + 0.02)
+    bps.add(M_END - 0.02)
+    bps = sorted(bps)
+    x, w = npleg.leggauss(n)
+    nodes, wts = [], []
+    for a, b in zip(bps[:-1], bps[1:]):
+        if a == W.M_LO:
+            s0, s1 = math.sqrt(a - M_TH), math.sqrt(b - M_TH)
+            s = 0.5 * (s1 - s0) * x + 0.5 * (s1 + s0)
+            nodes.append(M_TH + s * s)
+            wts.append(0.5 * (s1 - s0) * w * 2 * s)
+        elif b == M_END:
+            t0, t1 = 0.0, math.sqrt(b - a)
+            t = 0.5 * (t1 - t0) * x + 0.5 * (t1 + t0)
+            nodes.append(M_END - t * t)
+            wts.append(0.5 * (t1 - t0) * w * 2 * t)
+        else:
+            nodes.append(0.5 * (b - a) * x + 0.5 * (b + a))
+            wts.append(0.5 * (b - a) * w)
+    return np.concatenate(nodes), np.concatenate(wts)
+
+
+def _norm_1d(mo, c):
+    def f(m):
+        return O.breakup(W.M_B, m, W.M_PSI) * O.breakup(m, W.M_K, W.M_PI) * \
+            _kstar_angular_closed_form(mo, c, m)
+    pts = sorted({r.M for r in mo.res_list})
+    v, err = integrate.quad(f, W.M_LO, M_END, points=pts, epsabs=0, epsrel=1e-13, limit=800)
+    return v
+
+
+def test_pdf_integrates_to_one_tiny_model():
+    """Brute-force 4D tensor quadrature of P = S p q / I on the two-K* model, with I
+    from the exact angular integral and an adaptive 1D quadrature in m."""
+    res = W.CONFIGS["tiny"].resonances
+    mo = O.Model(res)
+    c = W.draw_couplings(res, W.CONFIGS["tiny"].coupling_seed)
+    p = W.couplings_to_params(c)
+    I1 = _norm_1d(mo, c)
+    mn, mw = _m_rule(res)
+    cK, cpsi, phi, wt = _angular_rule()
+    tot = 0.0
+    for m, w in zip(mn, mw):
+        S, pq = mo.density(p, (np.full(len(cK), m), cK, cpsi, phi))
+        tot += w * np.dot(wt, S * pq)
+    assert tot / I1 == pytest.approx(1.0, abs=1e-10)
+
+
+def test_mc_normalisation_within_statistical_error():
+    res = W.CONFIGS["tiny"].resonances
+    mo = O.Model(res)
+    c = W.draw_couplings(res, W.CONFIGS["tiny"].coupling_seed)
+    p = W.couplings_to_params(c)
+    I1 = _norm_1d(mo, c)
+    pts = W.uniform_points(200_000, 5)
+    S, pq = mo.density(p, pts)
+    f = W.BOX_VOLUME * S * pq
+    Imc = mo.norm(p, pts)
+    assert Imc == pytest.approx(f.mean(), rel=1e-12)
+    sigma = f.std() / math.sqrt(len(f))
+    assert abs(Imc - I1) < 4 * sigma
+
+
+def test_gram_reproduces_normalisation():
+    """I = (V/N) (u^T G u + u'^T G u') with u = (Re c, -Im c), u' = (Im c, Re c) interleaved."""
+    res = W.KSTAR_TABLE + [W.Z4430]
+    mo = O.Model(res)
+    c = W.draw_couplings(res, 3)
+    p = W.couplings_to_params(c)
+    pts = W.uniform_points(3000, 6)
+    G = mo.gram(p, pts)
+    u = np.empty(2 * len(c)); u[0::2] = c.real; u[1::2] = -c.imag
+    v = np.empty(2 * len(c)); v[0::2] = c.imag; v[1::2] = c.real
+    I_g = W.BOX_VOLUME / 3000 * (u @ G @ u + v @ G @ v)
+    assert I_g == pytest.approx(mo.norm(p, pts), rel=1e-12)
+    assert np.allclose(G, G.T, rtol=0, atol=1e-12 * np.abs(G).max())
+
+
+# ---------------------------------------------------------------- likelihood
+def _setup(name="kstar10_z", n=3000, n_mc=6000, float_names=None):
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    fl = cfg.float_mg if float_names is None else float_names
+    mo = O.Model(res, float_names=fl)
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c, W.float_mg_values(res, fl))
+    ev = W.peaked_points(n, cfg.data_seed, res)
+    nm = W.uniform_points(n_mc, cfg.norm_seed)
+    return mo, c, p, ev, nm
+
+
+def test_nll_invariant_under_global_phase_and_scale():
+    mo, c, p, ev, nm = _setup()
+    nll0 = mo.nll(p, ev, nm)[0]
+    K = len(c)
+    for beta in (0.3, -2.0):
+        c2 = c * np.exp(1j * beta)
+        p2 = p.copy(); p2[0:2 * K:2] = c2.real; p2[1:2 * K:2] = c2.imag
+        assert mo.nll(p2, ev, nm)[0] == pytest.approx(nll0, abs=1e-12 * abs(nll0))
+    p3 = p.copy(); p3[:2 * K] *= 3.7
+    assert mo.nll(p3, ev, nm)[0] == pytest.approx(nll0, abs=1e-12 * abs(nll0))
+
+
+def test_nll_gradient_matches_central_differences():
+    mo, c, p, ev, nm = _setup(n=1500, n_mc=3000)
+    _, g, _, rc = mo.nll(p, ev, nm, grad=True)
+    assert rc == 0
+    h = 1e-5
+    scale = np.abs(g).max()
+    for i in range(len(p)):
+        pp = p.copy(); pp[i] += h
+        a = mo.nll(pp, ev, nm)[0]
+        pp[i] -= 2 * h
+        b = mo.nll(pp, ev, nm)[0]
+        fd = (a - b) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3 * scale), (i, fd, g[i])
+
+
+def test_gradient_phase_and_scale_identities():
+    """NLL is homogeneous of degree 0 in c and invariant under c -> e^{i b} c, so
+    sum_k (Re c dIm - Im c dRe) = 0 and sum_k (Re c dRe + Im c dIm) = 0."""
+    mo, c, p, ev, nm = _setup(n=2000, n_mc=4000)
+    _, g, _, _ = mo.nll(p, ev, nm, grad=True)
+    K = len(c)
+    gr, gi = g[0:2 * K:2], g[1:2 * K:2]
+    scale = np.sum(np.abs(c.real * gr) + np.abs(c.imag * gi))
+    assert abs(np.sum(c.real * gi - c.imag * gr)) < 1e-10 * scale
+    assert abs(np.sum(c.real * gr + c.imag * gi)) < 1e-10 * scale
+
+
+def test_nll_domain_error_on_zero_density():
+    mo, c, p, ev, nm = _setup("tiny", n=50, n_mc=100, float_names=())
+    p0 = np.zeros_like(p)
+    nll, _, _, rc = mo.nll(p0, ev, nm)
+    assert rc == -1 and math.isinf(nll)
+
+
+# ---------------------------------------------------------------- generator
+def test_generator_follows_the_model_in_m():
+    """Accept-reject events: their m_Kpi histogram matches the 1D density
+    p q int S dOmega / I (chi^2 / ndf near 1)."""
+    cfg = W.CONFIGS["tiny"]
+    res = cfg.resonances
+    mo = O.Model(res)
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c)
+    (m, _, _, _), used, fmax = mo.generate(p, 20000, 1234)
+    I1 = _norm_1d(mo, c)
+    edges = np.linspace(W.M_LO, M_END, 41)
+    h, _ = np.histogram(m, edges)
+
+    def dens(x):
+        return O.breakup(W.M_B, x, W.M_PSI) * O.breakup(x, W.M_K, W.M_PI) * \
+            _kstar_angular_closed_form(mo, c, x) / I1
+    exp = np.array([integrate.quad(dens, a, b, epsrel=1e-10)[0] for a, b in zip(edges[:-1], edges[1:])])
+    exp *= len(m)
+    keep = exp > 5
+    chi2 = np.sum((h[keep] - exp[keep]) ** 2 / exp[keep])
+    ndf = keep.sum()
+    assert chi2 / ndf < 2.0
+    assert abs(exp.sum() - len(m)) < 1e-6 * len(m)
