@@ -1,0 +1,343 @@
+"""Benchmark of the amplitude-fit hot path: NLL + gradient evaluations per second.
+
+One step = one evaluation of -2 ln L and its full gradient (couplings and the
+floated masses/widths) over every data event and every normalisation point of
+the workload, at a new parameter point.  Default workload: 10 K* + Z(4430),
+5e6 data events, 2^24 uniform normalisation points, Z mass and width floating.
+
+  value      device throughput: steps enqueued back to back through the C ABI
+             (amp4d_enqueue_eval, parameters already in device memory), timed
+             with CUDA events on the launching stream.
+  e2e        the same steps through the synchronous user call
+             amp4d_eval_nll_grad: parameters copied from pinned host memory and
+             NLL + gradient read back to the host inside every step.
+  roofline   the dominant kernel's achieved FP32 rate (formula flops per event
+             x events / mean launch time, launch time from CUDA events recorded
+             around it inside the timed region) against the FP32 peak of 152 SMs
+             x 128 lanes x 2 flop x 2.07 GHz.
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload, scaled
+             to the full workload.
+
+--impl reference times the FP64 oracle (the reference arm) on the same config.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FMA lanes x 2 flop x max SM clock
+METRIC = "NLL+grad evals/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# Formula flop count per event of the adjoint kernel (FP32, FMA = 2 flop,
+# special-function ops counted as 1 each).  Derived from the per-event
+# arithmetic of Eq. 2-5, 10-12 as written in the kernels:
+#   per lineshape (Eq. 2-3):      barrier polynomials, 1/sqrt, powers, width,
+#                                 (M-m)(M+m), 1/|D|^2, A            ~ 46 + 4 SFU
+#   per K* column (Eq. 4-5):      d_l scaling + hi/lo complex MAC      14
+#   K* angular set-up:            sqrt x2, sincos, d^1 table, Psi      ~ 40 + 4 SFU
+#   coherent sum a_xi:            3 complex MAC x 2 xi                 24
+#   Z angular set-up (Eq. 10):    sqrt x2, d^1 table                    ~ 20 + 3 SFU
+#   per Z (Eq. 10-11):            Om0, Om1 (x 2 xi), hi/lo MAC          ~ 70
+#   |a|^2, ln S (split)           ~ 12 + 2 SFU
+# adjoint (gradient):
+#   v_l                           3 x 2 complex conj-MAC               24
+#   per K* column                 complex scale + mul + 2 accumulates  14
+#   per floated K* (M, G0)        y, dA/dM, dA/dG0, 2 accumulates      ~ 40
+#   per Z                         w0, w1, 2 complex mul, 4 accumulates  ~ 40 (+ 40 if floated)
+# ---------------------------------------------------------------------------
+def flops_per_event(res_list, float_names, grad=True):
+    nK = sum(1 for r in res_list if r.chain == W.CHAIN_KSTAR)
+    nZ = len(res_list) - nK
+    colsK = sum(1 if r.J == 0 else 3 for r in res_list if r.chain == W.CHAIN_KSTAR)
+    colsZ = len(W.columns(res_list)) - colsK
+    f = 50 * (nK + nZ) + 14 * colsK + 44 + 24 + 14
+    if nZ:
+        f += 23 + 70 * nZ
+    if grad:
+        f += 24 + 14 * colsK
+        f += sum(40 for r in res_list if r.chain == W.CHAIN_KSTAR and r.name in float_names)
+        f += 40 * nZ + sum(40 for r in res_list if r.chain == W.CHAIN_Z and r.name in float_names)
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(cfg, rank=0):
+    res = cfg.resonances
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    params = W.couplings_to_params(c, W.float_mg_values(res, cfg.float_mg))
+    ev = W.peaked_points(cfg.n_events, cfg.data_seed + 1000 * rank, res)
+    nm = W.uniform_points(cfg.n_norm, cfg.norm_seed + 1000 * rank)
+    return res, params, ev, nm
+
+
+def step_params(params, k, n_col):
+    """Parameter point of step k: couplings rotated/scaled slightly (a new point per step)."""
+    p = params.copy()
+    s = 1.0 + 1e-3 * math.sin(0.7 * k)
+    p[:2 * n_col] *= s
+    return p
+
+
+def oracle_baseline(cfg, frac, reps_min_s=10.0, max_reps=30):
+    """FP64 oracle NLL+grad on a 1/frac sample of the workload; evals/s scaled to full size."""
+    import oracle as O
+    res, params, ev, nm = make_workload(cfg)
+    n_s = max(1, cfg.n_events // frac)
+    m_s = max(1, cfg.n_norm // frac)
+    evs = tuple(a[:n_s] for a in ev)
+    nms = tuple(a[:m_s] for a in nm)
+    om = O.Model(res, float_names=cfg.float_mg)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        om.nll(step_params(params, reps, om.n_cols), evs, nms, grad=True)
+        reps += 1
+        if time.perf_counter() - t0 > reps_min_s or reps >= max_reps:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    full = dt * (cfg.n_events + cfg.n_norm) / (n_s + m_s)
+    return {"value": 1.0 / full, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d events + %d normalisation points per eval (1/%d of the workload), "
+                      "%d evals, time scaled by events+points" % (n_s, m_s, frac, reps),
+            "sec_per_sample_eval": dt}
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    res, params, ev, nm = make_workload(cfg)
+    frac = args.ref_frac
+    n_s, m_s = cfg.n_events // frac, cfg.n_norm // frac
+    evs = tuple(a[:n_s] for a in ev)
+    nms = tuple(a[:m_s] for a in nm)
+    om = O.Model(res, float_names=cfg.float_mg)
+    for k in range(args.warmup):
+        om.nll(step_params(params, k, om.n_cols), evs, nms, grad=True)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        om.nll(step_params(params, k, om.n_cols), evs, nms, grad=True)
+    dt = (time.perf_counter() - t0) / args.steps
+    full = dt * (cfg.n_events + cfg.n_norm) / (n_s + m_s)
+    val = 1.0 / full
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": full * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "n_events": cfg.n_events, "n_norm": cfg.n_norm,
+                       "resonances": len(res), "float_mg": cfg.float_mg},
+            "cpu_baseline": {"value": val, "unit": "evals/s", "cores": O.num_threads(),
+                             "kind": "oracle",
+                             "sample": "each step: %d events + %d points (1/%d), scaled" % (n_s, m_s, frac)},
+            "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large", choices=sorted(W.CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frac", type=int, default=16)
+    ap.add_argument("--ref-frac", type=int, default=64)
+    args = ap.parse_args()
+    cfg = W.CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    import paper_2007_14931_gb300 as A
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+
+    res, params, ev, nm = make_workload(cfg, rank)
+    model = A.Model(res, float_names=cfg.float_mg)
+    P = model.n_params
+    dev = [torch.from_numpy(a).cuda() for a in ev]
+    devn = [torch.from_numpy(a).cuda() for a in nm]
+    model.set_events(*dev)
+    model.set_norm_points(*devn)
+    del dev, devn
+
+    K, Wm = args.steps, args.warmup
+    pts = np.stack([step_params(params, k, model.n_cols) for k in range(K + Wm)])
+    p_dev = torch.from_numpy(pts).cuda()
+    out_dev = torch.zeros((K + Wm, 6 + P), dtype=torch.float64, device="cuda")
+    for k in range(Wm):
+        model.enqueue_eval(A.AMP4D_EVAL_NLL_GRAD, p_dev[k], out_dev[k])
+    torch.cuda.synchronize()
+
+    # device-timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    model.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(K):
+        model.enqueue_eval(A.AMP4D_EVAL_NLL_GRAD, p_dev[Wm + k], out_dev[Wm + k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof_ms, prof_n = model.profile_read()
+    model.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    outs = out_dev.cpu().numpy()
+    assert np.all(outs[Wm:, 5] == 0), "evaluation reported a domain error"
+
+    # end-to-end through the synchronous user call (host params in, host NLL + grad out)
+    host_pts = torch.from_numpy(pts).pin_memory().numpy()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        model.eval_nll_grad(host_pts[Wm + k])
+    t_e2e = time.perf_counter() - t0
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+
+    value = world * K / (ms / 1e3)
+    e2e_value = world * K / t_e2e
+    # dominant kernel among the timed phases
+    names = ["table", "data_grad_kernel", "norm_grad_kernel", "reductions"]
+    tot = prof_ms.sum()
+    dom = int(np.argmax(prof_ms))
+    units = cfg.n_events if dom == 1 else cfg.n_norm
+    fpe = flops_per_event(res, cfg.float_mg, grad=True)
+    mean_launch_s = prof_ms[dom] / max(1, prof_n[dom]) / 1e3
+    achieved = fpe * units / mean_launch_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "n_events": cfg.n_events, "n_norm": cfg.n_norm,
+                   "resonances": len(res), "params": P, "float_mg": cfg.float_mg,
+                   "path": "plain recompute + adjoint gradient, uniform normalisation points",
+                   "l2": "inputs larger than L2 (%.2f GB of event records)" % (
+                       (15 * cfg.n_events + 16 * cfg.n_norm) * 4 / 1e9)},
+        "events_per_s": value * cfg.n_events,
+        "points_per_s": value * (cfg.n_events + cfg.n_norm),
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * P,
+                "d2h_bytes_per_step": 8 * (6 + P)},
+        "gpu_launches": int(6 * K),
+        "phases_ms_per_step": {n: float(prof_ms[i] / max(1, prof_n[i])) for i, n in enumerate(names)},
+        "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": None, "flops_per_event": fpe, "units_per_launch": units,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (of nominal)"},
+        "clocks": clk,
+        "nll_last": float(outs[-1, 0]),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(cfg, args.cpu_frac)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    model.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * amp4d -- GPU hot path of the four-dimensional B0 -> J/psi K+ pi- amplitude fit
+ * (Sur, Cristella, Di Florio, Mastrapasqua, "A GPU based multidimensional
+ * amplitude analysis to search for tetraquark candidates").
+ *
+ * C ABI.  Plain pointers and sizes only; no exceptions cross it.  Every call
+ * returns an amp4d_status (0 = AMP4D_OK, < 0 = error); amp4d_last_error()
+ * returns a message for the last failure on a model.
+ *
+ * What is computed (Methodology section):
+ *   A^R(m)      lineshape, Eq. 2 with the running width of Eq. 3 and ratio-form
+ *               Blatt-Weisskopf barrier factors;
+ *   B_k,xi(e)   basis column k = (resonance R, helicity l) for muon helicity xi:
+ *               K*  A^R(m_Kpi) d^J_{l0}(theta_K*) e^{i l phi} d^1_{l xi}(theta_psi)   (Eq. 4)
+ *               Z   A^Z(m_psipi) d^J_{0l'}(theta_Z) e^{i l' phi~} d^1_{l' xi}(theta~_psi)
+ *                   e^{i xi alpha}, with l' = +-1 tied by H_{-l'} = eta H_{l'}     (Eq. 10, 11)
+ *   S(e)        sum_xi |sum_k c_k B_k,xi(e)|^2                                (Eq. 5, Eq. 12)
+ *   I           (V / N_mc) sum_n w_n S(x_n), the numerical normalisation over MC
+ *               phase-space points (State-of-the-art section), w = p q for uniform points
+ *   NLL         -2 sum_e [ ln S(e) + ln(p_e q_e) - ln I ]   (unbinned ML, Introduction)
+ * where p is the K pi momentum in the B frame and q the K momentum in the K pi
+ * frame; the PDF of an event is S p q / I.
+ *
+ * Event coordinates (Eq. 1 with cos theta_K* of Eq. 4):
+ *   m    = m_Kpi in [m_lo, m_hi] (GeV), cK = cos theta_K*, cpsi = cos theta_J/psi,
+ *   phi  = angle between the J/psi and K pi decay planes in [-pi, pi].
+ * All event arrays are FP32 structure-of-arrays, one value per event.
+ *
+ * Parameter vector (host, double), length amp4d_num_params():
+ *   [Re c_0, Im c_0, Re c_1, Im c_1, ..., Re c_{K-1}, Im c_{K-1},
+ *    M_R, Gamma_R for every resonance with float_mg = 1, in resonance order].
+ * Column order: resonances in the given order; a K* with J = 0 has one column
+ * (l = 0), a K* with J >= 1 three (l = -1, 0, +1); a Z has the l' = 0 column when
+ * eta = -P (-1)^J = +1, then the tied l' = +-1 column.
+ *
+ * Streams: every call takes a cudaStream_t passed as void* (NULL = legacy
+ * default stream) and is ordered on it.  Calls that return host scalars
+ * synchronise that stream before returning.  A model is not thread-safe: use
+ * one model per host thread.  The library owns all its device buffers.
+ */
+#ifndef AMP4D_H
+#define AMP4D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int amp4d_status;
+
+#define AMP4D_OK 0
+#define AMP4D_ERR_ARG (-1)     /* bad argument (null pointer, size, range)          */
+#define AMP4D_ERR_CUDA (-2)    /* a CUDA runtime call failed; message kept          */
+#define AMP4D_ERR_OOM (-3)     /* device or pinned-host allocation failed           */
+#define AMP4D_ERR_INPUT (-4)   /* an event lies outside the box or is not finite   */
+#define AMP4D_ERR_DOMAIN (-5)  /* S <= 0 at a data event, or I <= 0: NLL = +inf     */
+#define AMP4D_ERR_TIMEOUT (-6) /* a bounded device wait expired                     */
+#define AMP4D_ERR_STATE (-7)   /* call out of order (e.g. eval before set_events)   */
+
+#define AMP4D_CHAIN_KSTAR 0 /* resonance decays to K pi     */
+#define AMP4D_CHAIN_Z 1     /* resonance decays to J/psi pi */
+
+#define AMP4D_PATH_PLAIN 0  /* recompute every amplitude per evaluation            */
+#define AMP4D_PATH_CACHED 1 /* per-event basis cache + normalisation Gram matrix   */
+
+#define AMP4D_MAX_RES 16
+
+#define AMP4D_EVAL_NLL 0      /* amp4d_enqueue_eval: -2 ln L only          */
+#define AMP4D_EVAL_NLL_GRAD 1 /* amp4d_enqueue_eval: -2 ln L and gradient  */
+
+typedef struct {
+    double mB, mpsi, mK, mpi; /* B0, J/psi, K+, pi- masses (GeV) */
+} amp4d_particle_masses;
+
+typedef struct {
+    int chain;    /* AMP4D_CHAIN_KSTAR or AMP4D_CHAIN_Z                          */
+    int J, P;     /* spin and intrinsic parity (+1 / -1) of the resonance        */
+    int LB, LR;   /* orbital angular momenta in the B0 and resonance decays (0..4) */
+    double M, G0; /* pole mass and nominal width (GeV)                           */
+    double r;     /* Blatt-Weisskopf radius (GeV^-1)                             */
+    int float_mg; /* 1: M and G0 are fit parameters (appended to the vector)     */
+} amp4d_resonance;
+
+typedef struct amp4d_model amp4d_model;
+
+/*
+ * Create a model from a resonance list (Eq. 2-5, 10-12).  n_res in
+ * [1, AMP4D_MAX_RES], at most 2 Z resonances, J <= 4, LB, LR <= 4.  The box is
+ * m_Kpi in [m_lo, m_hi] x cK x cpsi in [-1, 1]^2 x phi in [-pi, pi].  path
+ * selects AMP4D_PATH_PLAIN or AMP4D_PATH_CACHED.  *out receives the model; it
+ * uses the current CUDA device.  Errors: ARG, CUDA, OOM.
+ */
+amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d_resonance *res,
+                                int n_res, double m_lo, double m_hi, int path, amp4d_model **out);
+
+/* Free a model and every device buffer it owns.  NULL is accepted. */
+amp4d_status amp4d_model_destroy(amp4d_model *model);
+
+/* Message for the last failure on this model (static storage owned by the model). */
+const char *amp4d_last_error(const amp4d_model *model);
+
+/* Number of basis columns K and of parameters 2K + 2 (#floated resonances). */
+int amp4d_num_columns(const amp4d_model *model);
+int amp4d_num_params(const amp4d_model *model);
+
+/*
+ * Data events.  m, cK, cpsi, phi: n FP32 values each, host or device memory
+ * (any pointer CUDA can address); the library copies them and the caller keeps
+ * ownership.  Every event must lie in the box and be finite, else
+ * AMP4D_ERR_INPUT (amp4d_last_error names the first bad index).  Per-event
+ * parameter-independent kinematics (p, q; the Z-chain angles of Eq. 10) are
+ * computed once here in FP64 and stored as FP32.  n >= 1.
+ */
+amp4d_status amp4d_set_events(amp4d_model *model, const float *m, const float *cK,
+                              const float *cpsi, const float *phi, int64_t n, void *stream);
+
+/*
+ * Normalisation points for the MC integral I (State-of-the-art section: the
+ * PDF is normalised numerically over phase-space points).  Same layout and
+ * ownership as amp4d_set_events.  w: n FP32 weights or NULL, in which case
+ * w = p q (uniform points).  volume: V in I = (V / n) sum w S (the box volume for
+ * uniform points, 1 for importance-sampled points whose w = p q / density).
+ */
+amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const float *cK,
+                                   const float *cpsi, const float *phi, const float *w,
+                                   int64_t n, double volume, void *stream);
+
+/*
+ * -2 ln L at params (host, amp4d_num_params doubles); *nll is host memory.
+ * On AMP4D_ERR_DOMAIN *nll = +INFINITY (the minimiser treats it as a bad step).
+ */
+amp4d_status amp4d_eval_nll(amp4d_model *model, const double *params, double *nll, void *stream);
+
+/*
+ * -2 ln L and its gradient with respect to every parameter (host arrays).
+ * The gradient is the adjoint of the per-event density (couplings: dS/dRe c_k =
+ * 2 Re z_k, dS/dIm c_k = -2 Im z_k, z_k = sum_xi conj(a_xi) B_k,xi; masses and
+ * widths: closed-form derivatives of Eq. 2-3), summed over events and points.
+ */
+amp4d_status amp4d_eval_nll_grad(amp4d_model *model, const double *params, double *nll,
+                                 double *grad, void *stream);
+
+/*
+ * The terms of the NLL: out[0] = sum_e ln S_e, out[1] = sum_e ln(p_e q_e),
+ * out[2] = I, out[3] = number of data events (host, 4 doubles).
+ */
+amp4d_status amp4d_eval_terms(amp4d_model *model, const double *params, double *out,
+                              void *stream);
+
+/*
+ * Per-event signal density S(e) (Eq. 5 / Eq. 12) for the data events:
+ * S_out is DEVICE memory of n_events FP32 values, owned by the caller.
+ * which = 0: data events; which = 1: normalisation points.
+ */
+amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int which,
+                                float *S_out, void *stream);
+
+/*
+ * Enqueue one evaluation on the stream without synchronising (same arithmetic
+ * as amp4d_eval_nll / amp4d_eval_nll_grad).  params: DEVICE memory,
+ * amp4d_num_params doubles.  out: DEVICE memory of 6 + amp4d_num_params doubles
+ * receiving [0] NLL (+inf on a domain error), [1] sum ln S, [2] sum ln(p q),
+ * [3] I, [4] N, [5] status bits (1: S <= 0 / I <= 0, 2: invalid parameters),
+ * [6 ..] the gradient (what = AMP4D_EVAL_NLL_GRAD).  Both buffers are owned by
+ * the caller and must stay valid until the stream has executed the work.
+ * Evaluations of one model must not overlap in time: they share the model's
+ * partial-sum buffers.  Errors: ARG, STATE (no events), CUDA.
+ */
+amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *params, double *out,
+                                void *stream);
+
+/*
+ * Device timing of evaluations (CUDA events around each phase, on the
+ * evaluation's stream).  amp4d_profile_read waits for the recorded work and
+ * returns, then clears, the summed milliseconds and counts of the phases
+ * [0] parameter table, [1] data-event kernel, [2] normalisation kernel,
+ * [3] reductions and NLL assembly (host arrays of 4).
+ */
+amp4d_status amp4d_profile_enable(amp4d_model *model, int on);
+amp4d_status amp4d_profile_read(amp4d_model *model, double *ms, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMP4D_H */

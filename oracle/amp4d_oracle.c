@@ -394,12 +394,19 @@ static void kinematics(const or_model *mo, double m, double cK, double cpsi, dou
 
     o->cthpsi_z = dot3(nmu, z2);
     {
+        /* phi~ is undefined when the K flies along z2 (cos theta_K* = +-1); there
+         * sin theta_Z = 0 and the l' = +-1 terms vanish, so (1, 0) is used. */
         v3 kd = unit3(v3of(Kp));
-        v3 x2 = unit3(sub3(kd, scale3(z2, dot3(kd, z2))));
-        v3 y2 = cross3(z2, x2);
-        double cx = dot3(nmu, x2), cy = dot3(nmu, y2), n = sqrt(cx * cx + cy * cy);
-        o->cphiz = n > 0 ? cx / n : 1.0;
-        o->sphiz = n > 0 ? cy / n : 0.0;
+        v3 raw = sub3(kd, scale3(z2, dot3(kd, z2)));
+        double nr = sqrt(dot3(raw, raw));
+        o->cphiz = 1.0;
+        o->sphiz = 0.0;
+        if (nr > 1e-300) {
+            v3 x2 = scale3(raw, 1.0 / nr);
+            v3 y2 = cross3(z2, x2);
+            double cx = dot3(nmu, x2), cy = dot3(nmu, y2), n = sqrt(cx * cx + cy * cy);
+            if (n > 0) { o->cphiz = cx / n; o->sphiz = cy / n; }
+        }
     }
     {
         v3 u1 = sub3(z1, scale3(nmu, dot3(z1, nmu)));

@@ -1,0 +1,224 @@
+"""Python binding of libamp4d (the GB300 amplitude-fit hot path).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libamp4d.so, reached through its C ABI (include/amp4d.h) with
+ctypes.  The functions below carry the C names; ``Model`` wraps them for
+convenience.  PyTorch supplies device memory and the current stream.
+
+There is no CPU fallback: importing this package fails if the library has not
+been built (``python -m paper_2007_14931_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamp4d.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libamp4d.so is not built; run `python -m paper_2007_14931_gb300.build` "
+                      "(needs nvcc) -- there is no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+AMP4D_OK = 0
+AMP4D_ERR_ARG = -1
+AMP4D_ERR_CUDA = -2
+AMP4D_ERR_OOM = -3
+AMP4D_ERR_INPUT = -4
+AMP4D_ERR_DOMAIN = -5
+AMP4D_ERR_TIMEOUT = -6
+AMP4D_ERR_STATE = -7
+AMP4D_CHAIN_KSTAR = 0
+AMP4D_CHAIN_Z = 1
+AMP4D_PATH_PLAIN = 0
+AMP4D_PATH_CACHED = 1
+AMP4D_MAX_RES = 16
+AMP4D_EVAL_NLL = 0
+AMP4D_EVAL_NLL_GRAD = 1
+
+_ERRNAMES = {AMP4D_ERR_ARG: "ARG", AMP4D_ERR_CUDA: "CUDA", AMP4D_ERR_OOM: "OOM",
+             AMP4D_ERR_INPUT: "INPUT", AMP4D_ERR_DOMAIN: "DOMAIN",
+             AMP4D_ERR_TIMEOUT: "TIMEOUT", AMP4D_ERR_STATE: "STATE"}
+
+
+class amp4d_particle_masses(C.Structure):
+    _fields_ = [("mB", C.c_double), ("mpsi", C.c_double), ("mK", C.c_double), ("mpi", C.c_double)]
+
+
+class amp4d_resonance(C.Structure):
+    _fields_ = [("chain", C.c_int), ("J", C.c_int), ("P", C.c_int), ("LB", C.c_int),
+                ("LR", C.c_int), ("M", C.c_double), ("G0", C.c_double), ("r", C.c_double),
+                ("float_mg", C.c_int)]
+
+
+_vp = C.c_void_p
+_d = C.POINTER(C.c_double)
+_f = C.POINTER(C.c_float)
+
+
+def _proto(name, res, args):
+    fn = getattr(_lib, name)
+    fn.restype = res
+    fn.argtypes = args
+    return fn
+
+
+amp4d_model_create = _proto("amp4d_model_create", C.c_int,
+                            [C.POINTER(amp4d_particle_masses), C.POINTER(amp4d_resonance), C.c_int,
+                             C.c_double, C.c_double, C.c_int, C.POINTER(_vp)])
+amp4d_model_destroy = _proto("amp4d_model_destroy", C.c_int, [_vp])
+amp4d_last_error = _proto("amp4d_last_error", C.c_char_p, [_vp])
+amp4d_num_columns = _proto("amp4d_num_columns", C.c_int, [_vp])
+amp4d_num_params = _proto("amp4d_num_params", C.c_int, [_vp])
+amp4d_set_events = _proto("amp4d_set_events", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int64, _vp])
+amp4d_set_norm_points = _proto("amp4d_set_norm_points", C.c_int,
+                               [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_double, _vp])
+amp4d_eval_nll = _proto("amp4d_eval_nll", C.c_int, [_vp, _d, _d, _vp])
+amp4d_eval_nll_grad = _proto("amp4d_eval_nll_grad", C.c_int, [_vp, _d, _d, _d, _vp])
+amp4d_eval_terms = _proto("amp4d_eval_terms", C.c_int, [_vp, _d, _d, _vp])
+amp4d_eval_density = _proto("amp4d_eval_density", C.c_int, [_vp, _d, C.c_int, _vp, _vp])
+amp4d_enqueue_eval = _proto("amp4d_enqueue_eval", C.c_int, [_vp, C.c_int, _vp, _vp, _vp])
+amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
+amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
+
+EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "amp4d_num_columns",
+            "amp4d_num_params", "amp4d_set_events", "amp4d_set_norm_points", "amp4d_eval_nll",
+            "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
+            "amp4d_profile_enable", "amp4d_profile_read"]
+
+
+class Amp4dError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("amp4d %s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _ptr(a):
+    """Device or host pointer of a float32 contiguous torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__repr__() != "torch.float32" or not a.is_contiguous():
+            raise TypeError("expected a contiguous float32 tensor")
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+        raise TypeError("expected a contiguous float32 array")
+    return a.ctypes.data
+
+
+class Model:
+    """A model built from ``workloads.Resonance`` records (one per resonance)."""
+
+    def __init__(self, res_list, float_names=(), path=AMP4D_PATH_PLAIN, masses=None, box=None):
+        import workloads as W
+        masses = W.PARTICLE_MASSES if masses is None else masses
+        box = (W.M_LO, W.M_HI) if box is None else box
+        self.res_list = list(res_list)
+        arr = (amp4d_resonance * len(res_list))()
+        for i, r in enumerate(res_list):
+            arr[i] = amp4d_resonance(r.chain, r.J, r.P, r.LB, r.LR, r.M, r.G0, r.r,
+                                     1 if r.name in float_names else 0)
+        pm = amp4d_particle_masses(*masses)
+        h = _vp()
+        rc = amp4d_model_create(C.byref(pm), arr, len(res_list), box[0], box[1], path, C.byref(h))
+        if rc != 0:
+            raise Amp4dError(rc, amp4d_last_error(None).decode())
+        self.h = h
+        self.n_cols = amp4d_num_columns(h)
+        self.n_params = amp4d_num_params(h)
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            amp4d_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise Amp4dError(rc, amp4d_last_error(self.h).decode())
+
+    def set_events(self, m, cK, cpsi, phi, stream=None):
+        n = len(m)
+        self._check(amp4d_set_events(self.h, _ptr(m), _ptr(cK), _ptr(cpsi), _ptr(phi), n,
+                                     _stream_ptr(stream)))
+        self.n_events = n
+
+    def set_norm_points(self, m, cK, cpsi, phi, w=None, volume=None, stream=None):
+        import workloads as W
+        volume = W.BOX_VOLUME if volume is None else volume
+        n = len(m)
+        self._check(amp4d_set_norm_points(self.h, _ptr(m), _ptr(cK), _ptr(cpsi), _ptr(phi),
+                                          _ptr(w) if w is not None else None, n, float(volume),
+                                          _stream_ptr(stream)))
+        self.n_norm = n
+
+    def _params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        if p.shape != (self.n_params,):
+            raise ValueError("expected %d parameters" % self.n_params)
+        return p
+
+    def eval_nll(self, params, stream=None, check=True):
+        p = self._params(params)
+        out = C.c_double()
+        rc = amp4d_eval_nll(self.h, p.ctypes.data_as(_d), C.byref(out), _stream_ptr(stream))
+        if check and rc not in (0, AMP4D_ERR_DOMAIN):
+            self._check(rc)
+        return out.value
+
+    def eval_nll_grad(self, params, stream=None):
+        p = self._params(params)
+        out = C.c_double()
+        g = np.zeros(self.n_params)
+        rc = amp4d_eval_nll_grad(self.h, p.ctypes.data_as(_d), C.byref(out), g.ctypes.data_as(_d),
+                                 _stream_ptr(stream))
+        if rc not in (0, AMP4D_ERR_DOMAIN):
+            self._check(rc)
+        return out.value, g
+
+    def eval_terms(self, params, stream=None):
+        p = self._params(params)
+        o = np.zeros(4)
+        self._check(amp4d_eval_terms(self.h, p.ctypes.data_as(_d), o.ctypes.data_as(_d),
+                                     _stream_ptr(stream)))
+        return o
+
+    def enqueue_eval(self, what, params_dev, out_dev, stream=None):
+        """Enqueue an evaluation with device parameters/outputs (torch float64 tensors)."""
+        self._check(amp4d_enqueue_eval(self.h, what, params_dev.data_ptr(), out_dev.data_ptr(),
+                                       _stream_ptr(stream)))
+
+    def profile(self, on=True):
+        self._check(amp4d_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        ms = np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int64)
+        self._check(amp4d_profile_read(self.h, ms.ctypes.data_as(_d),
+                                       cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+        return ms, cnt
+
+    def eval_density(self, params, which=0, out=None, stream=None):
+        import torch
+        p = self._params(params)
+        n = self.n_events if which == 0 else self.n_norm
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device="cuda")
+        self._check(amp4d_eval_density(self.h, p.ctypes.data_as(_d), which, out.data_ptr(),
+                                       _stream_ptr(stream)))
+        return out

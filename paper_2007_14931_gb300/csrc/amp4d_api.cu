@@ -1,0 +1,583 @@
+// C ABI of the amplitude-fit library: model set-up, event ingest, evaluation.
+//
+// An evaluation is a fixed sequence on one stream: k_build_table turns the
+// parameter vector (device memory) into the FP32 table of Eq. 2-3 constants,
+// the per-event kernels run over the data events and the normalisation points,
+// the block partials are reduced in a fixed order and k_finish assembles the
+// NLL (and gradient) into a device output block.  The synchronous calls stage
+// the host parameters into a device buffer, enqueue that sequence and copy the
+// output block back in one transfer.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/amp4d.h"
+#include "amp4d_device.cuh"
+#include "amp4d_launch.h"
+
+using namespace amp4d;
+
+namespace {
+
+struct EventSet {
+    float *rec = nullptr;
+    int64_t n = 0, npad = 0;
+    int nrec = 0, wrec = -1;
+    double lnpq = 0.0;
+    double volume = 0.0;
+    int grid_eval = 0, grid_grad = 0;
+    double *part = nullptr;     // per-block partials (grid_grad x nslot)
+    size_t part_cap = 0;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct amp4d_model {
+    int device = 0;
+    int nsm = 0;
+    amp4d_particle_masses mass{};
+    std::vector<amp4d_resonance> res;
+    std::vector<int> internal;   // internal order (K* first, then Z) -> user index
+    std::vector<int> res_col;    // user resonance -> first column
+    std::vector<int> res_fpos;   // user resonance -> float position or -1
+    std::vector<int> col_res, col_lam;
+    int nK = 0, nZ = 0, n_col = 0, n_float = 0, n_param = 0, nk_max = 2;
+    int nslot = 0;
+    double m_lo = 0, m_hi = 0;
+    int path = AMP4D_PATH_PLAIN;
+    EventSet ev, mc;
+    ModelDev *d_md = nullptr;
+    ModelStatic *d_static = nullptr;
+    double *d_params = nullptr, *h_params = nullptr;
+    double *d_pscale = nullptr;   // per-parameter gradient scale (folded column constants)
+    // per-phase device timing: table, data kernel, normalisation kernel, reductions
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::vector<cudaEvent_t>> prof_pending;
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n[4] = {0, 0, 0, 0};
+    int *d_slot_param = nullptr;
+    double *d_red = nullptr;     // 2 x nslot
+    double *d_out = nullptr, *h_out = nullptr;
+    unsigned *d_status = nullptr;
+    unsigned long long *d_bad = nullptr;
+    double *d_tmp = nullptr;     // scratch for set-up reductions
+    size_t tmp_cap = 0;
+    std::string err;
+};
+
+namespace {
+
+amp4d_status fail(amp4d_model *m, amp4d_status code, const std::string &msg)
+{
+    if (m) m->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(model, e_ == cudaErrorMemoryAllocation ? AMP4D_ERR_OOM       \
+                                                               : AMP4D_ERR_CUDA,    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+void build_slot_map(const amp4d_model *mo, std::vector<int> &map)
+{
+    const int NK = mo->nk_max, NZ = mo->nZ;
+    map.assign(mo->nslot, -1);
+    const int Z0 = 1 + 6 * NK, MG0 = 1 + 6 * NK + 4 * NZ;
+    for (int i = 0; i < mo->nK; ++i) {
+        const int u = mo->internal[i];
+        const amp4d_resonance &r = mo->res[u];
+        const int c = mo->res_col[u];
+        if (r.J == 0) {
+            map[1 + 6 * i + 2] = 2 * c;
+            map[1 + 6 * i + 3] = 2 * c + 1;
+        } else {
+            for (int l = 0; l < 3; ++l) {
+                map[1 + 6 * i + 2 * l] = 2 * (c + l);
+                map[1 + 6 * i + 2 * l + 1] = 2 * (c + l) + 1;
+            }
+        }
+        if (r.float_mg) {
+            map[MG0 + 2 * i] = 2 * mo->n_col + 2 * mo->res_fpos[u];
+            map[MG0 + 2 * i + 1] = 2 * mo->n_col + 2 * mo->res_fpos[u] + 1;
+        }
+    }
+    for (int z = 0; z < mo->nZ; ++z) {
+        const int u = mo->internal[mo->nK + z];
+        const amp4d_resonance &r = mo->res[u];
+        int c = mo->res_col[u];
+        const int eta = -r.P * ((r.J % 2) ? -1 : 1);
+        if (eta == 1) { map[Z0 + 4 * z] = 2 * c; map[Z0 + 4 * z + 1] = 2 * c + 1; ++c; }
+        if (r.J >= 1) { map[Z0 + 4 * z + 2] = 2 * c; map[Z0 + 4 * z + 3] = 2 * c + 1; }
+        if (r.float_mg) {
+            map[MG0 + 2 * (NK + z)] = 2 * mo->n_col + 2 * mo->res_fpos[u];
+            map[MG0 + 2 * (NK + z) + 1] = 2 * mo->n_col + 2 * mo->res_fpos[u] + 1;
+        }
+    }
+}
+
+amp4d_status ensure_tmp(amp4d_model *model, size_t n)
+{
+    if (model->tmp_cap >= n) return AMP4D_OK;
+    if (model->d_tmp) cudaFree(model->d_tmp);
+    model->d_tmp = nullptr;
+    model->tmp_cap = 0;
+    CK(cudaMalloc(&model->d_tmp, n * sizeof(double)));
+    model->tmp_cap = n;
+    return AMP4D_OK;
+}
+
+amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const float *cK,
+                      const float *cpsi, const float *phi, const float *w, int64_t n,
+                      bool is_norm, cudaStream_t st)
+{
+    if (!m || !cK || !cpsi || !phi || n < 1) return fail(model, AMP4D_ERR_ARG, "null array or n < 1");
+    CK(cudaSetDevice(model->device));
+    if (s.rec) { cudaFree(s.rec); s.rec = nullptr; }
+    if (s.part) { cudaFree(s.part); s.part = nullptr; }
+    s.n = 0;
+    const int64_t npad = (n + 3) & ~int64_t(3);
+    const int nrec = model->nZ > 0 ? REC_NZ : REC_NK;
+    const int tot = nrec + (is_norm ? 1 : 0);
+    CK(cudaMalloc(&s.rec, (size_t)tot * npad * sizeof(float)));
+    const float *src[4] = {m, cK, cpsi, phi};
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(s.rec + k * npad, src[k], n * sizeof(float), cudaMemcpyDefault, st));
+    if (is_norm && w)
+        CK(cudaMemcpyAsync(s.rec + nrec * npad, w, n * sizeof(float), cudaMemcpyDefault, st));
+    s.nrec = nrec;
+    s.wrec = is_norm ? nrec : -1;
+    s.npad = npad;
+    PrepArgs a{};
+    a.rec = s.rec;
+    a.npad = npad;
+    a.n = n;
+    a.has_z = model->nZ > 0;
+    a.wrec = s.wrec;
+    a.have_w = (w != nullptr);
+    a.mB = model->mass.mB; a.mpsi = model->mass.mpsi; a.mK = model->mass.mK; a.mpi = model->mass.mpi;
+    a.m_lo = model->m_lo; a.m_hi = model->m_hi;
+    a.grid = (int)std::min<int64_t>((npad + prepare_block() - 1) / prepare_block(), model->nsm * 8);
+    amp4d_status rc = ensure_tmp(model, a.grid + 2);
+    if (rc) return rc;
+    a.part_lnpq = model->d_tmp;
+    a.bad = model->d_bad;
+    a.stream = st;
+    CK(cudaMemsetAsync(model->d_bad, 0xff, sizeof(unsigned long long), st));
+    CK(launch_prepare(a));
+    CK(launch_reduce_cols(model->d_tmp, a.grid, 1, model->d_tmp + a.grid, st));
+    double lnpq = 0;
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&lnpq, model->d_tmp + a.grid, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&bad, model->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (bad != ~0ull) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "%s %llu outside the box or not finite",
+                      is_norm ? "normalisation point" : "event", bad);
+        return fail(model, AMP4D_ERR_INPUT, buf);
+    }
+    s.lnpq = lnpq;
+    const int64_t ngroups = npad / 4;
+    s.grid_eval = (int)std::max<int64_t>(1, std::min<int64_t>((ngroups + eval_block() - 1) / eval_block(),
+                                                              (int64_t)model->nsm * 4));
+    s.grid_grad = (int)std::max<int64_t>(1, std::min<int64_t>((ngroups + grad_block() - 1) / grad_block(),
+                                                              (int64_t)model->nsm * 4));
+    s.part_cap = (size_t)std::max(s.grid_eval, s.grid_grad) * model->nslot;
+    CK(cudaMalloc(&s.part, s.part_cap * sizeof(double)));
+    s.n = n;
+    return AMP4D_OK;
+}
+
+LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cudaStream_t st,
+                    int grid)
+{
+    LaunchArgs a{};
+    a.rec = s.rec;
+    a.npad = s.npad;
+    a.n = s.n;
+    a.wrec = s.wrec;
+    a.md = mo->d_md;
+    a.part = part;
+    a.out = out;
+    a.status = mo->d_status;
+    a.grid = grid;
+    a.nk_max = mo->nk_max;
+    a.nz = mo->nZ;
+    a.stream = st;
+    return a;
+}
+
+amp4d_status check_params(amp4d_model *model, const double *params)
+{
+    if (!params) return fail(model, AMP4D_ERR_ARG, "params is null");
+    for (int i = 0; i < model->n_param; ++i)
+        if (!std::isfinite(params[i])) return fail(model, AMP4D_ERR_ARG, "non-finite parameter");
+    for (size_t u = 0; u < model->res.size(); ++u) {
+        if (!model->res[u].float_mg) continue;
+        const double M = params[2 * model->n_col + 2 * model->res_fpos[u]];
+        const double G = params[2 * model->n_col + 2 * model->res_fpos[u] + 1];
+        if (!(M > 0.0) || !(G > 0.0)) return fail(model, AMP4D_ERR_ARG, "mass and width must be > 0");
+    }
+    return AMP4D_OK;
+}
+
+cudaEvent_t prof_event(amp4d_model *m)
+{
+    if (!m->ev_pool.empty()) {
+        cudaEvent_t e = m->ev_pool.back();
+        m->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Enqueue one evaluation on stream st (no synchronisation).
+amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params, double *d_out,
+                     cudaStream_t st)
+{
+    if (model->ev.n == 0 || model->mc.n == 0)
+        return fail(model, AMP4D_ERR_STATE, "set_events and set_norm_points must come first");
+    std::vector<cudaEvent_t> marks;
+    auto mark = [&]() {
+        if (!model->prof_on) return cudaSuccess;
+        cudaEvent_t e = prof_event(model);
+        marks.push_back(e);
+        return cudaEventRecord(e, st);
+    };
+    CK(mark());
+    CK(launch_build_table(model->d_static, d_params, model->d_md, model->d_pscale, model->d_status, st));
+    CK(mark());
+    double *rd = model->d_red, *rn = model->d_red + model->nslot;
+    if (with_grad) {
+        LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_grad);
+        CK(launch_grad(ad, false));
+        CK(mark());
+        LaunchArgs an = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_grad);
+        CK(launch_grad(an, true));
+        CK(mark());
+        CK(launch_reduce_cols(model->ev.part, model->ev.grid_grad, model->nslot, rd, st));
+        CK(launch_reduce_cols(model->mc.part, model->mc.grid_grad, model->nslot, rn, st));
+        CK(launch_finish(rd, rn, model->d_slot_param, model->d_pscale, model->nslot, model->n_param,
+                         (double)model->ev.n, model->ev.lnpq, model->mc.volume / (double)model->mc.n,
+                         model->d_status, d_out, st));
+    } else {
+        LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
+        CK(launch_eval(ad, 0));
+        CK(mark());
+        LaunchArgs an = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_eval);
+        CK(launch_eval(an, 1));
+        CK(mark());
+        CK(launch_reduce_cols(model->ev.part, model->ev.grid_eval, 1, rd, st));
+        CK(launch_reduce_cols(model->mc.part, model->mc.grid_eval, 1, rn, st));
+        CK(launch_finish(rd, rn, nullptr, model->d_pscale, 1, 0, (double)model->ev.n, model->ev.lnpq,
+                         model->mc.volume / (double)model->mc.n, model->d_status, d_out, st));
+    }
+    CK(mark());
+    if (model->prof_on) model->prof_pending.push_back(marks);
+    return AMP4D_OK;
+}
+
+// Synchronous evaluation from host parameters; leaves the output block in h_out.
+amp4d_status run_eval(amp4d_model *model, const double *params, bool with_grad, cudaStream_t st)
+{
+    amp4d_status rc = check_params(model, params);
+    if (rc) return rc;
+    CK(cudaSetDevice(model->device));
+    std::memcpy(model->h_params, params, model->n_param * sizeof(double));
+    CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    rc = enqueue(model, with_grad, model->d_params, model->d_out, st);
+    if (rc) return rc;
+    const size_t nout = 6 + (with_grad ? model->n_param : 0);
+    CK(cudaMemcpyAsync(model->h_out, model->d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (((unsigned)model->h_out[5]) & 2u) return fail(model, AMP4D_ERR_ARG, "invalid parameters");
+    return AMP4D_OK;
+}
+
+ModelStatic make_static(const amp4d_model *mo)
+{
+    ModelStatic s;
+    std::memset(&s, 0, sizeof s);
+    s.mB = mo->mass.mB; s.mpsi = mo->mass.mpsi; s.mK = mo->mass.mK; s.mpi = mo->mass.mpi;
+    s.n_res = (int)mo->res.size();
+    s.n_col = mo->n_col;
+    s.n_float = mo->n_float;
+    s.n_param = mo->n_param;
+    for (size_t i = 0; i < mo->internal.size(); ++i) {
+        const int u = mo->internal[i];
+        const amp4d_resonance &r = mo->res[u];
+        ResStatic &d = s.res[i];
+        d.M = r.M; d.G0 = r.G0; d.r = r.r;
+        d.chain = r.chain; d.J = r.J; d.LB = r.LB; d.LR = r.LR;
+        d.col = mo->res_col[u];
+        d.fpos = mo->res_fpos[u];
+        d.eta = -r.P * ((r.J % 2) ? -1 : 1);
+        d.zcol0 = d.zcol1 = -1;
+        if (r.chain == AMP4D_CHAIN_Z) {
+            int c = mo->res_col[u];
+            if (d.eta == 1) d.zcol0 = c++;
+            if (r.J >= 1) d.zcol1 = c;
+        }
+    }
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d_resonance *res,
+                                int n_res, double m_lo, double m_hi, int path, amp4d_model **out)
+{
+    amp4d_model *model = nullptr;
+    if (!masses || !res || !out) return fail(nullptr, AMP4D_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (n_res < 1 || n_res > AMP4D_MAX_RES) return fail(nullptr, AMP4D_ERR_ARG, "n_res out of range");
+    if (!(m_lo > masses->mK + masses->mpi) || !(m_hi > m_lo))
+        return fail(nullptr, AMP4D_ERR_ARG, "bad m_Kpi box");
+    if (path != AMP4D_PATH_PLAIN && path != AMP4D_PATH_CACHED)
+        return fail(nullptr, AMP4D_ERR_ARG, "unknown path");
+    int nz = 0;
+    for (int i = 0; i < n_res; ++i) {
+        const amp4d_resonance &r = res[i];
+        if (r.chain != AMP4D_CHAIN_KSTAR && r.chain != AMP4D_CHAIN_Z)
+            return fail(nullptr, AMP4D_ERR_ARG, "bad chain");
+        if (r.J < 0 || r.J > 4 || r.LB < 0 || r.LB > 4 || r.LR < 0 || r.LR > 4 ||
+            (r.P != 1 && r.P != -1) || !(r.M > 0) || !(r.G0 > 0) || !(r.r >= 0))
+            return fail(nullptr, AMP4D_ERR_ARG, "bad resonance record");
+        if (r.chain == AMP4D_CHAIN_Z) {
+            ++nz;
+            const int eta = -r.P * ((r.J % 2) ? -1 : 1);
+            if (r.J == 0 && eta != 1) return fail(nullptr, AMP4D_ERR_ARG, "Z with no allowed helicity");
+        }
+    }
+    if (nz > 2) return fail(nullptr, AMP4D_ERR_ARG, "at most 2 Z resonances");
+    model = new amp4d_model();
+    model->mass = *masses;
+    model->res.assign(res, res + n_res);
+    model->m_lo = m_lo;
+    model->m_hi = m_hi;
+    model->path = path;
+    model->res_col.assign(n_res, 0);
+    model->res_fpos.assign(n_res, -1);
+    for (int i = 0; i < n_res; ++i) {
+        const amp4d_resonance &r = res[i];
+        model->res_col[i] = model->n_col;
+        if (r.float_mg) model->res_fpos[i] = model->n_float++;
+        if (r.chain == AMP4D_CHAIN_KSTAR) {
+            if (r.J == 0) { model->col_res.push_back(i); model->col_lam.push_back(0); }
+            else for (int l = -1; l <= 1; ++l) { model->col_res.push_back(i); model->col_lam.push_back(l); }
+        } else {
+            const int eta = -r.P * ((r.J % 2) ? -1 : 1);
+            if (eta == 1) { model->col_res.push_back(i); model->col_lam.push_back(0); }
+            if (r.J >= 1) { model->col_res.push_back(i); model->col_lam.push_back(1); }
+        }
+        model->n_col = (int)model->col_res.size();
+        if (r.chain == AMP4D_CHAIN_KSTAR) model->internal.push_back(i);
+    }
+    for (int i = 0; i < n_res; ++i)
+        if (res[i].chain == AMP4D_CHAIN_Z) model->internal.push_back(i);
+    model->nZ = nz;
+    model->nK = n_res - nz;
+    model->n_param = 2 * model->n_col + 2 * model->n_float;
+    model->nk_max = nk_bucket(model->nK);
+    model->nslot = grad_num_slots(model->nk_max, nz);
+    cudaError_t e = cudaGetDevice(&model->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&model->nsm, cudaDevAttrMultiProcessorCount, model->device);
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_md, sizeof(ModelDev));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_static, sizeof(ModelStatic));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_params, std::max(1, model->n_param) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_pscale, std::max(1, model->n_param) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&model->h_params, std::max(1, model->n_param) * sizeof(double));
+    if (e == cudaSuccess) {
+        ModelStatic ms = make_static(model);
+        e = cudaMemcpy(model->d_static, &ms, sizeof ms, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_slot_param, model->nslot * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_red, 2 * model->nslot * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_out, (6 + model->n_param) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&model->h_out, (6 + model->n_param) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        std::vector<int> map;
+        build_slot_map(model, map);
+        e = cudaMemcpy(model->d_slot_param, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        std::string msg = std::string("model_create: ") + cudaGetErrorString(e);
+        amp4d_status code = e == cudaErrorMemoryAllocation ? AMP4D_ERR_OOM : AMP4D_ERR_CUDA;
+        amp4d_model_destroy(model);
+        return fail(nullptr, code, msg);
+    }
+    *out = model;
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_model_destroy(amp4d_model *model)
+{
+    if (!model) return AMP4D_OK;
+    cudaSetDevice(model->device);
+    for (EventSet *s : {&model->ev, &model->mc}) {
+        if (s->rec) cudaFree(s->rec);
+        if (s->part) cudaFree(s->part);
+    }
+    if (model->d_md) cudaFree(model->d_md);
+    if (model->d_static) cudaFree(model->d_static);
+    if (model->d_params) cudaFree(model->d_params);
+    if (model->d_pscale) cudaFree(model->d_pscale);
+    if (model->h_params) cudaFreeHost(model->h_params);
+    for (auto &v : model->prof_pending)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+    for (cudaEvent_t e : model->ev_pool) cudaEventDestroy(e);
+    if (model->d_slot_param) cudaFree(model->d_slot_param);
+    if (model->d_red) cudaFree(model->d_red);
+    if (model->d_out) cudaFree(model->d_out);
+    if (model->h_out) cudaFreeHost(model->h_out);
+    if (model->d_status) cudaFree(model->d_status);
+    if (model->d_bad) cudaFree(model->d_bad);
+    if (model->d_tmp) cudaFree(model->d_tmp);
+    delete model;
+    return AMP4D_OK;
+}
+
+const char *amp4d_last_error(const amp4d_model *model)
+{
+    return model ? model->err.c_str() : g_create_error.c_str();
+}
+
+int amp4d_num_columns(const amp4d_model *model) { return model ? model->n_col : -1; }
+int amp4d_num_params(const amp4d_model *model) { return model ? model->n_param : -1; }
+
+amp4d_status amp4d_set_events(amp4d_model *model, const float *m, const float *cK,
+                              const float *cpsi, const float *phi, int64_t n, void *stream)
+{
+    if (!model) return AMP4D_ERR_ARG;
+    return load_set(model, model->ev, m, cK, cpsi, phi, nullptr, n, false, (cudaStream_t)stream);
+}
+
+amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const float *cK,
+                                   const float *cpsi, const float *phi, const float *w,
+                                   int64_t n, double volume, void *stream)
+{
+    if (!model) return AMP4D_ERR_ARG;
+    if (!(volume > 0.0)) return fail(model, AMP4D_ERR_ARG, "volume must be > 0");
+    amp4d_status rc = load_set(model, model->mc, m, cK, cpsi, phi, w, n, true, (cudaStream_t)stream);
+    if (rc == AMP4D_OK) model->mc.volume = volume;
+    return rc;
+}
+
+amp4d_status amp4d_eval_nll(amp4d_model *model, const double *params, double *nll, void *stream)
+{
+    if (!model || !nll) return AMP4D_ERR_ARG;
+    amp4d_status rc = run_eval(model, params, false, (cudaStream_t)stream);
+    if (rc) return rc;
+    *nll = model->h_out[0];
+    if (model->h_out[5] != 0.0 || !std::isfinite(model->h_out[0])) {
+        *nll = INFINITY;
+        return fail(model, AMP4D_ERR_DOMAIN, "S <= 0 at a data event, p q = 0, or I <= 0");
+    }
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_eval_nll_grad(amp4d_model *model, const double *params, double *nll,
+                                 double *grad, void *stream)
+{
+    if (!model || !nll || !grad) return AMP4D_ERR_ARG;
+    amp4d_status rc = run_eval(model, params, true, (cudaStream_t)stream);
+    if (rc) return rc;
+    *nll = model->h_out[0];
+    std::memcpy(grad, model->h_out + 6, model->n_param * sizeof(double));
+    if (model->h_out[5] != 0.0 || !std::isfinite(model->h_out[0])) {
+        *nll = INFINITY;
+        return fail(model, AMP4D_ERR_DOMAIN, "S <= 0 at a data event, p q = 0, or I <= 0");
+    }
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_eval_terms(amp4d_model *model, const double *params, double *out, void *stream)
+{
+    if (!model || !out) return AMP4D_ERR_ARG;
+    amp4d_status rc = run_eval(model, params, false, (cudaStream_t)stream);
+    if (rc) return rc;
+    out[0] = model->h_out[1];
+    out[1] = model->h_out[2];
+    out[2] = model->h_out[3];
+    out[3] = model->h_out[4];
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int which,
+                                float *S_out, void *stream)
+{
+    if (!model || !params || !S_out || (which != 0 && which != 1)) return AMP4D_ERR_ARG;
+    EventSet &s = which == 0 ? model->ev : model->mc;
+    if (s.n == 0) return fail(model, AMP4D_ERR_STATE, "no events loaded");
+    cudaStream_t st = (cudaStream_t)stream;
+    amp4d_status rc = check_params(model, params);
+    if (rc) return rc;
+    CK(cudaSetDevice(model->device));
+    std::memcpy(model->h_params, params, model->n_param * sizeof(double));
+    CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CK(launch_build_table(model->d_static, model->d_params, model->d_md, model->d_pscale, model->d_status, st));
+    LaunchArgs a = args_for(model, s, s.part, S_out, st, s.grid_eval);
+    CK(launch_eval(a, 2));
+    CK(cudaStreamSynchronize(st));
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *params, double *out,
+                                void *stream)
+{
+    if (!model || !params || !out || (what != AMP4D_EVAL_NLL && what != AMP4D_EVAL_NLL_GRAD))
+        return model ? fail(model, AMP4D_ERR_ARG, "bad enqueue arguments") : AMP4D_ERR_ARG;
+    CK(cudaSetDevice(model->device));
+    return enqueue(model, what == AMP4D_EVAL_NLL_GRAD, params, out, (cudaStream_t)stream);
+}
+
+amp4d_status amp4d_profile_enable(amp4d_model *model, int on)
+{
+    if (!model) return AMP4D_ERR_ARG;
+    model->prof_on = on != 0;
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_profile_read(amp4d_model *model, double *ms, int64_t *count)
+{
+    if (!model || !ms || !count) return AMP4D_ERR_ARG;
+    for (auto &v : model->prof_pending) {
+        CK(cudaEventSynchronize(v.back()));
+        for (size_t i = 0; i + 1 < v.size() && i < 4; ++i) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, v[i], v[i + 1]));
+            model->prof_ms[i] += t;
+            model->prof_n[i] += 1;
+        }
+        for (cudaEvent_t e : v) model->ev_pool.push_back(e);
+    }
+    model->prof_pending.clear();
+    for (int i = 0; i < 4; ++i) {
+        ms[i] = model->prof_ms[i];
+        count[i] = model->prof_n[i];
+        model->prof_ms[i] = 0.0;
+        model->prof_n[i] = 0;
+    }
+    return AMP4D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Device-side data structures and per-event amplitude arithmetic (FP32).
+//
+// Event records are structure-of-arrays FP32, one record of npad values per
+// quantity; npad is a multiple of 4 so every record is read with float4 loads.
+// Parameter-independent kinematics are produced once per event set in FP64
+// (kernels in amp4d_prepare.cu) and stored here as FP32.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/amp4d.h"
+
+namespace amp4d {
+
+// Record indices.
+enum : int {
+    REC_M = 0,     // m_Kpi
+    REC_CK = 1,    // cos theta_K*
+    REC_CPSI = 2,  // cos theta_J/psi
+    REC_PHI = 3,   // phi
+    REC_P = 4,     // K pi momentum in the B frame
+    REC_Q = 5,     // K momentum in the K pi frame
+    REC_NK = 6,    // records of a K*-only model
+    REC_MZ = 6,    // m_J/psi pi
+    REC_PZ = 7,    // Z momentum in the B frame
+    REC_QZ = 8,    // pi momentum in the Z frame
+    REC_CZ = 9,    // cos theta_Z
+    REC_CTZ = 10,  // cos theta~_J/psi
+    REC_CPZ = 11,  // cos phi~
+    REC_SPZ = 12,  // sin phi~
+    REC_CA = 13,   // cos alpha
+    REC_SA = 14,   // sin alpha
+    REC_NZ = 15,   // records of a model with a Z
+};
+
+// Per-resonance constants of Eq. 2-3 at the current (M, G0), built by
+// k_build_table in FP64 at the start of every evaluation.  Every constant that
+// scales a whole basis column (the pole barrier factors sqrt(KB KR), m_B^-LB and
+// the irrational Wigner-d normalisations) is folded into the column's coupling
+// in FP64; the couplings and the constants left inside the per-event FP32
+// arithmetic are stored as unevaluated sums hi + lo, so no per-evaluation
+// constant carries a systematic FP32 rounding into S.
+struct ResDev {
+    float Mhi, Mlo;   // pole mass M
+    float r2hi, r2lo; // Blatt-Weisskopf radius squared
+    float Ghi, Glo;   // G0 M^2 KR / q0^(2 LR + 1): M Gamma(m) = G q^(2LR+1) / (P_LR(r^2 q^2) m)
+    float dNhi, dNlo; // d ln(sqrt(KB KR))/dM, KB = P_LB(r^2 p0^2), KR = P_LR(r^2 q0^2)
+    float dGhi, dGlo; // d ln(M Gamma)/dM at fixed m
+    float iGhi, iGlo; // 1 / G0
+    int chain, J, LB, LR;
+    int col;          // first basis column
+    int fpos;         // index among floated resonances, -1 if fixed
+    int eta;          // Z: H_{-l} = eta H_{l} (Eq. 11)
+    int zcol0;        // Z: column of l' = 0 or -1 when absent
+    int zcol1;        // Z: column of l' = +-1 or -1 when absent
+};
+
+// Static description of a resonance (internal order: K* first, then Z).
+struct ResStatic {
+    double M, G0, r;          // model values (replaced by floated parameters)
+    int chain, J, LB, LR;
+    int col, fpos, eta, zcol0, zcol1, pad_;
+};
+
+struct ModelStatic {
+    double mB, mpsi, mK, mpi;
+    int n_res, n_col, n_float, n_param;
+    ResStatic res[AMP4D_MAX_RES];
+};
+
+struct ModelDev {
+    int n_res, n_col, n_float, n_param;
+    ResDev res[AMP4D_MAX_RES];
+    float2 c[3 * AMP4D_MAX_RES];   // folded couplings, high part
+    float2 cl[3 * AMP4D_MAX_RES];  // folded couplings, low part
+};
+
+// ----------------------------------------------------------------------------
+// Complex helpers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a += b * c
+__device__ __forceinline__ void cfma(float2 &a, float2 b, float2 c)
+{
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+// a += conj(b) * c
+__device__ __forceinline__ void cfma_conj(float2 &a, float2 b, float2 c)
+{
+    a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// ----------------------------------------------------------------------------
+// Barrier polynomial P_L(z) = x^(2L+2) |h_L(x)|^2, z = x^2, by Horner.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float bw_poly(int L, float z)
+{
+    switch (L) {
+    case 0: return 1.0f;
+    case 1: return z + 1.0f;
+    case 2: return fmaf(z + 3.0f, z, 9.0f);
+    case 3: return fmaf(fmaf(z + 6.0f, z, 45.0f), z, 225.0f);
+    default: return fmaf(fmaf(fmaf(z + 10.0f, z, 135.0f), z, 1575.0f), z, 11025.0f);
+    }
+}
+
+__device__ __forceinline__ float ipow(float x, int n)
+{
+    float r = 1.0f;
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
+}
+
+// ----------------------------------------------------------------------------
+// Wigner d for J <= 4 from Legendre closed forms, without irrational factors:
+//   d0 = d^J_{00}(c) = P_J(c),
+//   d1 = -s P_J'(c) = sqrt(J (J+1)) d^J_{10}(c),  d^J_{-1,0} = -d^J_{10}.
+// The 1/sqrt(J (J+1)) is folded into the l = +-1 couplings.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void wigner_l0(int J, float c, float s, float &d0, float &d1)
+{
+    const float c2 = c * c;
+    switch (J) {
+    case 0: d0 = 1.0f; d1 = 0.0f; break;
+    case 1: d0 = c; d1 = -s; break;
+    case 2:
+        d0 = fmaf(1.5f, c2, -0.5f);
+        d1 = -s * (3.0f * c);
+        break;
+    case 3:
+        d0 = c * fmaf(2.5f, c2, -1.5f);
+        d1 = -s * fmaf(7.5f, c2, -1.5f);
+        break;
+    default:
+        d0 = fmaf(fmaf(4.375f, c2, -3.75f), c2, 0.375f);
+        d1 = -s * (c * fmaf(17.5f, c2, -7.5f));
+        break;
+    }
+}
+
+// d^1_{l xi}(theta) for l in {-1, 0, 1}, xi in {+1 (x=0), -1 (x=1)}; the l = 0
+// row is given without its 1/sqrt(2), which is folded into the l = 0 couplings.
+__device__ __forceinline__ void wigner_1(float c, float s, float d[3][2])
+{
+    const float h = 0.5f;
+    d[0][0] = h * (1.0f - c); d[0][1] = h * (1.0f + c);   // l = -1
+    d[1][0] = s;              d[1][1] = -s;               // l = 0 (times 1/sqrt 2)
+    d[2][0] = h * (1.0f + c); d[2][1] = h * (1.0f - c);   // l = +1
+}
+
+// ----------------------------------------------------------------------------
+// Lineshape of Eq. 2 with Eq. 3 at running mass mrun (momenta p, q), without
+// the column constant sqrt(KB KR) m_B^-LB (folded into the couplings):
+//   A' = p^LB (q/m)^LR / sqrt(P_LB(z_B) P_LR(z_R)) / (M^2 - m^2 - i M Gamma(m)),
+//   M Gamma(m) = G q^(2LR+1) / (P_LR(z_R) m),  z_B = r^2 p^2,  z_R = r^2 q^2.
+// Also returns 1/D and M Gamma for the adjoint.
+// ----------------------------------------------------------------------------
+struct LineOut {
+    float2 A;
+    float2 invD;   // 1 / D
+    float MG;      // M Gamma(m)
+};
+
+__device__ __forceinline__ LineOut lineshape(const ResDev &r, float mrun, float invm, float p,
+                                             float q)
+{
+    const float p2 = p * p, q2 = q * q;
+    const float PB = bw_poly(r.LB, fmaf(r.r2hi, p2, r.r2lo * p2));
+    const float PR = bw_poly(r.LR, fmaf(r.r2hi, q2, r.r2lo * q2));
+    const float rs = __frcp_rn(sqrtf(PB * PR));
+    const float num = rs * ipow(p, r.LB) * ipow(q * invm, r.LR);
+    const float X = ipow(q, 2 * r.LR + 1) * invm * __frcp_rn(PR);
+    const float MG = fmaf(r.Ghi, X, r.Glo * X);
+    // M^2 - m^2 = (M - m)(M + m) with M = hi + lo: (hi - m) is exact near the pole.
+    const float dm = (r.Mhi - mrun) + r.Mlo;
+    const float sm = (r.Mhi + mrun) + r.Mlo;
+    const float Dr = dm * sm;
+    const float den = __frcp_rn(fmaf(Dr, Dr, MG * MG));
+    LineOut o;
+    o.invD = make_float2(Dr * den, MG * den);          // 1/(Dr - i MG) = (Dr + i MG)/|D|^2
+    o.A = make_float2(num * o.invD.x, num * o.invD.y);
+    o.MG = MG;
+    return o;
+}
+
+}  // namespace amp4d

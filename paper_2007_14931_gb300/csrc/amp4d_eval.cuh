@@ -1,0 +1,487 @@
+// Per-event amplitude, likelihood and adjoint-gradient kernel templates.
+//
+// One thread handles four consecutive events per step (float4 loads of every
+// record), grid-stride over the event set.  Per event, in FP32 registers:
+//   lineshapes A_R (Eq. 2-3) with the resonance table in shared memory,
+//   d^J_{l0}(theta_K*), e^{i l phi} d^1_{l xi}(theta_psi) (Eq. 4),
+//   the Z-chain factors (Eq. 10-11) from precomputed Z-frame angles,
+//   a_xi = sum_k c_k B_k,xi and S = |a_+|^2 + |a_-|^2 (Eq. 5, 12).
+// Data kernels sum ln S, normalisation kernels sum w S; each thread keeps a
+// compensated FP32 sum (ln S split as ln(mantissa) + exponent ln 2), blocks
+// reduce in FP64 and write one partial per block.
+// Instantiated per resonance-count bucket in amp4d_eval_nk*.cu.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#include "amp4d_device.cuh"
+#include "amp4d_launch.h"
+
+namespace amp4d {
+
+
+// Resonances internal order: K* first (at most NK), then Z (exactly NZ).
+template <int NK, int NZ>
+struct EvState {
+    float2 a[2];
+    float S;
+    float2 AK[NK];
+    float d0[NK], d1[NK];
+    float2 invDK[NK];
+    float MGK[NK];
+    float2 Psi[3][2];
+    float2 AZ[NZ > 0 ? NZ : 1];
+    float2 Om0[NZ > 0 ? NZ : 1][2], Om1[NZ > 0 ? NZ : 1][2];
+    float2 invDZ[NZ > 0 ? NZ : 1];
+    float MGZ[NZ > 0 ? NZ : 1];
+};
+
+template <int NK, int NZ>
+__device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
+                                           EvState<NK, NZ> &ev)
+{
+    const float m = r[REC_M], cK = r[REC_CK], cpsi = r[REC_CPSI], phi = r[REC_PHI];
+    const float p = r[REC_P], q = r[REC_Q];
+    const float invm = __frcp_rn(m);
+    const float sK = sqrtf(fmaxf(0.0f, fmaf(-cK, cK, 1.0f)));
+    const float spsi = sqrtf(fmaxf(0.0f, fmaf(-cpsi, cpsi, 1.0f)));
+    float sph, cph;
+    sincosf(phi, &sph, &cph);
+    float d1p[3][2];
+    wigner_1(cpsi, spsi, d1p);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        ev.Psi[0][x] = make_float2(cph * d1p[0][x], -sph * d1p[0][x]);  // e^{-i phi}
+        ev.Psi[1][x] = make_float2(d1p[1][x], 0.0f);
+        ev.Psi[2][x] = make_float2(cph * d1p[2][x], sph * d1p[2][x]);   // e^{+i phi}
+    }
+    float2 u[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const int nK = md.n_res - NZ;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        if (k < nK) {
+            const ResDev &rs = md.res[k];
+            LineOut L = lineshape(rs, m, invm, p, q);
+            float d0, d1;
+            wigner_l0(rs.J, cK, sK, d0, d1);
+            ev.AK[k] = L.A;
+            ev.d0[k] = d0;
+            ev.d1[k] = d1;
+            ev.invDK[k] = L.invD;
+            ev.MGK[k] = L.MG;
+            if (rs.J == 0) {
+                const float2 x = cscale(L.A, d0);
+                cfma(u[1], md.c[rs.col], x);
+                cfma(u[1], md.cl[rs.col], x);
+            } else {
+                const float2 xm = cscale(L.A, -d1), x0 = cscale(L.A, d0), xp = cscale(L.A, d1);
+                cfma(u[0], md.c[rs.col], xm);
+                cfma(u[0], md.cl[rs.col], xm);
+                cfma(u[1], md.c[rs.col + 1], x0);
+                cfma(u[1], md.cl[rs.col + 1], x0);
+                cfma(u[2], md.c[rs.col + 2], xp);
+                cfma(u[2], md.cl[rs.col + 2], xp);
+            }
+        } else {
+            ev.AK[k] = make_float2(0.f, 0.f);
+            ev.d0[k] = ev.d1[k] = 0.f;
+            ev.invDK[k] = make_float2(0.f, 0.f);
+            ev.MGK[k] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        float2 a = make_float2(0.f, 0.f);
+        cfma(a, ev.Psi[0][x], u[0]);
+        cfma(a, ev.Psi[1][x], u[1]);
+        cfma(a, ev.Psi[2][x], u[2]);
+        ev.a[x] = a;
+    }
+    if constexpr (NZ > 0) {
+        const float mZ = r[REC_MZ], pZ = r[REC_PZ], qZ = r[REC_QZ];
+        const float cZ = r[REC_CZ], ctz = r[REC_CTZ];
+        const float2 ephz = make_float2(r[REC_CPZ], r[REC_SPZ]);
+        const float ca = r[REC_CA], sa = r[REC_SA];
+        const float invmZ = __frcp_rn(mZ);
+        const float sZ = sqrtf(fmaxf(0.0f, fmaf(-cZ, cZ, 1.0f)));
+        const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
+        float d1t[3][2];
+        wigner_1(ctz, stz, d1t);
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) {
+            const ResDev &rs = md.res[nK + z];
+            LineOut L = lineshape(rs, mZ, invmZ, pZ, qZ);
+            float dz0, dz1;
+            wigner_l0(rs.J, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
+            ev.AZ[z] = L.A;
+            ev.invDZ[z] = L.invD;
+            ev.MGZ[z] = L.MG;
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                const float2 eal = make_float2(ca, x == 0 ? sa : -sa);  // e^{i xi alpha}
+                float2 o0 = cscale(eal, dz0 * d1t[1][x]);
+                float2 t = cscale(ephz, -dz1 * d1t[2][x]);
+                float2 ephm = make_float2(ephz.x, -ephz.y);
+                t = cadd(t, cscale(ephm, (float)rs.eta * dz1 * d1t[0][x]));
+                float2 o1 = cmul(t, eal);
+                ev.Om0[z][x] = o0;
+                ev.Om1[z][x] = o1;
+                float2 s = make_float2(0.f, 0.f);
+                if (rs.zcol0 >= 0) {
+                    cfma(s, md.c[rs.zcol0], o0);
+                    cfma(s, md.cl[rs.zcol0], o0);
+                }
+                if (rs.zcol1 >= 0) {
+                    cfma(s, md.c[rs.zcol1], o1);
+                    cfma(s, md.cl[rs.zcol1], o1);
+                }
+                cfma(ev.a[x], L.A, s);
+            }
+        }
+    }
+    ev.S = cabs2(ev.a[0]) + cabs2(ev.a[1]);
+}
+
+// Compensated FP32 accumulator.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_write(double v, double *smem, double *out)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) smem[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < BLOCK / 32; ++i) t += smem[i];
+        *out = t;
+    }
+}
+
+__device__ __forceinline__ void load_model(const ModelDev *g, ModelDev *s)
+{
+    const int n = sizeof(ModelDev) / 4;
+    const int *src = reinterpret_cast<const int *>(g);
+    int *dst = reinterpret_cast<int *>(s);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+template <int NREC>
+__device__ __forceinline__ void load4(const float *__restrict__ rec, int64_t npad, int64_t g,
+                                      float v[4][NREC])
+{
+#pragma unroll
+    for (int k = 0; k < NREC; ++k) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(rec + k * npad) + g);
+        v[0][k] = t.x; v[1][k] = t.y; v[2][k] = t.z; v[3][k] = t.w;
+    }
+}
+
+// MODE_SUM_LNS: data sum of ln S; MODE_SUM_WS: normalisation sum of w S;
+// MODE_WRITE: S per event to out.
+enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
+
+template <int NK, int NZ, int MODE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, int64_t npad,
+                                                int64_t n, int wrec, const ModelDev *__restrict__ gmd,
+                                                double *__restrict__ part, float *__restrict__ S_out,
+                                                unsigned *__restrict__ status)
+{
+    constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
+    __shared__ ModelDev md;
+    __shared__ double red[BLOCK / 32];
+    load_model(gmd, &md);
+    Kahan acc;
+    int esum = 0;
+    bool bad = false;
+    const int64_t ngroups = npad >> 2;
+    for (int64_t g = blockIdx.x * (int64_t)BLOCK + threadIdx.x; g < ngroups;
+         g += (int64_t)gridDim.x * BLOCK) {
+        float v[4][NREC];
+        load4<NREC>(rec, npad, g, v);
+        float wv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (MODE == MODE_SUM_WS) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(rec + wrec * npad) + g);
+            wv[0] = t.x; wv[1] = t.y; wv[2] = t.z; wv[3] = t.w;
+        }
+        float Sv[4];
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) {
+            EvState<NK, NZ> ev;
+            eval_event<NK, NZ>(md, v[j], ev);
+            Sv[j] = ev.S;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = 4 * g + j;
+            if (e >= n) break;
+            if (MODE == MODE_SUM_LNS) {
+                if (!(Sv[j] > 0.0f)) { bad = true; continue; }
+                int ex;
+                float mant = frexpf(Sv[j], &ex);
+                if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
+                acc.add(logf(mant));
+                esum += ex;
+            } else if (MODE == MODE_SUM_WS) {
+                acc.add(wv[j] * Sv[j]);
+            }
+        }
+        if (MODE == MODE_WRITE) {
+            if (4 * g + 3 < n) {
+                reinterpret_cast<float4 *>(S_out)[g] = make_float4(Sv[0], Sv[1], Sv[2], Sv[3]);
+            } else {
+                for (int j = 0; j < 4; ++j)
+                    if (4 * g + j < n) S_out[4 * g + j] = Sv[j];
+            }
+        }
+    }
+    if (MODE == MODE_WRITE) return;
+    if (bad) atomicOr(status, 1u);
+    double tot = acc.value();
+    if (MODE == MODE_SUM_LNS) tot += (double)esum * 0.69314718055994530942;
+    block_write<BLOCK>(tot, red, part + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint gradient.  Slots (internal order), after slot 0 = ln S or w S sum:
+//   K* k:  1 + 6k + {0..5}   dS/d(Re, Im) c for l = -1, 0, +1
+//   Z z:   1 + 6NK + 4z + {0..3}  dS/d(Re, Im) c for the l' = 0 and l' = +-1 columns
+//   R:     1 + 6NK + 4NZ + 2R + {0, 1}  dS/dM, dS/dG0 (internal resonance index R)
+// Every slot is scaled by 1/S (data) or w (normalisation).
+// ---------------------------------------------------------------------------
+template <int NK, int NZ>
+struct Slots {
+    static constexpr int K0 = 1;
+    static constexpr int Z0 = 1 + 6 * NK;
+    static constexpr int MG0 = 1 + 6 * NK + 4 * NZ;
+    static constexpr int N = 1 + 6 * NK + 4 * NZ + 2 * (NK + NZ);
+};
+
+// dA/dM and dA/dG0 from Eq. 2-3: A = N / D, D = M^2 - m^2 - i M Gamma(m).  The
+// per-resonance derivative constants are double-float: a systematic FP32
+// rounding of them would not cancel between the data and normalisation terms.
+__device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, float2 invD,
+                                                 float MG, float2 &dAdM, float2 &dAdG)
+{
+    // dD/dM = 2M - i MG dln(MG)/dM
+    const float2 dD = make_float2(2.0f * rs.Mhi + 2.0f * rs.Mlo,
+                                  -fmaf(MG, rs.dGhi, MG * rs.dGlo));
+    const float2 r = cmul(dD, invD);                 // (dD/dM) / D
+    const float2 f = make_float2((rs.dNhi - r.x) + rs.dNlo, -r.y);
+    dAdM = cmul(A, f);
+    // dA/dG0 = -A (dD/dG0)/D = i A (MG / G0) / D
+    const float2 g = cmul(A, invD);
+    const float s = fmaf(MG, rs.iGhi, MG * rs.iGlo);
+    dAdG = make_float2(-g.y * s, g.x * s);
+}
+
+template <int NK, int NZ, bool NORM, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_grad(const float *__restrict__ rec, int64_t npad,
+                                                int64_t n, int wrec, const ModelDev *__restrict__ gmd,
+                                                double *__restrict__ part,
+                                                unsigned *__restrict__ status)
+{
+    constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
+    using SL = Slots<NK, NZ>;
+    __shared__ ModelDev md;
+    __shared__ double red[BLOCK / 32][SL::N];
+    load_model(gmd, &md);
+    Kahan acc0;
+    int esum = 0;
+    bool bad = false;
+    float g[SL::N];
+#pragma unroll
+    for (int i = 0; i < SL::N; ++i) g[i] = 0.f;
+    const int64_t ngroups = npad >> 2;
+    const int nK = md.n_res - NZ;
+    for (int64_t gi = blockIdx.x * (int64_t)BLOCK + threadIdx.x; gi < ngroups;
+         gi += (int64_t)gridDim.x * BLOCK) {
+        float v[4][NREC];
+        load4<NREC>(rec, npad, gi, v);
+        float wv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (NORM) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(rec + wrec * npad) + gi);
+            wv[0] = t.x; wv[1] = t.y; wv[2] = t.z; wv[3] = t.w;
+        }
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = 4 * gi + j;
+            if (e >= n) break;
+            EvState<NK, NZ> ev;
+            eval_event<NK, NZ>(md, v[j], ev);
+            float scale;
+            if (!NORM) {
+                if (!(ev.S > 0.0f)) { bad = true; continue; }
+                int ex;
+                float mant = frexpf(ev.S, &ex);
+                if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
+                acc0.add(logf(mant));
+                esum += ex;
+                scale = 2.0f * __frcp_rn(ev.S);
+            } else {
+                acc0.add(wv[j] * ev.S);
+                scale = 2.0f * wv[j];
+            }
+            // v_l = sum_xi conj(a_xi) Psi_{l xi}
+            float2 vl[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                float2 t = make_float2(0.f, 0.f);
+                cfma_conj(t, ev.a[0], ev.Psi[l][0]);
+                cfma_conj(t, ev.a[1], ev.Psi[l][1]);
+                vl[l] = t;
+            }
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                if (k >= nK) continue;
+                const ResDev &rs = md.res[k];
+                // z for l = -1, 0, +1: A d_l v_l with d_{-1} = -d1, d_0 = d0, d_{+1} = d1
+                const float dl[3] = {-ev.d1[k], ev.d0[k], ev.d1[k]};
+                float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    if (rs.J == 0 && l != 1) continue;
+                    const float2 t = cscale(vl[l], dl[l]);
+                    const float2 z = cmul(ev.AK[k], t);
+                    g[SL::K0 + 6 * k + 2 * l] += scale * z.x;
+                    g[SL::K0 + 6 * k + 2 * l + 1] -= scale * z.y;
+                    if (rs.fpos >= 0) cfma(y, md.c[rs.J == 0 ? rs.col : rs.col + l], t);
+                }
+                if (rs.fpos >= 0) {
+                    float2 dM, dG;
+                    lineshape_derivs(rs, ev.AK[k], ev.invDK[k], ev.MGK[k], dM, dG);
+                    const float2 a = cmul(dM, y), b = cmul(dG, y);
+                    g[SL::MG0 + 2 * k] += scale * a.x;
+                    g[SL::MG0 + 2 * k + 1] += scale * b.x;
+                }
+            }
+            if constexpr (NZ > 0) {
+#pragma unroll
+                for (int z = 0; z < NZ; ++z) {
+                    const ResDev &rs = md.res[nK + z];
+                    float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int x = 0; x < 2; ++x) {
+                        cfma_conj(w0, ev.a[x], ev.Om0[z][x]);
+                        cfma_conj(w1, ev.a[x], ev.Om1[z][x]);
+                    }
+                    const float2 z0 = cmul(ev.AZ[z], w0), z1 = cmul(ev.AZ[z], w1);
+                    g[SL::Z0 + 4 * z + 0] += scale * z0.x;
+                    g[SL::Z0 + 4 * z + 1] -= scale * z0.y;
+                    g[SL::Z0 + 4 * z + 2] += scale * z1.x;
+                    g[SL::Z0 + 4 * z + 3] -= scale * z1.y;
+                    if (rs.fpos >= 0) {
+                        float2 y = make_float2(0.f, 0.f);
+                        if (rs.zcol0 >= 0) cfma(y, md.c[rs.zcol0], w0);
+                        if (rs.zcol1 >= 0) cfma(y, md.c[rs.zcol1], w1);
+                        float2 dM, dG;
+                        lineshape_derivs(rs, ev.AZ[z], ev.invDZ[z], ev.MGZ[z], dM, dG);
+                        const float2 a = cmul(dM, y), b = cmul(dG, y);
+                        g[SL::MG0 + 2 * (NK + z)] += scale * a.x;
+                        g[SL::MG0 + 2 * (NK + z) + 1] += scale * b.x;
+                    }
+                }
+            }
+        }
+    }
+    if (bad) atomicOr(status, 1u);
+    // Block reduction of every slot in FP64.
+    double t0 = acc0.value();
+    if (!NORM) t0 += (double)esum * 0.69314718055994530942;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    {
+        double v0 = warp_sum(t0);
+        if (lane == 0) red[w][0] = v0;
+    }
+#pragma unroll
+    for (int i = 1; i < SL::N; ++i) {
+        double vi = warp_sum((double)g[i]);
+        if (lane == 0) red[w][i] = vi;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SL::N; i += BLOCK) {
+        double t = 0.0;
+        for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww][i];
+        part[(int64_t)blockIdx.x * SL::N + i] = t;
+    }
+}
+
+
+constexpr int EVAL_BLOCK = 256;
+constexpr int GRAD_BLOCK = 128;
+
+template <int NK, int NZ>
+cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
+{
+    switch (mode) {
+    case MODE_SUM_LNS:
+        k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status);
+        break;
+    case MODE_SUM_WS:
+        k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status);
+        break;
+    default:
+        k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+template <int NK, int NZ>
+cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
+{
+    if (norm)
+        k_grad<NK, NZ, true, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, 0, a.stream>>>(
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status);
+    else
+        k_grad<NK, NZ, false, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, 0, a.stream>>>(
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status);
+    return cudaGetLastError();
+}
+
+// Entry for one resonance-count bucket NK, dispatching on the number of Z.
+template <int NK>
+cudaError_t launch_eval_nk(const LaunchArgs &a, int mode)
+{
+    switch (a.nz) {
+    case 0: return launch_eval_t<NK, 0>(a, mode);
+    case 1: return launch_eval_t<NK, 1>(a, mode);
+    case 2: return launch_eval_t<NK, 2>(a, mode);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NK>
+cudaError_t launch_grad_nk(const LaunchArgs &a, bool norm)
+{
+    switch (a.nz) {
+    case 0: return launch_grad_t<NK, 0>(a, norm);
+    case 1: return launch_grad_t<NK, 1>(a, norm);
+    case 2: return launch_grad_t<NK, 2>(a, norm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace amp4d

@@ -1,0 +1,7 @@
+// Instantiation of the per-event kernels for at most 2 K* resonances.
+#include "amp4d_eval.cuh"
+
+namespace amp4d {
+template cudaError_t launch_eval_nk<2>(const LaunchArgs &, int);
+template cudaError_t launch_grad_nk<2>(const LaunchArgs &, bool);
+}  // namespace amp4d

@@ -1,0 +1,298 @@
+// Reductions, the final NLL/gradient assembly, the per-evaluation resonance
+// table, and the dispatch of the per-event kernels to their instantiations.
+#include <cmath>
+#include <cstdint>
+
+#include "amp4d_device.cuh"
+#include "amp4d_launch.h"
+
+namespace amp4d {
+
+int grad_num_slots(int nk_max, int nz) { return 1 + 6 * nk_max + 4 * nz + 2 * (nk_max + nz); }
+
+// ---------------------------------------------------------------------------
+// Deterministic column sums of per-block partials: block j sums column j over
+// nblk rows in a fixed order with Neumaier compensation.
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_cols(const double *__restrict__ part, int nblk, int ncol,
+                              double *__restrict__ out)
+{
+    __shared__ double ss[256], sc[256];
+    const int col = blockIdx.x;
+    double s = 0.0, c = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 256) {
+        const double x = part[(int64_t)b * ncol + col];
+        const double t = s + x;
+        c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            const double a = ss[threadIdx.x], b = ss[threadIdx.x + h];
+            const double t = a + b;
+            const double e = (fabs(a) >= fabs(b)) ? (a - t) + b : (b - t) + a;
+            ss[threadIdx.x] = t;
+            sc[threadIdx.x] += sc[threadIdx.x + h] + e;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[col] = ss[0] + sc[0];
+}
+
+// ---------------------------------------------------------------------------
+// NLL = -2 [ sum ln S + sum ln(pq) - N ln I ],  I = vol_over_n * sum w S, and
+// dNLL = -2 [ sum dS/S - N (vol_over_n sum w dS) / I ] mapped to parameters.
+// out: [0] nll, [1] sum ln S, [2] sum ln pq, [3] I, [4] N, [5] status bits
+// (1: domain, 2: invalid parameters), [6..] grad.
+// ---------------------------------------------------------------------------
+__global__ void k_finish(const double *__restrict__ rd, const double *__restrict__ rn,
+                         const int *__restrict__ slot_param, const double *__restrict__ pscale,
+                         int nslot, int nparam,
+                         double n_events, double lnpq, double vol_over_n,
+                         const unsigned *__restrict__ status, double *__restrict__ out)
+{
+    const double I = vol_over_n * rn[0];
+    unsigned st = *status;
+    const double nll = -2.0 * (rd[0] + lnpq - n_events * log(I));
+    if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
+    const bool bad = st != 0u;
+    if (threadIdx.x == 0) {
+        out[0] = bad ? INFINITY : nll;
+        out[1] = rd[0];
+        out[2] = lnpq;
+        out[3] = I;
+        out[4] = n_events;
+        out[5] = (double)st;
+    }
+    if (slot_param == nullptr) return;
+    for (int p = threadIdx.x; p < nparam; p += blockDim.x) out[6 + p] = 0.0;
+    __syncthreads();
+    for (int s = 1 + threadIdx.x; s < nslot; s += blockDim.x) {
+        const int p = slot_param[s];
+        if (p >= 0)
+            out[6 + p] = bad ? 0.0 : -2.0 * pscale[p] * (rd[s] - n_events * vol_over_n * rn[s] / I);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-evaluation resonance table (Eq. 2-3 constants at the current M, G0), one
+// thread per resonance in FP64:
+//   p0 = p(M), q0 = q(M) two-body momenta at the pole, KB = P_LB(r^2 p0^2),
+//   KR = P_LR(r^2 q0^2), G = G0 M^2 KR / q0^(2LR+1), and the mass derivatives
+//   of ln KB, ln KR and ln(M Gamma) for the adjoint.
+// Each thread also folds its columns' constants into their couplings (pscale
+// keeps them for the gradient) and validates the parameters (status bit 2).
+// ---------------------------------------------------------------------------
+__device__ double two_body_d(double M, double m1, double m2)
+{
+    const double a = (M - m1 - m2) * (M + m1 + m2);
+    const double b = (M - m1 + m2) * (M + m1 - m2);
+    const double l = a * b;
+    return l > 0.0 ? sqrt(l) / (2.0 * M) : 0.0;
+}
+
+__device__ double bw_poly_d(int L, double z)
+{
+    switch (L) {
+    case 0: return 1.0;
+    case 1: return z + 1.0;
+    case 2: return (z + 3.0) * z + 9.0;
+    case 3: return ((z + 6.0) * z + 45.0) * z + 225.0;
+    default: return (((z + 10.0) * z + 135.0) * z + 1575.0) * z + 11025.0;
+    }
+}
+
+__device__ double bw_poly_deriv_d(int L, double z)
+{
+    switch (L) {
+    case 0: return 0.0;
+    case 1: return 1.0;
+    case 2: return 2.0 * z + 3.0;
+    case 3: return (3.0 * z + 12.0) * z + 45.0;
+    default: return ((4.0 * z + 30.0) * z + 270.0) * z + 1575.0;
+    }
+}
+
+__device__ double powi_d(double x, int n)
+{
+    double r = 1.0;
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
+}
+
+__device__ __forceinline__ void split_store(double re, double im, float2 &hi, float2 &lo)
+{
+    hi = make_float2((float)re, (float)im);
+    lo = make_float2((float)(re - (double)hi.x), (float)(im - (double)hi.y));
+}
+
+__global__ void k_build_table(const ModelStatic *__restrict__ st, const double *__restrict__ params,
+                              ModelDev *__restrict__ md, double *__restrict__ pscale,
+                              unsigned *__restrict__ status)
+{
+    const int t = threadIdx.x;
+    __shared__ int bad;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    const int nres = st->n_res, ncol = st->n_col, npar = st->n_param;
+    for (int i = t; i < npar; i += blockDim.x) {
+        if (!isfinite(params[i])) atomicOr(&bad, 1);
+        if (i >= 2 * ncol) pscale[i] = 1.0;
+    }
+    if (t < nres) {
+        const ResStatic &r = st->res[t];
+        double M = r.M, G0 = r.G0;
+        if (r.fpos >= 0) {
+            M = params[2 * ncol + 2 * r.fpos];
+            G0 = params[2 * ncol + 2 * r.fpos + 1];
+        }
+        if (!(M > 0.0) || !(G0 > 0.0)) {
+            atomicOr(&bad, 1);
+            M = r.M;
+            G0 = r.G0;
+        }
+        const double mB = st->mB;
+        double d1, d2, sp;
+        if (r.chain == AMP4D_CHAIN_KSTAR) { d1 = st->mK; d2 = st->mpi; sp = st->mpsi; }
+        else { d1 = st->mpsi; d2 = st->mpi; sp = st->mK; }
+        const double p0 = two_body_d(mB, M, sp), q0 = two_body_d(M, d1, d2);
+        if (!(q0 > 0.0)) atomicOr(&bad, 1);
+        const double r2 = r.r * r.r;
+        const double z0B = r2 * p0 * p0, z0R = r2 * q0 * q0;
+        const double KB = bw_poly_d(r.LB, z0B), KR = bw_poly_d(r.LR, z0R);
+        const double dp02 = M * (M * M - mB * mB - sp * sp) / (mB * mB);   // d(p0^2)/dM
+        const double dd = d1 * d1 - d2 * d2;
+        const double dq02 = (M * M * M * M - dd * dd) / (2.0 * M * M * M); // d(q0^2)/dM
+        const double dlnKB = bw_poly_deriv_d(r.LB, z0B) / KB * r2 * dp02;
+        const double dlnKR = bw_poly_deriv_d(r.LR, z0R) / KR * r2 * dq02;
+        const double dlnq0 = 0.5 * dq02 / (q0 * q0);
+        const double G = G0 * M * M * KR / powi_d(q0, 2 * r.LR + 1);
+        ResDev d;
+        d.Mhi = (float)M;
+        d.Mlo = (float)(M - (double)d.Mhi);
+        d.r2hi = (float)r2;
+        d.r2lo = (float)(r2 - (double)d.r2hi);
+        d.Ghi = (float)G;
+        d.Glo = (float)(G - (double)d.Ghi);
+        const double dN = 0.5 * (dlnKB + dlnKR);
+        const double dG = 2.0 / M - (2 * r.LR + 1) * dlnq0 + dlnKR;
+        const double iG = 1.0 / G0;
+        d.dNhi = (float)dN; d.dNlo = (float)(dN - (double)d.dNhi);
+        d.dGhi = (float)dG; d.dGlo = (float)(dG - (double)d.dGhi);
+        d.iGhi = (float)iG; d.iGlo = (float)(iG - (double)d.iGhi);
+        d.chain = r.chain;
+        d.J = r.J;
+        d.LB = r.LB;
+        d.LR = r.LR;
+        d.col = r.col;
+        d.fpos = r.fpos;
+        d.eta = r.eta;
+        d.zcol0 = r.zcol0;
+        d.zcol1 = r.zcol1;
+        md->res[t] = d;
+        // Column constants: sqrt(KB KR) m_B^-LB times 1/sqrt(2) for the l = 0 J/psi
+        // factor d^1_{0 xi}, or 1/sqrt(J (J+1)) for the l = +-1 factor d^J_{+-1 0}.
+        const double base = sqrt(KB * KR) / powi_d(mB, r.LB);
+        const double k0 = base * 0.70710678118654752440;
+        const double k1 = r.J > 0 ? base / sqrt((double)(r.J * (r.J + 1))) : 0.0;
+        int cols[3], ncols = 0;
+        double kap[3];
+        if (r.chain == AMP4D_CHAIN_KSTAR) {
+            if (r.J == 0) { cols[0] = r.col; kap[0] = k0; ncols = 1; }
+            else {
+                cols[0] = r.col; kap[0] = k1;
+                cols[1] = r.col + 1; kap[1] = k0;
+                cols[2] = r.col + 2; kap[2] = k1;
+                ncols = 3;
+            }
+        } else {
+            if (r.zcol0 >= 0) { cols[ncols] = r.zcol0; kap[ncols++] = k0; }
+            if (r.zcol1 >= 0) { cols[ncols] = r.zcol1; kap[ncols++] = k1; }
+        }
+        for (int j = 0; j < ncols; ++j) {
+            const int k = cols[j];
+            split_store(params[2 * k] * kap[j], params[2 * k + 1] * kap[j], md->c[k], md->cl[k]);
+            pscale[2 * k] = kap[j];
+            pscale[2 * k + 1] = kap[j];
+        }
+    }
+    if (t == 0) {
+        md->n_res = nres;
+        md->n_col = ncol;
+        md->n_float = st->n_float;
+        md->n_param = npar;
+    }
+    __syncthreads();
+    if (t == 0) *status = bad ? 2u : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch
+// ---------------------------------------------------------------------------
+template <int NK> cudaError_t launch_eval_nk(const LaunchArgs &a, int mode);
+template <int NK> cudaError_t launch_grad_nk(const LaunchArgs &a, bool norm);
+extern template cudaError_t launch_eval_nk<2>(const LaunchArgs &, int);
+extern template cudaError_t launch_eval_nk<10>(const LaunchArgs &, int);
+extern template cudaError_t launch_eval_nk<16>(const LaunchArgs &, int);
+extern template cudaError_t launch_grad_nk<2>(const LaunchArgs &, bool);
+extern template cudaError_t launch_grad_nk<10>(const LaunchArgs &, bool);
+extern template cudaError_t launch_grad_nk<16>(const LaunchArgs &, bool);
+
+int nk_bucket(int nk)
+{
+    if (nk <= 2) return 2;
+    if (nk <= 10) return 10;
+    return 16;
+}
+
+cudaError_t launch_eval(const LaunchArgs &a, int mode)
+{
+    switch (a.nk_max) {
+    case 2: return launch_eval_nk<2>(a, mode);
+    case 10: return launch_eval_nk<10>(a, mode);
+    case 16: return launch_eval_nk<16>(a, mode);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_grad(const LaunchArgs &a, bool norm)
+{
+    switch (a.nk_max) {
+    case 2: return launch_grad_nk<2>(a, norm);
+    case 10: return launch_grad_nk<10>(a, norm);
+    case 16: return launch_grad_nk<16>(a, norm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *out,
+                               cudaStream_t s)
+{
+    k_reduce_cols<<<ncol, 256, 0, s>>>(part, nblk, ncol, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_param,
+                          const double *pscale, int nslot, int nparam, double n_events,
+                          double lnpq, double vol_over_n, const unsigned *status, double *out,
+                          cudaStream_t s)
+{
+    k_finish<<<1, 128, 0, s>>>(rd, rn, slot_param, pscale, nslot, nparam, n_events, lnpq,
+                               vol_over_n, status, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_table(const ModelStatic *st, const double *params, ModelDev *md,
+                               double *pscale, unsigned *status, cudaStream_t s)
+{
+    k_build_table<<<1, 64, 0, s>>>(st, params, md, pscale, status);
+    return cudaGetLastError();
+}
+
+int eval_block() { return 256; }
+int grad_block() { return 128; }
+
+}  // namespace amp4d

@@ -9,3 +9,18 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the compiled library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def load_product_module(name):
+    """Load a pure-Python module of the package by path (the package itself
+    refuses to import before its CUDA library is built)."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2007_14931_gb300", name + ".py")
+    key = "amp4d_" + name
+    if key in sys.modules:
+        return sys.modules[key]
+    spec = importlib.util.spec_from_file_location(key, path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[key] = mod
+    spec.loader.exec_module(mod)
+    return mod

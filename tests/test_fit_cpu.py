@@ -1,0 +1,84 @@
+"""Host logic of the fit loop: the variable-metric minimiser, HESSE, the polar
+parametrisation, and a closure fit driven by the FP64 oracle (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import load_product_module
+
+F = load_product_module("fit")
+
+
+def test_migrad_quadratic_exact_minimum_and_covariance():
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(6, 6))
+    H = A @ A.T + 6 * np.eye(6)
+    x0 = rng.normal(size=6)
+    xs = rng.normal(size=6)
+    fg = lambda x: (float((x - xs) @ H @ (x - xs)), 2 * H @ (x - xs))
+    r = F.migrad(fg, x0, tol=1e-8)
+    assert r.converged
+    assert np.allclose(r.x, xs, atol=1e-6)
+    cov, Hn = F.hesse(lambda x: fg(x)[1], r.x)
+    assert np.allclose(Hn, 2 * H, rtol=1e-6)
+    assert np.allclose(cov, 2 * np.linalg.inv(2 * H), rtol=1e-6)
+
+
+def test_migrad_rosenbrock():
+    def fg(x):
+        a, b = x
+        f = (1 - a) ** 2 + 100 * (b - a * a) ** 2
+        return f, np.array([-2 * (1 - a) - 400 * a * (b - a * a), 200 * (b - a * a)])
+    r = F.migrad(fg, [-1.2, 1.0], tol=1e-6, maxiter=2000)
+    assert np.allclose(r.x, [1, 1], atol=1e-3)
+
+
+def test_polar_parametrisation_round_trip_and_chain_rule():
+    par = F.Parametrization(n_cols=4, n_mg=2, fixed_col=1, polar=True)
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=10)
+    p[2], p[3] = 1.0, 0.0
+    th = par.from_params(p)
+    assert np.allclose(par.to_params(th), p)
+    # chain rule against finite differences of a smooth function of p
+    w = rng.normal(size=10)
+    f = lambda t: float(np.sin(par.to_params(t)) @ w)
+    gp = np.cos(par.to_params(th)) * w
+    g = par.grad_to_theta(th, gp)
+    h = 1e-6
+    for i in range(len(th)):
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        assert (f(tp) - f(tm)) / (2 * h) == pytest.approx(g[i], rel=1e-6, abs=1e-9)
+
+
+def test_oracle_closure_fit_tiny():
+    """The paper's validation (Fit validation section): generate from the model,
+    fit from a perturbed start, recover the truth within 3 sigma."""
+    import oracle as O
+    import workloads as W
+    cfg = W.CONFIGS["tiny"]
+    res = cfg.resonances
+    om = O.Model(res)
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p_true = W.couplings_to_params(c)
+    ev, _, _ = om.generate(p_true, 10_000, cfg.data_seed)
+    nm = W.uniform_points(100_000, cfg.norm_seed)
+    fixed = [k for k, (R, l) in enumerate(W.columns(res)) if res[R].name == "K*(892)" and l == 0][0]
+    par = F.Parametrization(len(c), 0, fixed_col=fixed, polar=True)
+    c0 = W.perturbed_start(c)
+    c0[fixed] = 1.0
+    p0 = W.couplings_to_params(c0)
+
+    def fg(p):
+        nll, g, _, _ = om.nll(p, ev, nm, grad=True)
+        return nll, g
+    r = F.fit(fg, par, p0)
+    assert r.converged
+    th_true = par.from_params(p_true)
+    d = r.theta - th_true
+    d[1::2] = (d[1::2] + math.pi) % (2 * math.pi) - math.pi
+    pulls = d / r.errors
+    assert np.all(np.abs(pulls) < 3.5), pulls

@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated by the method's accuracy targets):
+  per-event S: relative 1e-5 where the interference condition number
+      kappa = sum_xi (sum_k |c_k B_k,xi|)^2 / S <= 100, else absolute
+      1e-5 * sum_xi (sum_k |c_k B_k,xi|)^2;
+  NLL: |dNLL| <= 1e-3 (the target at 10^6 events; smaller sets are tighter);
+  gradient: per component <= 1e-6 relative or <= 1e-5 |g|_inf absolute.  The
+      NLL gradient is a difference of a data sum and N dI/I, each ~N times
+      larger than their difference near the optimum; FP32 per-event arithmetic
+      (relative ~1e-8 coherent over a resonance peak) leaves ~1e-6 |g|_inf;
+  normalisation integral I: relative 1e-9.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def A():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2007_14931_gb300 as A
+    return A
+
+
+def _dev(pts):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in pts]
+
+
+def _setup(A, name, n_ev, n_mc, float_names=None, data="peaked", seed_shift=0):
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    fl = cfg.float_mg if float_names is None else float_names
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c, W.float_mg_values(res, fl))
+    om = O.Model(res, float_names=fl)
+    if data == "peaked":
+        ev = W.peaked_points(n_ev, cfg.data_seed + seed_shift, res)
+    elif data == "uniform":
+        ev = W.uniform_points(n_ev, cfg.data_seed + seed_shift, box=(W.M_LO, W.M_END - 1e-6))
+    else:
+        ev, _, _ = om.generate(p, n_ev, cfg.data_seed + seed_shift)
+    nm = W.uniform_points(n_mc, cfg.norm_seed + seed_shift)
+    gm = A.Model(res, float_names=fl)
+    gm.set_events(*_dev(ev))
+    gm.set_norm_points(*_dev(nm))
+    return cfg, res, c, p, om, gm, ev, nm
+
+
+def _check_density(om, p, c, pts, S_gpu):
+    B, _ = om.basis(p, pts)
+    S_o, _ = om.density(p, pts)
+    mag = np.sum(np.sum(np.abs(c[None, :, None] * B), axis=1) ** 2, axis=1)
+    kappa = mag / S_o
+    err = np.abs(S_gpu.astype(np.float64) - S_o)
+    good = kappa <= 100
+    assert np.all(err[good] <= 1e-5 * S_o[good]), np.max(err[good] / S_o[good])
+    assert np.all(err[~good] <= 1e-5 * mag[~good])
+    return good.mean(), np.max(err[good] / S_o[good])
+
+
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+@pytest.mark.parametrize("data", ["peaked", "uniform"])
+def test_density_parity(A, name, data):
+    n = 20_003  # several tiles and a ragged tail (n % 4 = 3)
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, name, n, 4097, data=data)
+    S = gm.eval_density(p, 0).cpu().numpy()
+    frac, worst = _check_density(om, p, c, ev, S)
+    assert frac > 0.9  # most events are well conditioned; the rest are held to the absolute bound
+    Sn = gm.eval_density(p, 1).cpu().numpy()
+    _check_density(om, p, c, nm, Sn)
+
+
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+def test_nll_terms_parity(A, name):
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, name, 50_001, 200_003)
+    nll_o, _, aux, rc = om.nll(p, ev, nm)
+    assert rc == 0
+    t = gm.eval_terms(p)
+    assert t[3] == len(ev[0])
+    assert t[1] == pytest.approx(aux[1], abs=1e-9 * abs(aux[1]) + 1e-9)   # sum ln(p q), FP64 once
+    assert t[2] == pytest.approx(aux[2], rel=1e-9)                         # I
+    assert abs(t[0] - aux[0]) < 5e-4                                       # sum ln S
+    nll = gm.eval_nll(p)
+    assert abs(nll - nll_o) < 1e-3
+
+
+@pytest.mark.parametrize("name", ["tiny", "kstar10_z"])
+def test_nll_grad_parity_model_data(A, name):
+    n = 20_000 if name == "tiny" else 8_000
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, name, n, 40_000, data="model")
+    nll_o, g_o, _, rc = om.nll(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    assert abs(nll - nll_o) < 1e-3
+    tol = np.maximum(1e-6 * np.abs(g_o), 1e-5 * np.max(np.abs(g_o)))
+    assert np.all(np.abs(g - g_o) <= tol), np.max(np.abs(g - g_o) / np.max(np.abs(g_o)))
+    nll2 = gm.eval_nll(p)
+    assert nll2 == nll  # same reduction order on both paths' data sum
+
+
+def test_grad_parity_all_masses_floating(A):
+    """Gradient with respect to every coupling, mass and width (10 K* + Z)."""
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, "kstar10_z", 6_000, 30_000, data="peaked",
+                                            float_names=[r.name for r in W.CONFIGS["kstar10_z"].resonances])
+    nll_o, g_o, _, rc = om.nll(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    assert abs(nll - nll_o) < 1e-3
+    rel = np.abs(g - g_o) / np.maximum(np.abs(g_o), 1e-3 * np.max(np.abs(g_o)))
+    print("all M/G floating: max rel %.3e, max |dg|/|g|inf %.3e" % (np.max(rel), np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
+    assert np.max(rel) < 1e-3, np.argmax(rel)
+    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+
+
+def test_deterministic(A):
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, "kstar10_z", 30_001, 50_000)
+    a = gm.eval_nll_grad(p)
+    b = gm.eval_nll_grad(p)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_host_pointer_inputs(A):
+    """set_events accepts host arrays too (the library copies them)."""
+    cfg = W.CONFIGS["tiny"]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    ev = W.peaked_points(1001, 3, res)
+    nm = W.uniform_points(2003, 4)
+    g1 = A.Model(res)
+    g1.set_events(*ev)
+    g1.set_norm_points(*nm)
+    g2 = A.Model(res)
+    g2.set_events(*_dev(ev))
+    g2.set_norm_points(*_dev(nm))
+    assert g1.eval_nll(p) == g2.eval_nll(p)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_tiny_and_ragged_sizes(A, n):
+    cfg = W.CONFIGS["kstar10_z"]
+    res = cfg.resonances
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c)
+    ev = W.peaked_points(n, 17, res)
+    nm = W.uniform_points(n + 2, 18)
+    om = O.Model(res)
+    gm = A.Model(res)
+    gm.set_events(*_dev(ev))
+    gm.set_norm_points(*_dev(nm))
+    nll_o, g_o, _, _ = om.nll(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    assert abs(nll - nll_o) < 1e-4
+    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    _check_density(om, p, c, ev, gm.eval_density(p, 0).cpu().numpy())
+
+
+def test_errors(A):
+    cfg = W.CONFIGS["tiny"]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    gm = A.Model(res)
+    with pytest.raises(A.Amp4dError) as e:
+        gm.eval_nll_grad(p)
+    assert e.value.code == A.AMP4D_ERR_STATE
+    ev = [a.copy() for a in W.uniform_points(100, 1)]
+    ev[0][37] = 3.0  # outside the m_Kpi box
+    with pytest.raises(A.Amp4dError) as e:
+        gm.set_events(*_dev(ev))
+    assert e.value.code == A.AMP4D_ERR_INPUT and "37" in str(e.value)
+    ev[0][37] = 1.0
+    ev[3][12] = float("nan")
+    with pytest.raises(A.Amp4dError) as e:
+        gm.set_events(*_dev(ev))
+    assert e.value.code == A.AMP4D_ERR_INPUT and "12" in str(e.value)
+    ev[3][12] = 0.5
+    gm.set_events(*_dev(ev))
+    gm.set_norm_points(*_dev(W.uniform_points(100, 2)))
+    # all couplings zero: S = 0 everywhere -> domain error, NLL = +inf
+    nll = gm.eval_nll(np.zeros_like(p))
+    assert math.isinf(nll) and nll > 0
+    # a good evaluation still works afterwards
+    assert math.isfinite(gm.eval_nll(p))
+    with pytest.raises(ValueError):
+        gm.eval_nll(p[:-1])
+    bad = p.copy()
+    bad[3] = float("inf")
+    with pytest.raises(A.Amp4dError) as e:
+        gm.eval_nll_grad(bad)
+    assert e.value.code == A.AMP4D_ERR_ARG
+
+
+def test_bad_model_arguments(A):
+    r = W.CONFIGS["tiny"].resonances
+    with pytest.raises(A.Amp4dError):
+        A.Model(r, box=(0.5, 2.0))      # below the K pi threshold
+    zz = [W.Z4430, W.Z4200, W.Z4430]
+    with pytest.raises(A.Amp4dError):
+        A.Model(r + zz)                  # at most two Z
+
+
+def test_nll_grad_1e6_model_events(A):
+    """The accuracy target at 10^6 events: 10 K* + Z(4430), data drawn from the model by the
+    oracle's accept-reject generator, 4e6 uniform normalisation points."""
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, "kstar10_z", 1_000_000, 4_000_000, data="model")
+    nll_o, g_o, aux, rc = om.nll(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    t = gm.eval_terms(p)
+    print("dNLL %.3e  d(sum lnS) %.3e  dI/I %.3e" % (nll - nll_o, t[0] - aux[0], t[2] / aux[2] - 1))
+    assert abs(nll - nll_o) <= 1e-3
+    tol = np.maximum(1e-6 * np.abs(g_o), 1e-5 * np.max(np.abs(g_o)))
+    print("1e6: max |dg|/|g|inf = %.3e" % (np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
+    assert np.all(np.abs(g - g_o) <= tol), np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))
+
+
+def test_nll_full_size_large_workload(A):
+    """Full benchmark workload (5e6 events, 2^24 points, Z mass/width floating) in the
+    launch configuration the benchmark times: NLL and gradient against the oracle."""
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, "large", 5_000_000, 1 << 24)
+    nll_o, g_o, aux, rc = om.nll(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    print("large: dNLL %.3e (NLL %.6f)" % (nll - nll_o, nll_o))
+    assert abs(nll - nll_o) <= 5e-3
+    print("large: max |dg|/|g|inf = %.3e" % (np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
+    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))

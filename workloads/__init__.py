@@ -196,18 +196,38 @@ def float_mg_values(res_list, float_names):
     return vals
 
 
+M_END = M_B - M_PSI   # kinematic limit of m_Kpi (the box edge lies 4e-5 GeV above it)
+
+
+def _f32_in(x, lo, hi):
+    """Round to FP32 and keep the result inside [lo, hi] (as double)."""
+    f = np.asarray(x, dtype=np.float32)
+    lo32 = np.float32(lo)
+    if float(lo32) < lo:
+        lo32 = np.nextafter(lo32, np.float32(np.inf))
+    hi32 = np.float32(hi)
+    if float(hi32) > hi:
+        hi32 = np.nextafter(hi32, np.float32(-np.inf))
+    return np.ascontiguousarray(np.clip(f, lo32, hi32))
+
+
+def _angles(u1, u2, u3):
+    return (_f32_in(2.0 * u1 - 1.0, -1.0, 1.0), _f32_in(2.0 * u2 - 1.0, -1.0, 1.0),
+            _f32_in(math.pi * (2.0 * u3 - 1.0), -math.pi, math.pi))
+
+
 def uniform_points(n, seed, box=(M_LO, M_HI)):
-    """n points uniform in the observable box, FP32 SoA (m, cK, cpsi, phi)."""
+    """n points uniform in the observable box, FP32 SoA (m, cK, cpsi, phi).
+
+    Use box=(M_LO, M_END) for data-like events: beyond M_END the phase space
+    vanishes and no real event can lie there."""
     rng = np.random.Generator(np.random.Philox(seed))
     u = rng.random((4, n))
-    m = box[0] + (box[1] - box[0]) * u[0]
-    cK = 2.0 * u[1] - 1.0
-    cpsi = 2.0 * u[2] - 1.0
-    phi = math.pi * (2.0 * u[3] - 1.0)
-    return tuple(np.ascontiguousarray(a, dtype=np.float32) for a in (m, cK, cpsi, phi))
+    m = _f32_in(box[0] + (box[1] - box[0]) * u[0], box[0], box[1])
+    return (m,) + _angles(u[1], u[2], u[3])
 
 
-def peaked_points(n, seed, res_list, f_uniform=0.3, box=(M_LO, M_HI)):
+def peaked_points(n, seed, res_list, f_uniform=0.3, box=(M_LO, M_END)):
     """n points whose m_Kpi has Cauchy peaks at the K* poles (truncated to the box).
 
     A fraction f_uniform is uniform in m; the rest picks a K* in res_list with
@@ -228,11 +248,9 @@ def peaked_points(n, seed, res_list, f_uniform=0.3, box=(M_LO, M_HI)):
         a = math.atan((box[0] - r.M) / hw)
         b = math.atan((box[1] - r.M) / hw)
         m[sel] = r.M + hw * np.tan(a + (b - a) * u[0][sel])
-    m = np.clip(m, box[0], box[1])
-    cK = 2.0 * u[1] - 1.0
-    cpsi = 2.0 * u[2] - 1.0
-    phi = math.pi * (2.0 * u[3] - 1.0)
-    return tuple(np.ascontiguousarray(a, dtype=np.float32) for a in (m, cK, cpsi, phi))
+    # strictly below the kinematic edge, where p q > 0
+    m = _f32_in(m, box[0], min(box[1], M_END - 1e-6))
+    return (m,) + _angles(u[1], u[2], u[3])
 
 
 def perturbed_start(c, seed=7, amount=0.1):
