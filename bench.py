@@ -211,6 +211,22 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def _timed(model, A, pts_dev, out_dev, what, K, W0, stream):
+    """K back-to-back enqueued evaluations timed with CUDA events on the stream."""
+    import torch
+    for k in range(W0):
+        model.enqueue_eval(what, pts_dev[k % len(pts_dev)], out_dev[k % len(out_dev)])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(K):
+        model.enqueue_eval(what, pts_dev[(W0 + k) % len(pts_dev)], out_dev[(W0 + k) % len(out_dev)])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,6 +235,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large", choices=sorted(W.CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain GPU path")
     ap.add_argument("--cpu-frac", type=int, default=16)
     ap.add_argument("--ref-frac", type=int, default=64)
     args = ap.parse_args()
@@ -241,23 +258,29 @@ def main():
     stream = torch.cuda.current_stream()
 
     res, params, ev, nm = make_workload(cfg, rank)
-    model = A.Model(res, float_names=cfg.float_mg)
-    P = model.n_params
     dev = [torch.from_numpy(a).cuda() for a in ev]
     devn = [torch.from_numpy(a).cuda() for a in nm]
+    # Optimised form: adjoint gradient + tensor-core Gram normalisation (masses and
+    # widths fixed); falls back to per-point normalisation when some float.
+    model = A.Model(res, float_names=cfg.float_mg, path=A.AMP4D_PATH_CACHED)
+    P = model.n_params
     model.set_events(*dev)
     model.set_norm_points(*devn)
-    del dev, devn
+    gram_ms = None
+    if not cfg.float_mg:
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        model.build_gram(params)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gram_ms = g0.elapsed_time(g1)
 
     K, Wm = args.steps, args.warmup
     pts = np.stack([step_params(params, k, model.n_cols) for k in range(K + Wm)])
     p_dev = torch.from_numpy(pts).cuda()
     out_dev = torch.zeros((K + Wm, 6 + P), dtype=torch.float64, device="cuda")
-    for k in range(Wm):
-        model.enqueue_eval(A.AMP4D_EVAL_NLL_GRAD, p_dev[k], out_dev[k])
-    torch.cuda.synchronize()
 
-    # device-timed region
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -265,14 +288,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     model.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(K):
-        model.enqueue_eval(A.AMP4D_EVAL_NLL_GRAD, p_dev[Wm + k], out_dev[Wm + k])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = _timed(model, A, p_dev, out_dev, A.AMP4D_EVAL_NLL_GRAD, K, Wm, stream)
     prof_ms, prof_n = model.profile_read()
     model.profile(False)
     if dist:
@@ -281,12 +297,10 @@ def main():
         ms = float(t.item())
         dist.barrier()
     outs = out_dev.cpu().numpy()
-    assert np.all(outs[Wm:, 5] == 0), "evaluation reported a domain error"
+    assert np.all(outs[:, 5] == 0), "evaluation reported an error status"
 
     # end-to-end through the synchronous user call (host params in, host NLL + grad out)
     host_pts = torch.from_numpy(pts).pin_memory().numpy()
-    if dist:
-        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(K):
@@ -300,11 +314,9 @@ def main():
 
     value = world * K / (ms / 1e3)
     e2e_value = world * K / t_e2e
-    # dominant kernel among the timed phases
-    names = ["table", "data_grad_kernel", "norm_grad_kernel", "reductions"]
-    tot = prof_ms.sum()
+    names = ["table", "data_kernel", "norm_kernel", "finish"]
     dom = int(np.argmax(prof_ms))
-    units = cfg.n_events if dom == 1 else cfg.n_norm
+    units = cfg.n_events if dom in (1, 0, 3) else cfg.n_norm
     fpe = flops_per_event(res, cfg.float_mg, grad=True)
     mean_launch_s = prof_ms[dom] / max(1, prof_n[dom]) / 1e3
     achieved = fpe * units / mean_launch_s / 1e12
@@ -314,27 +326,54 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "n_events": cfg.n_events, "n_norm": cfg.n_norm,
                    "resonances": len(res), "params": P, "float_mg": cfg.float_mg,
-                   "path": "plain recompute + adjoint gradient, uniform normalisation points",
+                   "path": ("adjoint gradient + tensor-core Gram normalisation" if not cfg.float_mg
+                            else "adjoint gradient, per-point normalisation"),
                    "l2": "inputs larger than L2 (%.2f GB of event records)" % (
                        (15 * cfg.n_events + 16 * cfg.n_norm) * 4 / 1e9)},
         "events_per_s": value * cfg.n_events,
-        "points_per_s": value * (cfg.n_events + cfg.n_norm),
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * P,
                 "d2h_bytes_per_step": 8 * (6 + P)},
-        "gpu_launches": int(6 * K),
+        "gpu_launches": int(K * (4 if not cfg.float_mg else 6)),
         "phases_ms_per_step": {n: float(prof_ms[i] / max(1, prof_n[i])) for i, n in enumerate(names)},
-        "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": None, "flops_per_event": fpe, "units_per_launch": units,
+        "roofline": {"bound": "alu", "kernel": "k_grad data (adjoint, %s)" % names[dom],
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "flops_per_event": fpe, "units_per_launch": units,
                      "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (of nominal)"},
         "clocks": clk,
         "nll_last": float(outs[-1, 0]),
     }
+    if gram_ms is not None:
+        rows = 2 * cfg.n_norm
+        mma_flops = rows / 16 * 2 * 128 * (256 + 64) * 16
+        line["gram"] = {"build_ms": gram_ms, "rows": rows,
+                        "tensor_tflops_executed": mma_flops / (gram_ms / 1e3) / 1e12,
+                        "bf16_peak_measured": _peaks().get("bf16_tflops"),
+                        "note": "one-time per mass/width setting; colmax pass + tcgen05 kernel + reduce"}
+    model.close()
+    del model
+    if not args.no_plain:
+        # The plain GPU path on the same data: every amplitude recomputed per evaluation,
+        # uniform normalisation points summed per evaluation, adjoint gradient; and the
+        # GooFit-like form with the gradient by central differences (2P + 1 NLL evaluations).
+        plain = A.Model(res, float_names=cfg.float_mg, path=A.AMP4D_PATH_PLAIN)
+        plain.set_events(*dev)
+        plain.set_norm_points(*devn)
+        Kp = max(3, K // 2)
+        ms_g = _timed(plain, A, p_dev, out_dev, A.AMP4D_EVAL_NLL_GRAD, Kp, 2, stream)
+        ms_n = _timed(plain, A, p_dev, out_dev, A.AMP4D_EVAL_NLL, Kp, 2, stream)
+        nll_rate = Kp / (ms_n / 1e3)
+        line["plain_gpu"] = {
+            "adjoint_evals_per_s": world * Kp / (ms_g / 1e3),
+            "nll_evals_per_s": world * nll_rate,
+            "fd_grad_evals_per_s": world * nll_rate / (2 * P + 1),
+            "note": "same GPU, recompute per evaluation, uniform points; fd = 2P+1 NLL evaluations"}
+        line["speedup_vs_plain_fd"] = value / line["plain_gpu"]["fd_grad_evals_per_s"]
+        plain.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(cfg, args.cpu_frac)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    model.close()
     if dist:
         dist.destroy_process_group()
 

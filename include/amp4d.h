@@ -171,6 +171,36 @@ amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *para
                                 void *stream);
 
 /*
+ * Normalisation Gram matrix G = sum_n w_n sum_xi x x^T of the real 2K-vectors
+ * x = (Re B_0, Im B_0, Re B_1, ...) over the normalisation points (State-of-
+ * the-art section: numerical normalisation; Eq. 5, 12 for B), so that
+ * I = (V / N_mc) (u^T G u + v^T G v) with u = (Re c_0, -Im c_0, ...),
+ * v = (Im c_0, Re c_0, ...).  Built on the tensor cores (tcgen05) from exact
+ * BF16 digit slices of fixed-point columns, accumulated in INT64.
+ * amp4d_build_gram builds it for the masses and widths in params (host; the
+ * couplings are not used) and synchronises; K <= 32 columns.  Models created
+ * with AMP4D_PATH_CACHED and no floated masses/widths build it on their first
+ * evaluation (which then synchronises) and use it for I and dI/dc thereafter;
+ * amp4d_set_norm_points discards it.  amp4d_get_gram copies G (host, 2K x 2K,
+ * row-major) back.  Errors: STATE (no points / no Gram), ARG (K > 32),
+ * TIMEOUT (a bounded device wait expired), CUDA.
+ */
+amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *stream);
+amp4d_status amp4d_get_gram(amp4d_model *model, double *G, void *stream);
+
+/*
+ * Self-test of the tensor-core Gram accumulation on this GPU: X holds n points x
+ * 2 rows x 64 columns of fixed-point values (int32, |X| <= 2^30, host or device
+ * memory, caller-owned).  G_int (host, 64 x 64 int64) receives the kernel's
+ * integer Gram: per 512-point chunk, the digit products P_ab of the base-256
+ * digits d1..d4 of X (d1 = round(X / 2^24), ...) combined as
+ * sum_ab 2^(8 (5 - a - b)) P_ab, the a = b = 4 term dropped and the 2^-8 and
+ * 2^-16 terms rounded half up, summed over chunks.  A caller can reproduce it
+ * exactly in integer arithmetic.  Uses the current device; synchronises.
+ */
+amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, void *stream);
+
+/*
  * Device timing of evaluations (CUDA events around each phase, on the
  * evaluation's stream).  amp4d_profile_read waits for the recorded work and
  * returns, then clears, the summed milliseconds and counts of the phases

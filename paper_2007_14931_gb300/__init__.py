@@ -45,6 +45,16 @@ _ERRNAMES = {AMP4D_ERR_ARG: "ARG", AMP4D_ERR_CUDA: "CUDA", AMP4D_ERR_OOM: "OOM",
              AMP4D_ERR_TIMEOUT: "TIMEOUT", AMP4D_ERR_STATE: "STATE"}
 
 
+def gram_selftest(X, stream=None):
+    """Integer Gram of fixed-point values X (int32 array [n, 2, 64]) on the tensor cores."""
+    X = np.ascontiguousarray(X, dtype=np.int32)
+    out = np.zeros((64, 64), dtype=np.int64)
+    rc = amp4d_gram_selftest(X.ctypes.data, X.shape[0], out.ctypes.data, _stream_ptr(stream))
+    if rc != 0:
+        raise Amp4dError(rc, amp4d_last_error(None).decode())
+    return out
+
+
 class amp4d_particle_masses(C.Structure):
     _fields_ = [("mB", C.c_double), ("mpsi", C.c_double), ("mK", C.c_double), ("mpi", C.c_double)]
 
@@ -82,13 +92,17 @@ amp4d_eval_nll_grad = _proto("amp4d_eval_nll_grad", C.c_int, [_vp, _d, _d, _d, _
 amp4d_eval_terms = _proto("amp4d_eval_terms", C.c_int, [_vp, _d, _d, _vp])
 amp4d_eval_density = _proto("amp4d_eval_density", C.c_int, [_vp, _d, C.c_int, _vp, _vp])
 amp4d_enqueue_eval = _proto("amp4d_enqueue_eval", C.c_int, [_vp, C.c_int, _vp, _vp, _vp])
+amp4d_build_gram = _proto("amp4d_build_gram", C.c_int, [_vp, _d, _vp])
+amp4d_get_gram = _proto("amp4d_get_gram", C.c_int, [_vp, _d, _vp])
+amp4d_gram_selftest = _proto("amp4d_gram_selftest", C.c_int, [_vp, C.c_int64, _vp, _vp])
 amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
 amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
 
 EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "amp4d_num_columns",
             "amp4d_num_params", "amp4d_set_events", "amp4d_set_norm_points", "amp4d_eval_nll",
             "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
-            "amp4d_profile_enable", "amp4d_profile_read"]
+            "amp4d_profile_enable", "amp4d_profile_read", "amp4d_build_gram", "amp4d_get_gram",
+            "amp4d_gram_selftest"]
 
 
 class Amp4dError(RuntimeError):
@@ -202,6 +216,16 @@ class Model:
         """Enqueue an evaluation with device parameters/outputs (torch float64 tensors)."""
         self._check(amp4d_enqueue_eval(self.h, what, params_dev.data_ptr(), out_dev.data_ptr(),
                                        _stream_ptr(stream)))
+
+    def build_gram(self, params, stream=None):
+        p = self._params(params)
+        self._check(amp4d_build_gram(self.h, p.ctypes.data_as(_d), _stream_ptr(stream)))
+
+    def get_gram(self, stream=None):
+        d = 2 * self.n_cols
+        G = np.zeros((d, d))
+        self._check(amp4d_get_gram(self.h, G.ctypes.data_as(_d), _stream_ptr(stream)))
+        return G
 
     def profile(self, on=True):
         self._check(amp4d_profile_enable(self.h, 1 if on else 0))

@@ -68,6 +68,14 @@ struct amp4d_model {
     unsigned long long *d_bad = nullptr;
     double *d_tmp = nullptr;     // scratch for set-up reductions
     size_t tmp_cap = 0;
+    // normalisation Gram matrix (cached path)
+    double *d_G = nullptr;           // 2K x 2K, folded basis
+    long long *d_gram_part = nullptr;
+    unsigned *d_colmax = nullptr;
+    float *d_gscale = nullptr;
+    int *d_gram_err = nullptr;
+    int gram_grid = 0;
+    bool gram_valid = false;
     std::string err;
 };
 
@@ -244,6 +252,55 @@ cudaEvent_t prof_event(amp4d_model *m)
     return e;
 }
 
+bool use_gram(const amp4d_model *m)
+{
+    return m->path == AMP4D_PATH_CACHED && m->n_float == 0 && 2 * m->n_col <= 64;
+}
+
+// Build the normalisation Gram matrix for the masses and widths in d_params
+// (synchronous; checks the kernel's bounded-wait flag).
+amp4d_status build_gram(amp4d_model *model, cudaStream_t st)
+{
+    if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "no normalisation points");
+    if (2 * model->n_col > 64) return fail(model, AMP4D_ERR_ARG, "Gram matrix supports at most 32 columns");
+    if (!model->d_G) {
+        model->gram_grid = model->nsm;
+        CK(cudaMalloc(&model->d_G, 64 * 64 * sizeof(double)));
+        CK(cudaMalloc(&model->d_gram_part, (size_t)model->gram_grid * 4096 * sizeof(long long)));
+        CK(cudaMalloc(&model->d_colmax, 64 * sizeof(unsigned)));
+        CK(cudaMalloc(&model->d_gscale, 64 * sizeof(float)));
+        CK(cudaMalloc(&model->d_gram_err, sizeof(int)));
+    }
+    CK(cudaMemsetAsync(model->d_gram_err, 0, sizeof(int), st));
+    CK(launch_build_table(model->d_static, model->d_params, model->d_md, model->d_pscale,
+                          model->d_status, st));
+    GramArgs g{};
+    g.rec = model->mc.rec;
+    g.npad = model->mc.npad;
+    g.n = model->mc.n;
+    g.wrec = model->mc.wrec;
+    g.md = model->d_md;
+    g.colmax = model->d_colmax;
+    g.gscale = model->d_gscale;
+    g.part = model->d_gram_part;
+    g.err = model->d_gram_err;
+    g.G = model->d_G;
+    g.dim = 2 * model->n_col;
+    g.grid_colmax = model->nsm * 4;
+    const int64_t nchunks = (model->mc.n + gram_chunk_points() - 1) / gram_chunk_points();
+    g.grid_tc = (int)std::max<int64_t>(1, std::min<int64_t>(model->gram_grid, nchunks));
+    g.nk_max = model->nk_max;
+    g.nz = model->nZ;
+    g.stream = st;
+    CK(launch_gram(g));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, model->d_gram_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) return fail(model, AMP4D_ERR_TIMEOUT, "Gram kernel: a bounded wait expired");
+    model->gram_valid = true;
+    return AMP4D_OK;
+}
+
 // Enqueue one evaluation on stream st (no synchronisation).
 amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params, double *d_out,
                      cudaStream_t st)
@@ -261,6 +318,32 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
     CK(launch_build_table(model->d_static, d_params, model->d_md, model->d_pscale, model->d_status, st));
     CK(mark());
     double *rd = model->d_red, *rn = model->d_red + model->nslot;
+    if (use_gram(model)) {
+        if (!model->gram_valid) {
+            amp4d_status rc = build_gram(model, st);
+            if (rc) return rc;
+        }
+        const double von = model->mc.volume / (double)model->mc.n;
+        if (with_grad) {
+            LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_grad);
+            CK(launch_grad(ad, false));
+            CK(mark());
+            CK(mark());
+            CK(launch_reduce_cols(model->ev.part, model->ev.grid_grad, model->nslot, rd, st));
+        } else {
+            LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
+            CK(launch_eval(ad, 0));
+            CK(mark());
+            CK(mark());
+            CK(launch_reduce_cols(model->ev.part, model->ev.grid_eval, 1, rd, st));
+        }
+        CK(launch_finish_gram(rd, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
+                              model->n_param, (double)model->ev.n, model->ev.lnpq, von, d_params,
+                              model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st));
+        CK(mark());
+        if (model->prof_on) model->prof_pending.push_back(marks);
+        return AMP4D_OK;
+    }
     if (with_grad) {
         LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_grad);
         CK(launch_grad(ad, false));
@@ -451,6 +534,11 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
     if (model->d_status) cudaFree(model->d_status);
     if (model->d_bad) cudaFree(model->d_bad);
     if (model->d_tmp) cudaFree(model->d_tmp);
+    if (model->d_G) cudaFree(model->d_G);
+    if (model->d_gram_part) cudaFree(model->d_gram_part);
+    if (model->d_colmax) cudaFree(model->d_colmax);
+    if (model->d_gscale) cudaFree(model->d_gscale);
+    if (model->d_gram_err) cudaFree(model->d_gram_err);
     delete model;
     return AMP4D_OK;
 }
@@ -476,6 +564,7 @@ amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const flo
 {
     if (!model) return AMP4D_ERR_ARG;
     if (!(volume > 0.0)) return fail(model, AMP4D_ERR_ARG, "volume must be > 0");
+    model->gram_valid = false;
     amp4d_status rc = load_set(model, model->mc, m, cK, cpsi, phi, w, n, true, (cudaStream_t)stream);
     if (rc == AMP4D_OK) model->mc.volume = volume;
     return rc;
@@ -548,6 +637,67 @@ amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *para
         return model ? fail(model, AMP4D_ERR_ARG, "bad enqueue arguments") : AMP4D_ERR_ARG;
     CK(cudaSetDevice(model->device));
     return enqueue(model, what == AMP4D_EVAL_NLL_GRAD, params, out, (cudaStream_t)stream);
+}
+
+amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *stream)
+{
+    if (!model) return AMP4D_ERR_ARG;
+    amp4d_status rc = check_params(model, params);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(model->device));
+    std::memcpy(model->h_params, params, model->n_param * sizeof(double));
+    CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    return build_gram(model, st);
+}
+
+amp4d_status amp4d_get_gram(amp4d_model *model, double *G, void *stream)
+{
+    if (!model || !G) return AMP4D_ERR_ARG;
+    if (!model->gram_valid) return fail(model, AMP4D_ERR_STATE, "no Gram matrix built");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dim = 2 * model->n_col;
+    std::vector<double> gp(dim * dim), ps(model->n_param);
+    CK(cudaMemcpyAsync(gp.data(), model->d_G, dim * dim * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ps.data(), model->d_pscale, model->n_param * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) G[i * dim + j] = gp[i * dim + j] * ps[i] * ps[j];
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, void *stream)
+{
+    amp4d_model *model = nullptr;
+    if (!X || !G_int || n < 1) return fail(nullptr, AMP4D_ERR_ARG, "bad self-test arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t nchunks = (n + gram_chunk_points() - 1) / gram_chunk_points();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, nchunks));
+    int *d_X = nullptr, *d_err = nullptr;
+    long long *d_part = nullptr, *d_out = nullptr;
+    ModelDev *d_md = nullptr;
+    cudaError_t e = cudaMalloc(&d_X, (size_t)n * 128 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_part, (size_t)grid * 4096 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, 4096 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_md, sizeof(ModelDev));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_md, 0, sizeof(ModelDev), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_X, X, (size_t)n * 128 * sizeof(int), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = launch_gram_selftest(d_X, n, d_md, d_part, grid, d_err, d_out, st);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G_int, d_out, 4096 * sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_X); cudaFree(d_part); cudaFree(d_out); cudaFree(d_err); cudaFree(d_md);
+    if (e != cudaSuccess) return fail(nullptr, AMP4D_ERR_CUDA, std::string("gram self-test: ") + cudaGetErrorString(e));
+    if (err) return fail(nullptr, AMP4D_ERR_TIMEOUT, "gram self-test: a bounded wait expired");
+    return AMP4D_OK;
 }
 
 amp4d_status amp4d_profile_enable(amp4d_model *model, int on)

@@ -95,6 +95,16 @@ __device__ __forceinline__ void cfma_conj(float2 &a, float2 b, float2 c)
     a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
     a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
 }
+// a += (hi + lo) * c: the low part enters the same FMA chain as the high-part
+// product, so the constant hi + lo is applied before each term is rounded (an
+// addition after the rounding would drop it whenever it is below half an ulp).
+__device__ __forceinline__ void cfma2(float2 &a, float2 hi, float2 lo, float2 c)
+{
+    const float tx = fmaf(hi.x, c.x, fmaf(-hi.y, c.y, fmaf(lo.x, c.x, -lo.y * c.y)));
+    const float ty = fmaf(hi.x, c.y, fmaf(hi.y, c.x, fmaf(lo.x, c.y, lo.y * c.x)));
+    a.x += tx;
+    a.y += ty;
+}
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
@@ -180,10 +190,10 @@ __device__ __forceinline__ LineOut lineshape(const ResDev &r, float mrun, float 
     const float num = rs * ipow(p, r.LB) * ipow(q * invm, r.LR);
     const float X = ipow(q, 2 * r.LR + 1) * invm * __frcp_rn(PR);
     const float MG = fmaf(r.Ghi, X, r.Glo * X);
-    // M^2 - m^2 = (M - m)(M + m) with M = hi + lo: (hi - m) is exact near the pole.
+    // M^2 - m^2 = (M - m)(M + m) with M = hi + lo: (hi - m) is exact near the pole,
+    // and lo enters (M + m) inside the final FMA.
     const float dm = (r.Mhi - mrun) + r.Mlo;
-    const float sm = (r.Mhi + mrun) + r.Mlo;
-    const float Dr = dm * sm;
+    const float Dr = fmaf(dm, r.Mhi + mrun, dm * r.Mlo);
     const float den = __frcp_rn(fmaf(Dr, Dr, MG * MG));
     LineOut o;
     o.invD = make_float2(Dr * den, MG * den);          // 1/(Dr - i MG) = (Dr + i MG)/|D|^2

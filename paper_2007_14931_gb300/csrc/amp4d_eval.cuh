@@ -70,17 +70,11 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
             ev.invDK[k] = L.invD;
             ev.MGK[k] = L.MG;
             if (rs.J == 0) {
-                const float2 x = cscale(L.A, d0);
-                cfma(u[1], md.c[rs.col], x);
-                cfma(u[1], md.cl[rs.col], x);
+                cfma2(u[1], md.c[rs.col], md.cl[rs.col], cscale(L.A, d0));
             } else {
-                const float2 xm = cscale(L.A, -d1), x0 = cscale(L.A, d0), xp = cscale(L.A, d1);
-                cfma(u[0], md.c[rs.col], xm);
-                cfma(u[0], md.cl[rs.col], xm);
-                cfma(u[1], md.c[rs.col + 1], x0);
-                cfma(u[1], md.cl[rs.col + 1], x0);
-                cfma(u[2], md.c[rs.col + 2], xp);
-                cfma(u[2], md.cl[rs.col + 2], xp);
+                cfma2(u[0], md.c[rs.col], md.cl[rs.col], cscale(L.A, -d1));
+                cfma2(u[1], md.c[rs.col + 1], md.cl[rs.col + 1], cscale(L.A, d0));
+                cfma2(u[2], md.c[rs.col + 2], md.cl[rs.col + 2], cscale(L.A, d1));
             }
         } else {
             ev.AK[k] = make_float2(0.f, 0.f);
@@ -127,14 +121,8 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                 ev.Om0[z][x] = o0;
                 ev.Om1[z][x] = o1;
                 float2 s = make_float2(0.f, 0.f);
-                if (rs.zcol0 >= 0) {
-                    cfma(s, md.c[rs.zcol0], o0);
-                    cfma(s, md.cl[rs.zcol0], o0);
-                }
-                if (rs.zcol1 >= 0) {
-                    cfma(s, md.c[rs.zcol1], o1);
-                    cfma(s, md.cl[rs.zcol1], o1);
-                }
+                if (rs.zcol0 >= 0) cfma2(s, md.c[rs.zcol0], md.cl[rs.zcol0], o0);
+                if (rs.zcol1 >= 0) cfma2(s, md.c[rs.zcol1], md.cl[rs.zcol1], o1);
                 cfma(ev.a[x], L.A, s);
             }
         }
@@ -283,10 +271,11 @@ __device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, flo
                                                  float MG, float2 &dAdM, float2 &dAdG)
 {
     // dD/dM = 2M - i MG dln(MG)/dM
-    const float2 dD = make_float2(2.0f * rs.Mhi + 2.0f * rs.Mlo,
-                                  -fmaf(MG, rs.dGhi, MG * rs.dGlo));
-    const float2 r = cmul(dD, invD);                 // (dD/dM) / D
-    const float2 f = make_float2((rs.dNhi - r.x) + rs.dNlo, -r.y);
+    const float2 dD = make_float2(2.0f * rs.Mhi, -fmaf(MG, rs.dGhi, MG * rs.dGlo));
+    // (dD/dM) / D, with the 2 M_lo part of dD/dM inside the FMA
+    const float2 r = make_float2(fmaf(dD.x, invD.x, fmaf(-dD.y, invD.y, 2.0f * rs.Mlo * invD.x)),
+                                 fmaf(dD.x, invD.y, fmaf(dD.y, invD.x, 2.0f * rs.Mlo * invD.y)));
+    const float2 f = make_float2(rs.dNhi - r.x + rs.dNlo, -r.y);
     dAdM = cmul(A, f);
     // dA/dG0 = -A (dD/dG0)/D = i A (MG / G0) / D
     const float2 g = cmul(A, invD);

@@ -78,6 +78,68 @@ __global__ void k_finish(const double *__restrict__ rd, const double *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// NLL and gradient with the normalisation from the Gram matrix G (cached path):
+// with the folded couplings c'_k = kappa_k c_k, u = (Re c', -Im c'), v = (Im c',
+// Re c') interleaved, I = vol_over_n (u^T G u + v^T G v) and
+// dI/dRe c'_k = 2 vol_over_n ((Gu)_2k + (Gv)_2k+1),
+// dI/dIm c'_k = 2 vol_over_n ((Gv)_2k - (Gu)_2k+1).  One block; fixed order.
+// ---------------------------------------------------------------------------
+__global__ void k_finish_gram(const double *__restrict__ rd, const int *__restrict__ slot_param,
+                              const double *__restrict__ pscale, int nslot, int ncol, int nparam,
+                              double n_events, double lnpq, double vol_over_n,
+                              const double *__restrict__ params, const double *__restrict__ G,
+                              const unsigned *__restrict__ status, double *__restrict__ out,
+                              int with_grad)
+{
+    __shared__ double u[96], v[96], Gu[96], Gv[96];
+    __shared__ double Ish;
+    const int dim = 2 * ncol, t = threadIdx.x;
+    for (int k = t; k < ncol; k += blockDim.x) {
+        const double re = pscale[2 * k] * params[2 * k], im = pscale[2 * k] * params[2 * k + 1];
+        u[2 * k] = re; u[2 * k + 1] = -im;
+        v[2 * k] = im; v[2 * k + 1] = re;
+    }
+    __syncthreads();
+    for (int i = t; i < dim; i += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < dim; ++j) {
+            a += G[i * dim + j] * u[j];
+            b += G[i * dim + j] * v[j];
+        }
+        Gu[i] = a;
+        Gv[i] = b;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double q = 0.0;
+        for (int i = 0; i < dim; ++i) q += u[i] * Gu[i] + v[i] * Gv[i];
+        const double I = vol_over_n * q;
+        unsigned st = *status;
+        const double nll = -2.0 * (rd[0] + lnpq - n_events * log(I));
+        if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
+        out[0] = st ? INFINITY : nll;
+        out[1] = rd[0];
+        out[2] = lnpq;
+        out[3] = I;
+        out[4] = n_events;
+        out[5] = (double)st;
+        Ish = st ? 0.0 : I;
+    }
+    __syncthreads();
+    if (!with_grad) return;
+    const double I = Ish;
+    for (int p = t; p < nparam; p += blockDim.x) out[6 + p] = 0.0;
+    __syncthreads();
+    for (int s = 1 + t; s < nslot; s += blockDim.x) {
+        const int p = slot_param[s];
+        if (p < 0 || p >= dim || I == 0.0) continue;
+        const int k = p >> 1;
+        const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1]) : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
+        out[6 + p] = -2.0 * pscale[p] * (rd[s] - n_events * vol_over_n * dq / I);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Per-evaluation resonance table (Eq. 2-3 constants at the current M, G0), one
 // thread per resonance in FP64:
 //   p0 = p(M), q0 = q(M) two-body momenta at the pole, KB = P_LB(r^2 p0^2),
@@ -282,6 +344,16 @@ cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_pa
 {
     k_finish<<<1, 128, 0, s>>>(rd, rn, slot_param, pscale, nslot, nparam, n_events, lnpq,
                                vol_over_n, status, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
+                               int nslot, int ncol, int nparam, double n_events, double lnpq,
+                               double vol_over_n, const double *params, const double *G,
+                               const unsigned *status, double *out, int with_grad, cudaStream_t s)
+{
+    k_finish_gram<<<1, 128, 0, s>>>(rd, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
+                                    vol_over_n, params, G, status, out, with_grad);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,31 @@ cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_pa
 
 cudaError_t launch_build_table(const ModelStatic *st, const double *params, ModelDev *md,
                                double *pscale, unsigned *status, cudaStream_t s);
+cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
+                               int nslot, int ncol, int nparam, double n_events, double lnpq,
+                               double vol_over_n, const double *params, const double *G,
+                               const unsigned *status, double *out, int with_grad, cudaStream_t s);
+
+// Normalisation Gram matrix (amp4d_gram.cu).
+struct GramArgs {
+    const float *rec;        // normalisation-point records (weights in record wrec)
+    int64_t npad, n;
+    int wrec;
+    const ModelDev *md;
+    unsigned *colmax;        // 64 (scratch)
+    float *gscale;           // 64 (scratch): fixed-point scale per real column
+    long long *part;         // grid_tc x 4096 INT64 partials (scratch)
+    int *err;                // set to 1 if a bounded wait expired
+    double *G;               // dim x dim output
+    int dim;                 // 2 K
+    int grid_colmax, grid_tc;
+    int nk_max, nz;
+    cudaStream_t stream;
+};
+cudaError_t launch_gram(const GramArgs &a);
+cudaError_t launch_gram_selftest(const int *synth, int64_t n, const ModelDev *md, long long *part,
+                                 int grid, int *err, long long *out, cudaStream_t st);
+int gram_chunk_points();
 
 // One-time FP64 preparation of an event set (amp4d_prepare.cu).
 struct PrepArgs {

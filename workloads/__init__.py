@@ -153,8 +153,9 @@ CONFIGS = {
     "kstar10_z": Config("kstar10_z", 2, ALL_KSTAR + ["Z(4430)"], 1_000_000, 4_000_000,
                         float_mg=ALL_KSTAR + ["Z(4430)"]),
     "learned": Config("learned", 3, ALL_KSTAR + ["Z(4430)"], 1 << 20, 1 << 20),
-    "large": Config("large", 4, ALL_KSTAR + ["Z(4430)"], 5_000_000, 1 << 24,
-                    float_mg=["Z(4430)"]),
+    "large": Config("large", 4, ALL_KSTAR + ["Z(4430)"], 5_000_000, 1 << 24),
+    "large_float_z": Config("large_float_z", 5, ALL_KSTAR + ["Z(4430)"], 5_000_000, 1 << 24,
+                            float_mg=["Z(4430)"]),
 }
 
 
