@@ -68,6 +68,14 @@ def lib():
             L.or_generate.argtypes = [C.c_void_p, _d, C.c_uint64, C.c_int64, C.c_int64,
                                       C.c_int64, _f, _f, _f, _f, _d]
             L.or_philox4x32_10.argtypes = [_u32, _u32, _u32]
+            L.or_mlp_num_params.restype = C.c_int
+            L.or_mlp_forward.argtypes = [_d, _d, C.c_int64, _d]
+            L.or_mlp_loss_grad.argtypes = [_d, _d, C.c_int64, _d, C.c_int64, _d, _d]
+            L.or_adam_step.argtypes = [_d, _d, _d, _d, C.c_int64, C.c_double, C.c_double,
+                                       C.c_double, C.c_double, C.c_int64]
+            L.or_grid_sample.argtypes = [_d, _i, C.c_double, C.c_uint64, C.c_int64, C.c_double,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         _f, _f, _f, _f, _d, C.POINTER(C.c_int64)]
             L.or_num_threads.restype = C.c_int
             L.or_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -246,3 +254,50 @@ class Model:
         if used < 0:
             raise RuntimeError("oracle generator: candidate budget exhausted")
         return tuple(outs), used, fmax.value
+
+
+# ---------------------------------------------------------------- learned proposal
+def mlp_num_params():
+    return lib().or_mlp_num_params()
+
+
+def mlp_forward(theta, x):
+    """g(x) of the proposal MLP (x: n x 4 in [-1, 1]^4)."""
+    th = _f64(theta)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    g = np.zeros(len(x))
+    lib().or_mlp_forward(_pd(th), _pd(x), len(x), _pd(g))
+    return g
+
+
+def mlp_loss_grad(theta, xd, xu):
+    """KL objective -mean ln g(xd) + ln(16 mean g(xu)) and its gradient."""
+    th = _f64(theta)
+    xd = np.ascontiguousarray(xd, dtype=np.float64).reshape(-1, 4)
+    xu = np.ascontiguousarray(xu, dtype=np.float64).reshape(-1, 4)
+    g = np.zeros(mlp_num_params())
+    loss = C.c_double()
+    lib().or_mlp_loss_grad(_pd(th), _pd(xd), len(xd), _pd(xu), len(xu), C.byref(loss), _pd(g))
+    return loss.value, g
+
+
+def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam update of theta, m, v (float64 arrays)."""
+    lib().or_adam_step(_pd(theta), _pd(m), _pd(v), _pd(_f64(grad)), len(theta), lr, beta1, beta2,
+                       eps, int(t))
+
+
+def grid_sample(gc, nb, alpha, seed, n, masses=None, box=None):
+    """Samples of the grid proposal: (m, cK, cpsi, phi) FP32, weights p q / density, cells."""
+    import workloads as W
+    masses = W.PARTICLE_MASSES if masses is None else masses
+    box = (W.M_LO, W.M_HI) if box is None else box
+    gcv = _f64(gc)
+    nbv = np.ascontiguousarray(nb, dtype=np.int32)
+    outs = [np.zeros(n, np.float32) for _ in range(4)]
+    w = np.zeros(n)
+    cell = np.zeros(n, np.int64)
+    lib().or_grid_sample(_pd(gcv), _pi(nbv), float(alpha), int(seed), int(n), box[0], box[1],
+                         *masses, *(_pf(a) for a in outs), _pd(w),
+                         cell.ctypes.data_as(C.POINTER(C.c_int64)))
+    return tuple(outs), w, cell

@@ -875,3 +875,180 @@ void or_set_num_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned importance-sampling proposal (normalisation integral):      */
+/* MLP 4 -> 64 -> 64 -> 1 with tanh hidden units and softplus output,  */
+/* a density g over x in [-1, 1]^4 trained on events drawn from the    */
+/* model; then a piecewise-constant proposal on a cell grid mixed with */
+/* the uniform density.                                                 */
+/* Parameter layout: W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3. */
+/* ------------------------------------------------------------------ */
+#define MLP_H 64
+#define MLP_NP (MLP_H * 4 + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1)
+
+int or_mlp_num_params(void) { return MLP_NP; }
+
+static double softplus_d(double o) { return o > 30.0 ? o : log1p(exp(o)); }
+static double sigmoid_d(double o) { return 1.0 / (1.0 + exp(-o)); }
+
+typedef struct {
+    double h1[MLP_H], h2[MLP_H], o, g;
+} mlp_act;
+
+static void mlp_fwd(const double *th, const double *x, mlp_act *a)
+{
+    const double *W1 = th, *b1 = W1 + MLP_H * 4, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b1[i];
+        for (int j = 0; j < 4; ++j) z += W1[i * 4 + j] * x[j];
+        a->h1[i] = tanh(z);
+    }
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b2[i];
+        for (int j = 0; j < MLP_H; ++j) z += W2[i * MLP_H + j] * a->h1[j];
+        a->h2[i] = tanh(z);
+    }
+    double o = b3[0];
+    for (int j = 0; j < MLP_H; ++j) o += W3[j] * a->h2[j];
+    a->o = o;
+    a->g = softplus_d(o);
+}
+
+/* g(x) for n points (x: n x 4, row-major). */
+void or_mlp_forward(const double *th, const double *x, int64_t n, double *g)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n; ++e) {
+        mlp_act a;
+        mlp_fwd(th, x + 4 * e, &a);
+        g[e] = a.g;
+    }
+}
+
+/* Accumulate coef * dg/dtheta of one point into grad. */
+static void mlp_bwd_add(const double *th, const double *x, const mlp_act *a, double coef, double *grad)
+{
+    const double *W2 = th + MLP_H * 4 + MLP_H, *W3 = W2 + MLP_H * MLP_H + MLP_H;
+    double *gW1 = grad, *gb1 = gW1 + MLP_H * 4, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H;
+    double *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_H;
+    const double dO = coef * sigmoid_d(a->o);
+    double d2[MLP_H], d1[MLP_H];
+    for (int j = 0; j < MLP_H; ++j) {
+        gW3[j] += dO * a->h2[j];
+        d2[j] = dO * W3[j] * (1.0 - a->h2[j] * a->h2[j]);
+    }
+    gb3[0] += dO;
+    for (int j = 0; j < MLP_H; ++j) d1[j] = 0.0;
+    for (int i = 0; i < MLP_H; ++i) {
+        gb2[i] += d2[i];
+        for (int j = 0; j < MLP_H; ++j) {
+            gW2[i * MLP_H + j] += d2[i] * a->h1[j];
+            d1[j] += W2[i * MLP_H + j] * d2[i];
+        }
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        d1[j] *= 1.0 - a->h1[j] * a->h1[j];
+        gb1[j] += d1[j];
+        for (int k = 0; k < 4; ++k) gW1[j * 4 + k] += d1[j] * x[k];
+    }
+}
+
+/*
+ * KL objective of a density model g over the box X = [-1, 1]^4 (volume 16):
+ *   L = -(1/nd) sum_d ln g(x_d) + ln( 16 (1/nu) sum_u g(x_u) ),
+ * x_d drawn from the target, x_u uniform.  grad = dL/dtheta.  Serial (order fixed).
+ */
+int or_mlp_loss_grad(const double *th, const double *xd, int64_t nd, const double *xu, int64_t nu,
+                     double *loss, double *grad)
+{
+    memset(grad, 0, MLP_NP * sizeof(double));
+    double *gu = (double *)calloc(MLP_NP, sizeof(double));
+    double sl = 0.0, su = 0.0;
+    for (int64_t e = 0; e < nd; ++e) {
+        mlp_act a;
+        mlp_fwd(th, xd + 4 * e, &a);
+        sl += log(a.g);
+        mlp_bwd_add(th, xd + 4 * e, &a, -1.0 / ((double)nd * a.g), grad);
+    }
+    for (int64_t e = 0; e < nu; ++e) {
+        mlp_act a;
+        mlp_fwd(th, xu + 4 * e, &a);
+        su += a.g;
+        mlp_bwd_add(th, xu + 4 * e, &a, 1.0, gu);
+    }
+    for (int i = 0; i < MLP_NP; ++i) grad[i] += gu[i] / su;
+    free(gu);
+    *loss = -sl / (double)nd + log(16.0 * su / (double)nu);
+    return 0;
+}
+
+/* One Adam step (Kingma & Ba, 2015) at step number t >= 1. */
+void or_adam_step(double *th, double *m, double *v, const double *grad, int64_t n, double lr,
+                  double beta1, double beta2, double eps, int64_t t)
+{
+    const double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+        th[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}
+
+/*
+ * Grid proposal: cells nb[0] x nb[1] x nb[2] x nb[3] over x in [-1, 1]^4 (cell index
+ * ((i0 nb1 + i1) nb2 + i2) nb3 + i3), cell values gc >= 0.  Cell probabilities
+ * P_c = alpha / ncell + (1 - alpha) gc_c / sum gc, CDF in double (serial sums).
+ * Sample i: Philox(counter (i, 0, i >> 32, 0), key seed) gives u0 (cell by CDF
+ * search: first c with cdf_c > u0) and u1..u3, a second call (counter (i, 1, ...))
+ * gives u4; x_d = lo_d + width_d u_{d+1}.  Map to (m, cK, cpsi, phi):
+ * m = m_lo + (m_hi - m_lo)(x0 + 1)/2, cK = x1, cpsi = x2, phi = pi x3, rounded to FP32.
+ * Density in the observables q = P_c ncell / 16 * 2 / ((m_hi - m_lo) pi); weight
+ * w = p q_ps / q with p q_ps the phase-space density at the FP32 point.
+ */
+void or_grid_sample(const double *gc, const int *nb, double alpha, uint64_t seed, int64_t n,
+                    double m_lo, double m_hi, double mB, double mpsi, double mK, double mpi,
+                    float *om, float *ocK, float *ocpsi, float *ophi, double *w, int64_t *cell)
+{
+    const int64_t nc = (int64_t)nb[0] * nb[1] * nb[2] * nb[3];
+    double sg = 0.0;
+    for (int64_t c = 0; c < nc; ++c) sg += gc[c];
+    double *cdf = (double *)malloc(nc * sizeof(double));
+    double acc = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+        acc += alpha / (double)nc + (1.0 - alpha) * gc[c] / sg;
+        cdf[c] = acc;
+    }
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t c0[4] = {(uint32_t)i, 0u, (uint32_t)((uint64_t)i >> 32), 0u}, r0[4];
+        uint32_t c1[4] = {(uint32_t)i, 1u, (uint32_t)((uint64_t)i >> 32), 0u}, r1[4];
+        or_philox4x32_10(c0, key, r0);
+        or_philox4x32_10(c1, key, r1);
+        const double u0 = u01(r0[0]) * cdf[nc - 1];
+        int64_t lo = 0, hi = nc - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (cdf[mid] > u0) hi = mid;
+            else lo = mid + 1;
+        }
+        const int64_t c = lo;
+        int64_t rem = c;
+        int idx[4];
+        for (int d = 3; d >= 0; --d) { idx[d] = (int)(rem % nb[d]); rem /= nb[d]; }
+        const double us[4] = {u01(r0[1]), u01(r0[2]), u01(r0[3]), u01(r1[0])};
+        double x[4];
+        for (int d = 0; d < 4; ++d) x[d] = -1.0 + 2.0 * (idx[d] + us[d]) / nb[d];
+        const float fm = (float)(m_lo + (m_hi - m_lo) * 0.5 * (x[0] + 1.0));
+        const float fcK = (float)x[1], fcpsi = (float)x[2], fphi = (float)(M_PI * x[3]);
+        const double Pc = cdf[c] - (c > 0 ? cdf[c - 1] : 0.0);
+        const double q = Pc / cdf[nc - 1] * (double)nc / 16.0 * 2.0 / ((m_hi - m_lo) * M_PI);
+        const double p = or_breakup(mB, fm, mpsi), qq = or_breakup(fm, mK, mpi);
+        om[i] = fm; ocK[i] = fcK; ocpsi[i] = fcpsi; ophi[i] = fphi;
+        w[i] = p * qq / q;
+        cell[i] = c;
+    }
+    free(cdf);
+}
