@@ -84,6 +84,15 @@ typedef struct {
 
 typedef struct amp4d_model amp4d_model;
 
+/* Training and grid settings of the learned normalisation proposal. */
+typedef struct {
+    int nb[4];      /* grid cells per dimension of x = (m, cK, cpsi, phi) mapped to [-1, 1]^4 */
+    double alpha;   /* weight of the uniform density in the defensive mixture, (0, 1]       */
+    int64_t steps;  /* Adam steps                                                          */
+    int batch;      /* data rows and uniform rows per step                                 */
+    double lr;      /* Adam learning rate (beta1 0.9, beta2 0.999, eps 1e-8)               */
+} amp4d_mlp_cfg;
+
 /*
  * Create a model from a resonance list (Eq. 2-5, 10-12).  n_res in
  * [1, AMP4D_MAX_RES], at most 2 Z resonances, J <= 4, LB, LR <= 4.  The box is
@@ -199,6 +208,58 @@ amp4d_status amp4d_get_gram(amp4d_model *model, double *G, void *stream);
  * exactly in integer arithmetic.  Uses the current device; synchronises.
  */
 amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, void *stream);
+
+/*
+ * Pseudo-data from the model at params (Fit validation section: events generated
+ * by MC from the fit model): accept-reject over the uniform box with density
+ * S p q.  Candidate i uses Philox4x32-10 (counter (i, 0, i >> 32, 0), key seed) for
+ * its coordinates and counter (i, 1, ...) for the acceptance uniform; f_max is
+ * 1.5 x the largest S p q of 2^20 scan candidates (stream 2) and doubles, with a
+ * restart, if a candidate exceeds it.  Accepted events keep candidate order.
+ * m, cK, cpsi, phi: DEVICE outputs of n floats (caller-owned).  Synchronises.
+ * Errors: ARG, DOMAIN (S p q vanishes or the candidate budget is exhausted), CUDA, OOM.
+ */
+amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t seed, int64_t n,
+                            float *m, float *cK, float *cpsi, float *phi, void *stream);
+
+/*
+ * Learned importance-sampling proposal for the normalisation integral: an MLP
+ * 4 -> 64 -> 64 -> 1 (tanh, softplus output g >= 0; BF16 weights with an FP32
+ * master copy, FP32 accumulation) over x in [-1, 1]^4 (x0 = 2 (m - m_lo)/(m_hi -
+ * m_lo) - 1, x1 = cK, x2 = cpsi, x3 = phi / pi), trained by Adam on the KL
+ * objective -mean_data ln g + ln(16 mean_uniform g) with data rows drawn from
+ * the given events (DEVICE SoA, n each; e.g. from amp4d_generate at the fit's
+ * start point) and uniform rows, Philox-keyed by seed.  Then g at the centres of
+ * the cfg->nb grid and the FP64 CDF of P_c = alpha / ncell + (1 - alpha) g_c / sum g
+ * are kept in the model.  *loss (host, nullable) receives the last batch loss.
+ * amp4d_proposal_sample draws n points (DEVICE outputs) cell by CDF, uniformly in
+ * the cell, with weights w = p q / q(Phi), so that I = (1/n) sum w S: pass them
+ * to amp4d_set_norm_points with volume 1.  Both synchronise.
+ */
+amp4d_status amp4d_proposal_train(amp4d_model *model, const float *m, const float *cK,
+                                  const float *cpsi, const float *phi, int64_t n,
+                                  const amp4d_mlp_cfg *cfg, uint64_t seed, double *loss, void *stream);
+amp4d_status amp4d_proposal_sample(amp4d_model *model, int64_t n, uint64_t seed, float *m, float *cK,
+                                   float *cpsi, float *phi, float *w, void *stream);
+
+/*
+ * The proposal pieces on explicit inputs (model-free; for validation):
+ * amp4d_mlp_forward: g(x) for n rows x (DEVICE n x 4) with the FP32 weights theta
+ *   (4545 floats, host or device; rounded to BF16 inside) into g (DEVICE, n).
+ * amp4d_mlp_loss_grad: the KL objective on data rows xd (DEVICE nd x 4) and
+ *   uniform rows xu (DEVICE nu x 4): out (host, 4546 doubles) = gradient, loss.
+ * amp4d_grid_sample: the sampler on given cell values gcell (host or device,
+ *   nb[0] nb[1] nb[2] nb[3] floats); outputs DEVICE, cell (DEVICE int64, nullable)
+ *   receives the sampled cell index.  Philox streams as amp4d_proposal_sample.
+ * All synchronise.
+ */
+amp4d_status amp4d_mlp_forward(const float *theta, const float *x, int64_t n, float *g, void *stream);
+amp4d_status amp4d_mlp_loss_grad(const float *theta, const float *xd, int64_t nd, const float *xu,
+                                 int64_t nu, double *out, void *stream);
+amp4d_status amp4d_grid_sample(const float *gcell, const int *nb, double alpha, uint64_t seed,
+                               int64_t n, double m_lo, double m_hi, const amp4d_particle_masses *masses,
+                               float *m, float *cK, float *cpsi, float *phi, float *w, int64_t *cell,
+                               void *stream);
 
 /*
  * Device timing of evaluations (CUDA events around each phase, on the

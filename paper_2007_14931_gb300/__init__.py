@@ -55,6 +55,49 @@ def gram_selftest(X, stream=None):
     return out
 
 
+def _check_global(rc):
+    if rc != 0:
+        raise Amp4dError(rc, amp4d_last_error(None).decode())
+
+
+def mlp_forward(theta, x, stream=None):
+    """g(x) of the proposal MLP for FP32 weights theta (4545, host) and rows x (torch cuda n x 4)."""
+    import torch
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    x = x.contiguous()
+    g = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check_global(amp4d_mlp_forward(th.ctypes.data, x.data_ptr(), x.shape[0], g.data_ptr(),
+                                    _stream_ptr(stream)))
+    return g
+
+
+def mlp_loss_grad(theta, xd, xu, stream=None):
+    """(loss, gradient) of the KL objective on rows xd (data) and xu (uniform), torch cuda."""
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    out = np.zeros(MLP_NUM_PARAMS + 1)
+    xd, xu = xd.contiguous(), xu.contiguous()
+    _check_global(amp4d_mlp_loss_grad(th.ctypes.data, xd.data_ptr(), xd.shape[0], xu.data_ptr(),
+                                      xu.shape[0], out.ctypes.data_as(_d), _stream_ptr(stream)))
+    return out[-1], out[:-1]
+
+
+def grid_sample(gcell, nb, alpha, seed, n, masses=None, box=None, stream=None):
+    """Sampler of the grid proposal on given cell values: (m, cK, cpsi, phi), w, cell (torch cuda)."""
+    import torch
+    import workloads as W
+    masses = W.PARTICLE_MASSES if masses is None else masses
+    box = (W.M_LO, W.M_HI) if box is None else box
+    gc = np.ascontiguousarray(gcell, dtype=np.float32)
+    nbv = (C.c_int * 4)(*nb)
+    outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(5)]
+    cell = torch.empty(n, dtype=torch.int64, device="cuda")
+    pm = amp4d_particle_masses(*masses)
+    _check_global(amp4d_grid_sample(gc.ctypes.data, nbv, float(alpha), int(seed), int(n), box[0], box[1],
+                                    C.byref(pm), *(o.data_ptr() for o in outs), cell.data_ptr(),
+                                    _stream_ptr(stream)))
+    return tuple(outs[:4]), outs[4], cell
+
+
 class amp4d_particle_masses(C.Structure):
     _fields_ = [("mB", C.c_double), ("mpsi", C.c_double), ("mK", C.c_double), ("mpi", C.c_double)]
 
@@ -63,6 +106,11 @@ class amp4d_resonance(C.Structure):
     _fields_ = [("chain", C.c_int), ("J", C.c_int), ("P", C.c_int), ("LB", C.c_int),
                 ("LR", C.c_int), ("M", C.c_double), ("G0", C.c_double), ("r", C.c_double),
                 ("float_mg", C.c_int)]
+
+
+class amp4d_mlp_cfg(C.Structure):
+    _fields_ = [("nb", C.c_int * 4), ("alpha", C.c_double), ("steps", C.c_int64),
+                ("batch", C.c_int), ("lr", C.c_double)]
 
 
 _vp = C.c_void_p
@@ -95,6 +143,17 @@ amp4d_enqueue_eval = _proto("amp4d_enqueue_eval", C.c_int, [_vp, C.c_int, _vp, _
 amp4d_build_gram = _proto("amp4d_build_gram", C.c_int, [_vp, _d, _vp])
 amp4d_get_gram = _proto("amp4d_get_gram", C.c_int, [_vp, _d, _vp])
 amp4d_gram_selftest = _proto("amp4d_gram_selftest", C.c_int, [_vp, C.c_int64, _vp, _vp])
+amp4d_generate = _proto("amp4d_generate", C.c_int, [_vp, _d, C.c_uint64, C.c_int64, _vp, _vp, _vp, _vp, _vp])
+amp4d_proposal_train = _proto("amp4d_proposal_train", C.c_int,
+                              [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.POINTER(amp4d_mlp_cfg), C.c_uint64,
+                               _d, _vp])
+amp4d_proposal_sample = _proto("amp4d_proposal_sample", C.c_int,
+                               [_vp, C.c_int64, C.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp])
+amp4d_mlp_forward = _proto("amp4d_mlp_forward", C.c_int, [_vp, _vp, C.c_int64, _vp, _vp])
+amp4d_mlp_loss_grad = _proto("amp4d_mlp_loss_grad", C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _d, _vp])
+amp4d_grid_sample = _proto("amp4d_grid_sample", C.c_int,
+                           [_vp, _vp, C.c_double, C.c_uint64, C.c_int64, C.c_double, C.c_double,
+                            C.POINTER(amp4d_particle_masses), _vp, _vp, _vp, _vp, _vp, _vp, _vp])
 amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
 amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
 
@@ -102,7 +161,10 @@ EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "am
             "amp4d_num_params", "amp4d_set_events", "amp4d_set_norm_points", "amp4d_eval_nll",
             "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
             "amp4d_profile_enable", "amp4d_profile_read", "amp4d_build_gram", "amp4d_get_gram",
-            "amp4d_gram_selftest"]
+            "amp4d_gram_selftest", "amp4d_generate", "amp4d_proposal_train",
+            "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample"]
+
+MLP_NUM_PARAMS = 4545
 
 
 class Amp4dError(RuntimeError):
@@ -226,6 +288,32 @@ class Model:
         G = np.zeros((d, d))
         self._check(amp4d_get_gram(self.h, G.ctypes.data_as(_d), _stream_ptr(stream)))
         return G
+
+    def generate(self, params, n, seed, stream=None):
+        """n events drawn from the model at params (device float32 tensors m, cK, cpsi, phi)."""
+        import torch
+        p = self._params(params)
+        outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(4)]
+        self._check(amp4d_generate(self.h, p.ctypes.data_as(_d), int(seed), int(n),
+                                   *(o.data_ptr() for o in outs), _stream_ptr(stream)))
+        return tuple(outs)
+
+    def proposal_train(self, events, nb=(128, 16, 16, 32), alpha=0.1, steps=1500, batch=4096,
+                       lr=2e-3, seed=1, stream=None):
+        cfg = amp4d_mlp_cfg((C.c_int * 4)(*nb), alpha, steps, batch, lr)
+        loss = C.c_double()
+        ev = [e.contiguous() for e in events]
+        self._check(amp4d_proposal_train(self.h, *(e.data_ptr() for e in ev), ev[0].shape[0],
+                                         C.byref(cfg), int(seed), C.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def proposal_sample(self, n, seed, stream=None):
+        """n importance-sampled points and weights w = p q / q (device float32 tensors)."""
+        import torch
+        outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(5)]
+        self._check(amp4d_proposal_sample(self.h, int(n), int(seed), *(o.data_ptr() for o in outs),
+                                          _stream_ptr(stream)))
+        return tuple(outs[:4]), outs[4]
 
     def profile(self, on=True):
         self._check(amp4d_profile_enable(self.h, 1 if on else 0))

@@ -76,6 +76,13 @@ struct amp4d_model {
     int *d_gram_err = nullptr;
     int gram_grid = 0;
     bool gram_valid = false;
+    // learned proposal
+    float *d_th = nullptr, *d_am = nullptr, *d_av = nullptr;   // FP32 master weights, Adam moments
+    __nv_bfloat16 *d_wb = nullptr;                              // BF16 weights
+    float *d_gcell = nullptr;
+    double *d_cdf = nullptr;
+    int nb[4] = {0, 0, 0, 0};
+    bool proposal_ready = false;
     std::string err;
 };
 
@@ -539,6 +546,9 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
     if (model->d_colmax) cudaFree(model->d_colmax);
     if (model->d_gscale) cudaFree(model->d_gscale);
     if (model->d_gram_err) cudaFree(model->d_gram_err);
+    for (void *ptr : {(void *)model->d_th, (void *)model->d_am, (void *)model->d_av, (void *)model->d_wb,
+                      (void *)model->d_gcell, (void *)model->d_cdf})
+        if (ptr) cudaFree(ptr);
     delete model;
     return AMP4D_OK;
 }
@@ -697,6 +707,262 @@ amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, 
     cudaFree(d_X); cudaFree(d_part); cudaFree(d_out); cudaFree(d_err); cudaFree(d_md);
     if (e != cudaSuccess) return fail(nullptr, AMP4D_ERR_CUDA, std::string("gram self-test: ") + cudaGetErrorString(e));
     if (err) return fail(nullptr, AMP4D_ERR_TIMEOUT, "gram self-test: a bounded wait expired");
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t seed, int64_t n,
+                            float *m, float *cK, float *cpsi, float *phi, void *stream)
+{
+    if (!model || !m || !cK || !cpsi || !phi || n < 1) return AMP4D_ERR_ARG;
+    amp4d_status rc = check_params(model, params);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(model->device));
+    std::memcpy(model->h_params, params, model->n_param * sizeof(double));
+    CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CK(launch_build_table(model->d_static, model->d_params, model->d_md, model->d_pscale,
+                          model->d_status, st));
+    const int64_t B = 1 << 22, nscan = 1 << 20;
+    const int nrec = model->nZ > 0 ? REC_NZ : REC_NK;
+    const int nblk = (int)((B + gen_tile() - 1) / gen_tile());
+    EventSet g;
+    g.npad = B;
+    g.nrec = nrec;
+    float *S = nullptr, *ua = nullptr;
+    unsigned *cnt = nullptr, *flag = nullptr;
+    unsigned long long *off = nullptr;
+    double *part = nullptr;
+    auto cleanup = [&]() {
+        for (void *ptr : {(void *)g.rec, (void *)S, (void *)ua, (void *)cnt, (void *)flag, (void *)off,
+                          (void *)part})
+            if (ptr) cudaFree(ptr);
+    };
+#define CKG(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            cleanup();                                                                     \
+            return fail(model, e_ == cudaErrorMemoryAllocation ? AMP4D_ERR_OOM : AMP4D_ERR_CUDA, \
+                        std::string("generate: ") + cudaGetErrorString(e_));              \
+        }                                                                                  \
+    } while (0)
+    CKG(cudaMalloc(&g.rec, (size_t)nrec * B * sizeof(float)));
+    CKG(cudaMalloc(&S, B * sizeof(float)));
+    CKG(cudaMalloc(&ua, B * sizeof(float)));
+    CKG(cudaMalloc(&cnt, nblk * sizeof(unsigned)));
+    CKG(cudaMalloc(&flag, 2 * sizeof(unsigned)));
+    CKG(cudaMalloc(&off, (nblk + 1) * sizeof(unsigned long long)));
+    CKG(cudaMalloc(&part, (size_t)model->nsm * 8 * sizeof(double)));
+    // Evaluate S p q at count candidates of the given Philox stream starting at first.
+    auto eval_batch = [&](uint64_t first, int64_t count, uint32_t sid, float *uacc) -> cudaError_t {
+        cudaError_t e = launch_gen_candidates(g.rec, B, count, first, sid, seed, model->m_lo,
+                                              model->m_hi, uacc, st);
+        if (e != cudaSuccess) return e;
+        PrepArgs a{};
+        a.rec = g.rec; a.npad = B; a.n = count; a.has_z = model->nZ > 0; a.wrec = -1; a.have_w = 0;
+        a.mB = model->mass.mB; a.mpsi = model->mass.mpsi; a.mK = model->mass.mK; a.mpi = model->mass.mpi;
+        a.m_lo = model->m_lo; a.m_hi = model->m_hi;
+        a.grid = model->nsm * 8; a.part_lnpq = nullptr; a.bad = model->d_bad; a.stream = st;
+        e = launch_prepare(a);
+        if (e != cudaSuccess) return e;
+        g.n = count;
+        LaunchArgs la = args_for(model, g, part, S, st, model->nsm * 8);
+        return launch_eval(la, 2);
+    };
+    // f_max: 1.5 x the largest S p q over the scan candidates (stream 2)
+    CKG(cudaMemsetAsync(flag, 0, 2 * sizeof(unsigned), st));
+    CKG(eval_batch(0, nscan, 2u, nullptr));
+    CKG(launch_gen_accept(g.rec, B, nscan, S, nullptr, 0.0, cnt, flag, flag + 1, st));
+    unsigned fbits = 0;
+    CKG(cudaMemcpyAsync(&fbits, flag + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CKG(cudaStreamSynchronize(st));
+    float fm32;
+    std::memcpy(&fm32, &fbits, sizeof fm32);
+    double fmax = 1.5 * (double)fm32;
+    if (!(fmax > 0.0)) { cleanup(); return fail(model, AMP4D_ERR_DOMAIN, "generate: S p q vanishes"); }
+    int64_t got = 0;
+    uint64_t first = 0;
+    int restarts = 0;
+    while (got < n) {
+        if (first > (uint64_t)(4000 * n + (1 << 24))) { cleanup(); return fail(model, AMP4D_ERR_DOMAIN, "generate: candidate budget exhausted"); }
+        CKG(cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
+        CKG(eval_batch(first, B, 0u, ua));
+        CKG(launch_gen_accept(g.rec, B, B, S, ua, fmax, cnt, flag, nullptr, st));
+        unsigned over = 0;
+        CKG(cudaMemcpyAsync(&over, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CKG(cudaStreamSynchronize(st));
+        if (over) {
+            fmax *= 2.0;
+            got = 0;
+            first = 0;
+            if (++restarts > 20) { cleanup(); return fail(model, AMP4D_ERR_DOMAIN, "generate: f_max did not settle"); }
+            continue;
+        }
+        CKG(launch_gen_scatter(g.rec, B, B, S, ua, fmax, cnt, off, got, n, m, cK, cpsi, phi, st));
+        unsigned long long tot = 0;
+        CKG(cudaMemcpyAsync(&tot, off + nblk, sizeof(tot), cudaMemcpyDeviceToHost, st));
+        CKG(cudaStreamSynchronize(st));
+        got += (int64_t)tot;
+        first += B;
+    }
+#undef CKG
+    cleanup();
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_proposal_train(amp4d_model *model, const float *m, const float *cK,
+                                  const float *cpsi, const float *phi, int64_t n,
+                                  const amp4d_mlp_cfg *cfg, uint64_t seed, double *loss, void *stream)
+{
+    if (!model || !m || !cK || !cpsi || !phi || !cfg || n < 1 || cfg->batch < 1 || cfg->steps < 1)
+        return AMP4D_ERR_ARG;
+    for (int d = 0; d < 4; ++d)
+        if (cfg->nb[d] < 1) return fail(model, AMP4D_ERR_ARG, "grid cells must be >= 1");
+    if (!(cfg->alpha > 0.0 && cfg->alpha <= 1.0)) return fail(model, AMP4D_ERR_ARG, "alpha in (0, 1]");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(model->device));
+    const int P = mlp_num_params();
+    if (!model->d_th) {
+        CK(cudaMalloc(&model->d_th, P * sizeof(float)));
+        CK(cudaMalloc(&model->d_am, P * sizeof(float)));
+        CK(cudaMalloc(&model->d_av, P * sizeof(float)));
+        CK(cudaMalloc(&model->d_wb, P * sizeof(__nv_bfloat16)));
+    }
+    std::vector<float> th(P);
+    mlp_init_params(th.data(), seed);
+    CK(cudaMemcpyAsync(model->d_th, th.data(), P * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(model->d_am, 0, P * sizeof(float), st));
+    CK(cudaMemsetAsync(model->d_av, 0, P * sizeof(float), st));
+    CK(launch_to_bf16(model->d_th, model->d_wb, st));
+    const int64_t nd = cfg->batch, nu = cfg->batch;
+    float *xd = nullptr, *xu = nullptr, *part = nullptr;
+    double *gout = nullptr;
+    auto cleanup = [&]() {
+        for (void *ptr : {(void *)xd, (void *)xu, (void *)part, (void *)gout})
+            if (ptr) cudaFree(ptr);
+    };
+    cudaError_t e = cudaMalloc(&xd, nd * 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&xu, nu * 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)mlp_grad_blocks(nd, nu) * (P + 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&gout, (P + 1) * sizeof(double));
+    for (int64_t t = 1; e == cudaSuccess && t <= cfg->steps; ++t) {
+        e = launch_mlp_batch(m, cK, cpsi, phi, n, nd, nu, seed, (uint64_t)t, model->m_lo, model->m_hi,
+                             xd, xu, st);
+        if (e == cudaSuccess) e = launch_mlp_grad(model->d_wb, xd, nd, xu, nu, part, gout, st);
+        if (e == cudaSuccess)
+            e = launch_adam(model->d_th, model->d_am, model->d_av, gout, (float)cfg->lr, 0.9f, 0.999f,
+                            1e-8f, t, model->d_wb, st);
+    }
+    double L = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&L, gout + P, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return fail(model, AMP4D_ERR_CUDA, std::string("proposal_train: ") + cudaGetErrorString(e));
+    if (loss) *loss = L;
+    // Grid of cell-centre values and the FP64 CDF of the defensive mixture.
+    const int64_t nc = (int64_t)cfg->nb[0] * cfg->nb[1] * cfg->nb[2] * cfg->nb[3];
+    if (model->d_gcell) { cudaFree(model->d_gcell); model->d_gcell = nullptr; }
+    if (model->d_cdf) { cudaFree(model->d_cdf); model->d_cdf = nullptr; }
+    CK(cudaMalloc(&model->d_gcell, nc * sizeof(float)));
+    CK(cudaMalloc(&model->d_cdf, nc * sizeof(double)));
+    {
+        amp4d_status rc = ensure_tmp(model, 2 * cdf_scratch(nc) + 2);
+        if (rc) return rc;
+    }
+    for (int d = 0; d < 4; ++d) model->nb[d] = cfg->nb[d];
+    CK(launch_mlp_grid(model->d_wb, model->nb, model->d_gcell, st));
+    CK(launch_grid_cdf(model->d_gcell, nc, cfg->alpha, model->d_tmp, model->d_cdf, st));
+    CK(cudaStreamSynchronize(st));
+    model->proposal_ready = true;
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_proposal_sample(amp4d_model *model, int64_t n, uint64_t seed, float *m, float *cK,
+                                   float *cpsi, float *phi, float *w, void *stream)
+{
+    if (!model || !m || !cK || !cpsi || !phi || !w || n < 1) return AMP4D_ERR_ARG;
+    if (!model->proposal_ready) return fail(model, AMP4D_ERR_STATE, "proposal not trained");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(model->device));
+    CK(launch_grid_sample(model->d_cdf, model->nb, seed, n, model->m_lo, model->m_hi, model->mass.mB,
+                          model->mass.mpsi, model->mass.mK, model->mass.mpi, m, cK, cpsi, phi, w,
+                          nullptr, st));
+    CK(cudaStreamSynchronize(st));
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_mlp_forward(const float *theta, const float *x, int64_t n, float *g, void *stream)
+{
+    amp4d_model *model = nullptr;
+    if (!theta || !x || !g || n < 1) return fail(nullptr, AMP4D_ERR_ARG, "bad mlp_forward arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = mlp_num_params();
+    float *th = nullptr;
+    __nv_bfloat16 *wb = nullptr;
+    CK(cudaMalloc(&th, P * sizeof(float)));
+    cudaError_t e = cudaMalloc(&wb, P * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(th, theta, P * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = launch_to_bf16(th, wb, st);
+    if (e == cudaSuccess) e = launch_mlp_forward(wb, x, n, g, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(th);
+    if (wb) cudaFree(wb);
+    if (e != cudaSuccess) return fail(nullptr, AMP4D_ERR_CUDA, std::string("mlp_forward: ") + cudaGetErrorString(e));
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_mlp_loss_grad(const float *theta, const float *xd, int64_t nd, const float *xu,
+                                 int64_t nu, double *out, void *stream)
+{
+    amp4d_model *model = nullptr;
+    if (!theta || !xd || !xu || !out || nd < 1 || nu < 1) return fail(nullptr, AMP4D_ERR_ARG, "bad mlp_loss_grad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = mlp_num_params();
+    float *th = nullptr, *part = nullptr;
+    __nv_bfloat16 *wb = nullptr;
+    double *go = nullptr;
+    CK(cudaMalloc(&th, P * sizeof(float)));
+    cudaError_t e = cudaMalloc(&wb, P * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)mlp_grad_blocks(nd, nu) * (P + 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&go, (P + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(th, theta, P * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = launch_to_bf16(th, wb, st);
+    if (e == cudaSuccess) e = launch_mlp_grad(wb, xd, nd, xu, nu, part, go, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, go, (P + 1) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (void *ptr : {(void *)th, (void *)wb, (void *)part, (void *)go})
+        if (ptr) cudaFree(ptr);
+    if (e != cudaSuccess) return fail(nullptr, AMP4D_ERR_CUDA, std::string("mlp_loss_grad: ") + cudaGetErrorString(e));
+    return AMP4D_OK;
+}
+
+amp4d_status amp4d_grid_sample(const float *gcell, const int *nb, double alpha, uint64_t seed,
+                               int64_t n, double m_lo, double m_hi, const amp4d_particle_masses *masses,
+                               float *m, float *cK, float *cpsi, float *phi, float *w, int64_t *cell,
+                               void *stream)
+{
+    amp4d_model *model = nullptr;
+    if (!gcell || !nb || !masses || !m || !cK || !cpsi || !phi || !w || n < 1 || !(alpha > 0.0 && alpha <= 1.0))
+        return fail(nullptr, AMP4D_ERR_ARG, "bad grid_sample arguments");
+    for (int d = 0; d < 4; ++d)
+        if (nb[d] < 1) return fail(nullptr, AMP4D_ERR_ARG, "grid cells must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nc = (int64_t)nb[0] * nb[1] * nb[2] * nb[3];
+    float *gc = nullptr;
+    double *cdf = nullptr, *scr = nullptr;
+    CK(cudaMalloc(&gc, nc * sizeof(float)));
+    cudaError_t e = cudaMalloc(&cdf, nc * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&scr, (2 * cdf_scratch(nc) + 2) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gc, gcell, nc * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = launch_grid_cdf(gc, nc, alpha, scr, cdf, st);
+    if (e == cudaSuccess)
+        e = launch_grid_sample(cdf, nb, seed, n, m_lo, m_hi, masses->mB, masses->mpsi, masses->mK,
+                               masses->mpi, m, cK, cpsi, phi, w, cell, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (void *ptr : {(void *)gc, (void *)cdf, (void *)scr})
+        if (ptr) cudaFree(ptr);
+    if (e != cudaSuccess) return fail(nullptr, AMP4D_ERR_CUDA, std::string("grid_sample: ") + cudaGetErrorString(e));
     return AMP4D_OK;
 }
 

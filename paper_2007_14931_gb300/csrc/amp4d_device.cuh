@@ -21,17 +21,19 @@ enum : int {
     REC_PHI = 3,   // phi
     REC_P = 4,     // K pi momentum in the B frame
     REC_Q = 5,     // K momentum in the K pi frame
-    REC_NK = 6,    // records of a K*-only model
-    REC_MZ = 6,    // m_J/psi pi
-    REC_PZ = 7,    // Z momentum in the B frame
-    REC_QZ = 8,    // pi momentum in the Z frame
-    REC_CZ = 9,    // cos theta_Z
-    REC_CTZ = 10,  // cos theta~_J/psi
-    REC_CPZ = 11,  // cos phi~
-    REC_SPZ = 12,  // sin phi~
-    REC_CA = 13,   // cos alpha
-    REC_SA = 14,   // sin alpha
-    REC_NZ = 15,   // records of a model with a Z
+    REC_CPHI = 6,  // cos phi (FP64 once, stored FP32)
+    REC_SPHI = 7,  // sin phi
+    REC_NK = 8,    // records of a K*-only model
+    REC_MZ = 8,    // m_J/psi pi
+    REC_PZ = 9,    // Z momentum in the B frame
+    REC_QZ = 10,   // pi momentum in the Z frame
+    REC_CZ = 11,   // cos theta_Z
+    REC_CTZ = 12,  // cos theta~_J/psi
+    REC_CPZ = 13,  // cos phi~
+    REC_SPZ = 14,  // sin phi~
+    REC_CA = 15,   // cos alpha
+    REC_SA = 16,   // sin alpha
+    REC_NZ = 17,   // records of a model with a Z
 };
 
 // Per-resonance constants of Eq. 2-3 at the current (M, G0), built by

@@ -27,26 +27,24 @@ struct EvState {
     float S;
     float2 AK[NK];
     float d0[NK], d1[NK];
-    float2 invDK[NK];
-    float MGK[NK];
     float2 Psi[3][2];
     float2 AZ[NZ > 0 ? NZ : 1];
     float2 Om0[NZ > 0 ? NZ : 1][2], Om1[NZ > 0 ? NZ : 1][2];
-    float2 invDZ[NZ > 0 ? NZ : 1];
-    float MGZ[NZ > 0 ? NZ : 1];
+    float m, invm, p, q;          // kept to recompute lineshapes for mass/width derivatives
+    float mZ, invmZ, pZ, qZ;
 };
 
 template <int NK, int NZ>
 __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                                            EvState<NK, NZ> &ev)
 {
-    const float m = r[REC_M], cK = r[REC_CK], cpsi = r[REC_CPSI], phi = r[REC_PHI];
+    const float m = r[REC_M], cK = r[REC_CK], cpsi = r[REC_CPSI];
     const float p = r[REC_P], q = r[REC_Q];
     const float invm = __frcp_rn(m);
+    ev.m = m; ev.invm = invm; ev.p = p; ev.q = q;
     const float sK = sqrtf(fmaxf(0.0f, fmaf(-cK, cK, 1.0f)));
     const float spsi = sqrtf(fmaxf(0.0f, fmaf(-cpsi, cpsi, 1.0f)));
-    float sph, cph;
-    sincosf(phi, &sph, &cph);
+    const float cph = r[REC_CPHI], sph = r[REC_SPHI];   // e^{i phi}, FP64 at ingest
     float d1p[3][2];
     wigner_1(cpsi, spsi, d1p);
 #pragma unroll
@@ -67,8 +65,6 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
             ev.AK[k] = L.A;
             ev.d0[k] = d0;
             ev.d1[k] = d1;
-            ev.invDK[k] = L.invD;
-            ev.MGK[k] = L.MG;
             if (rs.J == 0) {
                 cfma2(u[1], md.c[rs.col], md.cl[rs.col], cscale(L.A, d0));
             } else {
@@ -79,8 +75,6 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
         } else {
             ev.AK[k] = make_float2(0.f, 0.f);
             ev.d0[k] = ev.d1[k] = 0.f;
-            ev.invDK[k] = make_float2(0.f, 0.f);
-            ev.MGK[k] = 0.f;
         }
     }
 #pragma unroll
@@ -97,6 +91,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
         const float2 ephz = make_float2(r[REC_CPZ], r[REC_SPZ]);
         const float ca = r[REC_CA], sa = r[REC_SA];
         const float invmZ = __frcp_rn(mZ);
+        ev.mZ = mZ; ev.invmZ = invmZ; ev.pZ = pZ; ev.qZ = qZ;
         const float sZ = sqrtf(fmaxf(0.0f, fmaf(-cZ, cZ, 1.0f)));
         const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
         float d1t[3][2];
@@ -108,8 +103,6 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
             float dz0, dz1;
             wigner_l0(rs.J, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
             ev.AZ[z] = L.A;
-            ev.invDZ[z] = L.invD;
-            ev.MGZ[z] = L.MG;
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
                 const float2 eal = make_float2(ca, x == 0 ? sa : -sa);  // e^{i xi alpha}
@@ -283,137 +276,130 @@ __device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, flo
     dAdG = make_float2(-g.y * s, g.x * s);
 }
 
+// Per-thread gradient accumulators live in shared memory, one column per thread
+// (slot-major: slot s of thread t at s * BLOCK + t, so a warp's accesses hit 32
+// distinct banks), which keeps the register count low enough for 4 blocks/SM.
+// Events are read one per iteration with coalesced scalar loads.
 template <int NK, int NZ, bool NORM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_grad(const float *__restrict__ rec, int64_t npad,
-                                                int64_t n, int wrec, const ModelDev *__restrict__ gmd,
-                                                double *__restrict__ part,
-                                                unsigned *__restrict__ status)
+__global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec, int64_t npad,
+                                                   int64_t n, int wrec, const ModelDev *__restrict__ gmd,
+                                                   double *__restrict__ part,
+                                                   unsigned *__restrict__ status)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     using SL = Slots<NK, NZ>;
     __shared__ ModelDev md;
-    __shared__ double red[BLOCK / 32][SL::N];
+    __shared__ double red[BLOCK / 32];
+    extern __shared__ float gsl[];   // [SL::N][BLOCK]
     load_model(gmd, &md);
+    const int tid = threadIdx.x;
+    for (int i = 1; i < SL::N; ++i) gsl[i * BLOCK + tid] = 0.f;
+    float *g = gsl + tid;            // g[s * BLOCK] = slot s of this thread
     Kahan acc0;
     int esum = 0;
     bool bad = false;
-    float g[SL::N];
-#pragma unroll
-    for (int i = 0; i < SL::N; ++i) g[i] = 0.f;
-    const int64_t ngroups = npad >> 2;
     const int nK = md.n_res - NZ;
-    for (int64_t gi = blockIdx.x * (int64_t)BLOCK + threadIdx.x; gi < ngroups;
-         gi += (int64_t)gridDim.x * BLOCK) {
-        float v[4][NREC];
-        load4<NREC>(rec, npad, gi, v);
-        float wv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (NORM) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(rec + wrec * npad) + gi);
-            wv[0] = t.x; wv[1] = t.y; wv[2] = t.z; wv[3] = t.w;
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + tid; e < n; e += (int64_t)gridDim.x * BLOCK) {
+        float v[NREC];
+#pragma unroll
+        for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
+        EvState<NK, NZ> ev;
+        eval_event<NK, NZ>(md, v, ev);
+        float scale;
+        if (!NORM) {
+            if (!(ev.S > 0.0f)) { bad = true; continue; }
+            int ex;
+            float mant = frexpf(ev.S, &ex);
+            if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
+            acc0.add(logf(mant));
+            esum += ex;
+            scale = 2.0f * __frcp_rn(ev.S);
+        } else {
+            const float w = __ldg(rec + wrec * npad + e);
+            acc0.add(w * ev.S);
+            scale = 2.0f * w;
         }
-#pragma unroll 1
-        for (int j = 0; j < 4; ++j) {
-            const int64_t e = 4 * gi + j;
-            if (e >= n) break;
-            EvState<NK, NZ> ev;
-            eval_event<NK, NZ>(md, v[j], ev);
-            float scale;
-            if (!NORM) {
-                if (!(ev.S > 0.0f)) { bad = true; continue; }
-                int ex;
-                float mant = frexpf(ev.S, &ex);
-                if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
-                acc0.add(logf(mant));
-                esum += ex;
-                scale = 2.0f * __frcp_rn(ev.S);
-            } else {
-                acc0.add(wv[j] * ev.S);
-                scale = 2.0f * wv[j];
-            }
-            // v_l = sum_xi conj(a_xi) Psi_{l xi}
-            float2 vl[3];
+        // v_l = sum_xi conj(a_xi) Psi_{l xi}
+        float2 vl[3];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            float2 t = make_float2(0.f, 0.f);
+            cfma_conj(t, ev.a[0], ev.Psi[l][0]);
+            cfma_conj(t, ev.a[1], ev.Psi[l][1]);
+            vl[l] = t;
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            if (k >= nK) continue;
+            const ResDev &rs = md.res[k];
+            // z for l = -1, 0, +1: A d_l v_l with d_{-1} = -d1, d_0 = d0, d_{+1} = d1
+            const float dl[3] = {-ev.d1[k], ev.d0[k], ev.d1[k]};
+            float2 y = make_float2(0.f, 0.f);
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                float2 t = make_float2(0.f, 0.f);
-                cfma_conj(t, ev.a[0], ev.Psi[l][0]);
-                cfma_conj(t, ev.a[1], ev.Psi[l][1]);
-                vl[l] = t;
+                if (rs.J == 0 && l != 1) continue;
+                const float2 t = cscale(vl[l], dl[l]);
+                const float2 z = cmul(ev.AK[k], t);
+                g[(SL::K0 + 6 * k + 2 * l) * BLOCK] += scale * z.x;
+                g[(SL::K0 + 6 * k + 2 * l + 1) * BLOCK] -= scale * z.y;
+                if (rs.fpos >= 0) cfma(y, md.c[rs.J == 0 ? rs.col : rs.col + l], t);
             }
+            if (rs.fpos >= 0) {
+                const LineOut L = lineshape(rs, ev.m, ev.invm, ev.p, ev.q);
+                float2 dM, dG;
+                lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
+                const float2 a = cmul(dM, y), b = cmul(dG, y);
+                g[(SL::MG0 + 2 * k) * BLOCK] += scale * a.x;
+                g[(SL::MG0 + 2 * k + 1) * BLOCK] += scale * b.x;
+            }
+        }
+        if constexpr (NZ > 0) {
 #pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                if (k >= nK) continue;
-                const ResDev &rs = md.res[k];
-                // z for l = -1, 0, +1: A d_l v_l with d_{-1} = -d1, d_0 = d0, d_{+1} = d1
-                const float dl[3] = {-ev.d1[k], ev.d0[k], ev.d1[k]};
-                float2 y = make_float2(0.f, 0.f);
+            for (int z = 0; z < NZ; ++z) {
+                const ResDev &rs = md.res[nK + z];
+                float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    if (rs.J == 0 && l != 1) continue;
-                    const float2 t = cscale(vl[l], dl[l]);
-                    const float2 z = cmul(ev.AK[k], t);
-                    g[SL::K0 + 6 * k + 2 * l] += scale * z.x;
-                    g[SL::K0 + 6 * k + 2 * l + 1] -= scale * z.y;
-                    if (rs.fpos >= 0) cfma(y, md.c[rs.J == 0 ? rs.col : rs.col + l], t);
+                for (int x = 0; x < 2; ++x) {
+                    cfma_conj(w0, ev.a[x], ev.Om0[z][x]);
+                    cfma_conj(w1, ev.a[x], ev.Om1[z][x]);
                 }
+                const float2 z0 = cmul(ev.AZ[z], w0), z1 = cmul(ev.AZ[z], w1);
+                g[(SL::Z0 + 4 * z + 0) * BLOCK] += scale * z0.x;
+                g[(SL::Z0 + 4 * z + 1) * BLOCK] -= scale * z0.y;
+                g[(SL::Z0 + 4 * z + 2) * BLOCK] += scale * z1.x;
+                g[(SL::Z0 + 4 * z + 3) * BLOCK] -= scale * z1.y;
                 if (rs.fpos >= 0) {
+                    float2 y = make_float2(0.f, 0.f);
+                    if (rs.zcol0 >= 0) cfma(y, md.c[rs.zcol0], w0);
+                    if (rs.zcol1 >= 0) cfma(y, md.c[rs.zcol1], w1);
+                    const LineOut L = lineshape(rs, ev.mZ, ev.invmZ, ev.pZ, ev.qZ);
                     float2 dM, dG;
-                    lineshape_derivs(rs, ev.AK[k], ev.invDK[k], ev.MGK[k], dM, dG);
+                    lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
                     const float2 a = cmul(dM, y), b = cmul(dG, y);
-                    g[SL::MG0 + 2 * k] += scale * a.x;
-                    g[SL::MG0 + 2 * k + 1] += scale * b.x;
-                }
-            }
-            if constexpr (NZ > 0) {
-#pragma unroll
-                for (int z = 0; z < NZ; ++z) {
-                    const ResDev &rs = md.res[nK + z];
-                    float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int x = 0; x < 2; ++x) {
-                        cfma_conj(w0, ev.a[x], ev.Om0[z][x]);
-                        cfma_conj(w1, ev.a[x], ev.Om1[z][x]);
-                    }
-                    const float2 z0 = cmul(ev.AZ[z], w0), z1 = cmul(ev.AZ[z], w1);
-                    g[SL::Z0 + 4 * z + 0] += scale * z0.x;
-                    g[SL::Z0 + 4 * z + 1] -= scale * z0.y;
-                    g[SL::Z0 + 4 * z + 2] += scale * z1.x;
-                    g[SL::Z0 + 4 * z + 3] -= scale * z1.y;
-                    if (rs.fpos >= 0) {
-                        float2 y = make_float2(0.f, 0.f);
-                        if (rs.zcol0 >= 0) cfma(y, md.c[rs.zcol0], w0);
-                        if (rs.zcol1 >= 0) cfma(y, md.c[rs.zcol1], w1);
-                        float2 dM, dG;
-                        lineshape_derivs(rs, ev.AZ[z], ev.invDZ[z], ev.MGZ[z], dM, dG);
-                        const float2 a = cmul(dM, y), b = cmul(dG, y);
-                        g[SL::MG0 + 2 * (NK + z)] += scale * a.x;
-                        g[SL::MG0 + 2 * (NK + z) + 1] += scale * b.x;
-                    }
+                    g[(SL::MG0 + 2 * (NK + z)) * BLOCK] += scale * a.x;
+                    g[(SL::MG0 + 2 * (NK + z) + 1) * BLOCK] += scale * b.x;
                 }
             }
         }
     }
     if (bad) atomicOr(status, 1u);
-    // Block reduction of every slot in FP64.
     double t0 = acc0.value();
     if (!NORM) t0 += (double)esum * 0.69314718055994530942;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    {
-        double v0 = warp_sum(t0);
-        if (lane == 0) red[w][0] = v0;
-    }
-#pragma unroll
-    for (int i = 1; i < SL::N; ++i) {
-        double vi = warp_sum((double)g[i]);
-        if (lane == 0) red[w][i] = vi;
-    }
+    t0 = warp_sum(t0);
+    if ((tid & 31) == 0) red[tid >> 5] = t0;
     __syncthreads();
-    for (int i = threadIdx.x; i < SL::N; i += BLOCK) {
+    if (tid == 0) {
         double t = 0.0;
-        for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww][i];
-        part[(int64_t)blockIdx.x * SL::N + i] = t;
+        for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww];
+        part[(int64_t)blockIdx.x * SL::N] = t;
+    }
+    // Block sums of every gradient slot in FP64, in thread order.
+    for (int s2 = 1 + tid; s2 < SL::N; s2 += BLOCK) {
+        double t = 0.0;
+        for (int j = 0; j < BLOCK; ++j) t += (double)gsl[s2 * BLOCK + j];
+        part[(int64_t)blockIdx.x * SL::N + s2] = t;
     }
 }
-
 
 constexpr int EVAL_BLOCK = 256;
 constexpr int GRAD_BLOCK = 128;
@@ -441,12 +427,20 @@ cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
 template <int NK, int NZ>
 cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
 {
-    if (norm)
-        k_grad<NK, NZ, true, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, 0, a.stream>>>(
+    const size_t smem = (size_t)Slots<NK, NZ>::N * GRAD_BLOCK * sizeof(float);
+    if (norm) {
+        cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, true, GRAD_BLOCK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_grad<NK, NZ, true, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
             a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status);
-    else
-        k_grad<NK, NZ, false, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, 0, a.stream>>>(
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, false, GRAD_BLOCK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_grad<NK, NZ, false, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
             a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status);
+    }
     return cudaGetLastError();
 }
 

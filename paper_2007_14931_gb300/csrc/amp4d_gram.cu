@@ -25,7 +25,9 @@
 // Operand tiles: each K-step covers 16 rows (8 points x 2 xi); the four digit
 // slices of the 64 padded columns form a 256 x 16 BF16 tile in the canonical
 // K-major no-swizzle layout (8-row x 16-byte core matrices, K-direction core
-// stride 128 B, row-group stride 256 B).  Per K-step two MMAs, M = 128:
+// stride 144 B, row-group stride 288 B, stages 9248 B apart: the padding puts
+// the 2-byte digit stores of a warp -- 8 points in each of 4 stages -- on 32
+// distinct shared-memory banks).  Per K-step two MMAs, M = 128:
 //   MMA1: A = slices {1,2} (rows 0..127) x B = slices {1..4} (N = 256)
 //   MMA2: A = slices {3,4} (rows 128..255) x B = slice 3     (N = 64)
 // Warp roles: warps 0-3 produce the tiles (basis of Eq. 2-5, 10-12 per point,
@@ -42,17 +44,18 @@ namespace amp4d {
 constexpr int GT_PROD = 128;               // producer threads (warps 0-3)
 constexpr int GT_THREADS = 9 * 32;
 constexpr int GT_NSTAGE = 16;
-constexpr int GT_STAGE_BYTES = 256 * 16 * 2;
+constexpr int GT_LBO = 144;                // K-direction core-matrix stride (128 B + 16 B pad)
+constexpr int GT_SBO = 288;                // 8-row group stride
+constexpr int GT_STAGE_BYTES = 32 * GT_SBO + 32;   // 9248: stage starts 8 banks apart
 constexpr int GT_CHUNK_KSTEPS = 64;        // 1024 rows = 512 points per chunk
 constexpr int GT_CHUNK_POINTS = GT_CHUNK_KSTEPS * 8;
 constexpr int GT_TMEM_COLS = 512;
-constexpr int GT_LBO = 128;                // K-direction core-matrix stride
-constexpr int GT_SBO = 256;                // 8-row group stride
 constexpr long long GT_WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz
+constexpr int GT_GS = 65;                  // row stride of the INT64 accumulator (bank spread)
 
 struct GramSmem {
     alignas(1024) uint8_t stage[GT_NSTAGE][GT_STAGE_BYTES];
-    unsigned long long G[64 * 64];
+    unsigned long long G[64 * GT_GS];
     unsigned long long full[GT_NSTAGE], empty[GT_NSTAGE], acc_full, acc_empty, drain;
     float scale[64];
     uint32_t tmem_base;
@@ -140,6 +143,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     // Set-up: zero tiles and G, scales, barriers, tensor memory.
     for (int i = tid; i < GT_NSTAGE * GT_STAGE_BYTES / 16; i += GT_THREADS)
         reinterpret_cast<uint4 *>(&S.stage[0][0])[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < 64 * 64; i += GT_THREADS) S.G[i] = 0ull;
+    for (int i = tid; i < 64 * GT_GS; i += GT_THREADS) S.G[i] = 0ull;
     if (tid < 64) S.scale[tid] = gscale ? gscale[tid] : 1.0f;
     if (tid == 0) {
         S.abort_flag = 0;
@@ -346,16 +362,16 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
             tc_fence_after();
             const int i = row & 63;
             const bool lo = row < 64;        // slice-1 rows (lo) or slice-2 rows (hi)
-            for (int jb = 0; jb < 64; jb += 32) {
-                float q1[32], q2[32], q3[32], q4[32], q5[32];
-                tmem_ld32(lane_addr + jb, q1);        // P_a1
-                tmem_ld32(lane_addr + 64 + jb, q2);   // P_a2
-                tmem_ld32(lane_addr + 128 + jb, q3);  // P_a3
-                tmem_ld32(lane_addr + 192 + jb, q4);  // P_a4
-                tmem_ld32(lane_addr + 256 + jb, q5);  // lo: P_33, hi: P_43
+            for (int jb = 0; jb < 64; jb += 16) {
+                float q1[16], q2[16], q3[16], q4[16], q5[16];
+                tmem_ld16(lane_addr + jb, q1);        // P_a1
+                tmem_ld16(lane_addr + 64 + jb, q2);   // P_a2
+                tmem_ld16(lane_addr + 128 + jb, q3);  // P_a3
+                tmem_ld16(lane_addr + 192 + jb, q4);  // P_a4
+                tmem_ld16(lane_addr + 256 + jb, q5);  // lo: P_33, hi: P_43
                 tmem_wait_ld();
-#pragma unroll 4
-                for (int t = 0; t < 32; ++t) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
                     const long long p1 = __float2ll_rn(q1[t]), p2 = __float2ll_rn(q2[t]);
                     const long long p3 = __float2ll_rn(q3[t]), p4 = __float2ll_rn(q4[t]);
                     const long long p5 = __float2ll_rn(q5[t]);
@@ -369,8 +385,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                         T = p3 + r24 + r43;                         // (3,2), (4,2), (3,4)
                     }
                     const int j = jb + t;
-                    atomicAdd(&S.G[i * 64 + j], (unsigned long long)D);
-                    atomicAdd(&S.G[j * 64 + i], (unsigned long long)T);
+                    atomicAdd(&S.G[i * GT_GS + j], (unsigned long long)D);
+                    atomicAdd(&S.G[j * GT_GS + i], (unsigned long long)T);
                 }
             }
             tc_fence_before();
@@ -395,7 +411,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                 tc_fence_after();
                 const uint32_t base = smem_u32(S.stage[s]);
                 const uint64_t dA1 = smem_desc(base), dB1 = smem_desc(base);
-                const uint64_t dA2 = smem_desc(base + 16 * GT_SBO), dB2 = smem_desc(base + 16 * GT_SBO);
+                const uint64_t dA2 = smem_desc(base + 16 * GT_SBO), dB2 = smem_desc(base + 16 * GT_SBO);  // rows 128..
                 mma_bf16(tmem, dA1, dB1, id1, kk > 0);
                 mma_bf16(tmem + 256, dA2, dB2, id2, kk > 0);
                 mma_commit(&S.empty[s]);
@@ -422,7 +438,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     }
     if (S.abort_flag && tid == 0) atomicExch(err, 1);
     for (int i = tid; i < 64 * 64; i += GT_THREADS)
-        part[(int64_t)blockIdx.x * 4096 + i] = (long long)S.G[i];
+        part[(int64_t)blockIdx.x * 4096 + i] = (long long)S.G[(i >> 6) * GT_GS + (i & 63)];
 }
 
 // Sum the per-CTA INT64 partials and convert: with X_i = x_i g_i (g = gscale) and

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace amp4d {
@@ -63,6 +64,41 @@ cudaError_t launch_gram(const GramArgs &a);
 cudaError_t launch_gram_selftest(const int *synth, int64_t n, const ModelDev *md, long long *part,
                                  int grid, int *err, long long *out, cudaStream_t st);
 int gram_chunk_points();
+
+// Generator and learned proposal (amp4d_proposal.cu).
+cudaError_t launch_gen_candidates(float *rec, int64_t npad, int64_t n, uint64_t first,
+                                  uint32_t stream_id, uint64_t seed, double m_lo, double m_hi,
+                                  float *uacc, cudaStream_t st);
+int gen_tile();
+cudaError_t launch_gen_accept(const float *rec, int64_t npad, int64_t n, const float *S,
+                              const float *uacc, double fmax, unsigned *blk_count, unsigned *over,
+                              unsigned *fmax_bits, cudaStream_t st);
+cudaError_t launch_gen_scatter(const float *rec, int64_t npad, int64_t n, const float *S,
+                               const float *uacc, double fmax, const unsigned *blk_count,
+                               unsigned long long *off, int64_t base, int64_t n_want, float *om,
+                               float *ocK, float *ocpsi, float *ophi, cudaStream_t st);
+int mlp_num_params();
+void mlp_init_params(float *th, uint64_t seed);
+cudaError_t launch_mlp_forward(const __nv_bfloat16 *wb, const float *x, int64_t n, float *g,
+                               cudaStream_t st);
+cudaError_t launch_mlp_grid(const __nv_bfloat16 *wb, const int nb[4], float *g, cudaStream_t st);
+size_t mlp_grad_smem();
+int mlp_grad_blocks(int64_t nd, int64_t nu);
+cudaError_t launch_mlp_grad(const __nv_bfloat16 *wb, const float *xd, int64_t nd, const float *xu,
+                            int64_t nu, float *part, double *out, cudaStream_t st);
+cudaError_t launch_adam(float *th, float *m, float *v, const double *grad, float lr, float b1,
+                        float b2, float eps, int64_t t, __nv_bfloat16 *wb, cudaStream_t st);
+cudaError_t launch_to_bf16(const float *th, __nv_bfloat16 *wb, cudaStream_t st);
+cudaError_t launch_mlp_batch(const float *em, const float *ecK, const float *ecpsi, const float *ephi,
+                             int64_t n, int64_t nd, int64_t nu, uint64_t seed, uint64_t step,
+                             double m_lo, double m_hi, float *xd, float *xu, cudaStream_t st);
+int64_t cdf_scratch(int64_t ncell);
+cudaError_t launch_grid_cdf(const float *g, int64_t ncell, double alpha, double *scratch,
+                            double *cdf, cudaStream_t st);
+cudaError_t launch_grid_sample(const double *cdf, const int nb[4], uint64_t seed, int64_t n,
+                               double m_lo, double m_hi, double mB, double mpsi, double mK,
+                               double mpi, float *om, float *ocK, float *ocpsi, float *ophi, float *w,
+                               int64_t *cell, cudaStream_t st);
 
 // One-time FP64 preparation of an event set (amp4d_prepare.cu).
 struct PrepArgs {

@@ -1,7 +1,8 @@
 // One-time preparation of an event (or normalisation-point) set, in FP64.
 //
 // Per event: validates the coordinates against the box, computes the two-body
-// momenta p (K pi in the B frame) and q (K in the K pi frame), and for models
+// momenta p (K pi in the B frame) and q (K in the K pi frame), cos phi and
+// sin phi, and for models
 // with a Z the J/psi pi chain quantities of Eq. 10: m_psipi, the Z momentum in
 // the B frame, the pi momentum in the Z frame, cos theta_Z, cos theta~_psi,
 // (cos, sin) phi~ and (cos, sin) alpha.  Results are stored as FP32 records;
@@ -74,6 +75,12 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_prepare(PrepArgs a)
         const double q = two_body(m, a.mK, a.mpi);
         rec[REC_P * np + e] = (float)p;
         rec[REC_Q * np + e] = (float)q;
+        {
+            double sphi0, cphi0;
+            sincos(phi, &sphi0, &cphi0);
+            rec[REC_CPHI * np + e] = (float)cphi0;
+            rec[REC_SPHI * np + e] = (float)sphi0;
+        }
         if (e < a.n) lnpq += log(p * q);
         if (a.wrec >= 0 && !a.have_w) rec[a.wrec * np + e] = e < a.n ? (float)(p * q) : 0.0f;
         if (HZ) {

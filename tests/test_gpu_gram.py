@@ -150,7 +150,8 @@ def test_cached_path_nll_grad(A, name):
     nll2, g2 = gm.eval_nll_grad(p2)
     nll2_o, g2_o, _, _ = om.nll(p2, ev, nm, grad=True)
     assert abs(nll2 - nll2_o) < 1e-3
-    assert gm.eval_nll(p2) == pytest.approx(nll2, abs=1e-9)
+    # the NLL-only and NLL+gradient kernels sum in different orders (FP32 per-thread sums)
+    assert gm.eval_nll(p2) == pytest.approx(nll2, abs=1e-5)
 
 
 def test_cached_path_with_floating_mass_uses_points(A):
