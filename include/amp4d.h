@@ -262,6 +262,31 @@ amp4d_status amp4d_grid_sample(const float *gcell, const int *nb, double alpha, 
                                void *stream);
 
 /*
+ * Allocation-free variant of amp4d_mlp_loss_grad, for callers that may not
+ * call cudaMalloc: code that runs while another component's pool owns the
+ * device memory budget, or code that must avoid the device-wide
+ * synchronisation an allocation or free can cause.  The paper has no
+ * counterpart; this is an interface of this library only.
+ *
+ * theta (4545 FP32 weights), xd (nd x 4 data rows) and xu (nu x 4 uniform rows)
+ * are DEVICE memory; out is DEVICE memory of 4546 doubles receiving the
+ * gradient of the KL objective and then its value (same arithmetic as
+ * amp4d_mlp_loss_grad).  All are caller-owned.  The call is stream-ordered and
+ * does not synchronise; it allocates nothing: its scratch (about 1.2 MB) is a
+ * file-scope device array that every GPU which loads the library holds until
+ * the process exits.  nd and nu must not exceed AMP4D_NOALLOC_MAX_ROWS, else
+ * AMP4D_ERR_ARG.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) for the device; make that first call before
+ * any stream capture.  Every call uses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: order them on
+ * one stream.  amp4d_noalloc_last_error describes the last failure.
+ */
+#define AMP4D_NOALLOC_MAX_ROWS 4096
+amp4d_status amp4d_mlp_loss_grad_noalloc(const float *theta, const float *xd, int64_t nd,
+                                         const float *xu, int64_t nu, double *out, void *stream);
+const char *amp4d_noalloc_last_error(void);
+
+/*
  * Device timing of evaluations (CUDA events around each phase, on the
  * evaluation's stream).  amp4d_profile_read waits for the recorded work and
  * returns, then clears, the summed milliseconds and counts of the phases

@@ -81,6 +81,16 @@ def mlp_loss_grad(theta, xd, xu, stream=None):
     return out[-1], out[:-1]
 
 
+def mlp_loss_grad_noalloc(theta_dev, xd, xu, out_dev, stream=None):
+    """Allocation-free KL gradient: all arguments are torch cuda tensors; out_dev (4546
+    float64) receives the gradient and then the loss.  Stream-ordered, no sync."""
+    rc = amp4d_mlp_loss_grad_noalloc(theta_dev.data_ptr(), xd.data_ptr(), xd.shape[0],
+                                     xu.data_ptr(), xu.shape[0], out_dev.data_ptr(),
+                                     _stream_ptr(stream))
+    if rc != 0:
+        raise Amp4dError(rc, amp4d_noalloc_last_error().decode())
+
+
 def grid_sample(gcell, nb, alpha, seed, n, masses=None, box=None, stream=None):
     """Sampler of the grid proposal on given cell values: (m, cK, cpsi, phi), w, cell (torch cuda)."""
     import torch
@@ -154,6 +164,10 @@ amp4d_mlp_loss_grad = _proto("amp4d_mlp_loss_grad", C.c_int, [_vp, _vp, C.c_int6
 amp4d_grid_sample = _proto("amp4d_grid_sample", C.c_int,
                            [_vp, _vp, C.c_double, C.c_uint64, C.c_int64, C.c_double, C.c_double,
                             C.POINTER(amp4d_particle_masses), _vp, _vp, _vp, _vp, _vp, _vp, _vp])
+amp4d_mlp_loss_grad_noalloc = _proto("amp4d_mlp_loss_grad_noalloc", C.c_int,
+                                     [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp])
+amp4d_noalloc_last_error = _proto("amp4d_noalloc_last_error", C.c_char_p, [])
+AMP4D_NOALLOC_MAX_ROWS = 4096
 amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
 amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
 
@@ -162,7 +176,8 @@ EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "am
             "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
             "amp4d_profile_enable", "amp4d_profile_read", "amp4d_build_gram", "amp4d_get_gram",
             "amp4d_gram_selftest", "amp4d_generate", "amp4d_proposal_train",
-            "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample"]
+            "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample",
+            "amp4d_mlp_loss_grad_noalloc", "amp4d_noalloc_last_error"]
 
 MLP_NUM_PARAMS = 4545
 
