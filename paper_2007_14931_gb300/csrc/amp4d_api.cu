@@ -31,6 +31,8 @@ struct EventSet {
     int grid_eval = 0, grid_grad = 0;
     double *part = nullptr;     // per-block partials (grid_grad x nslot)
     size_t part_cap = 0;
+    float2 *lcache = nullptr;   // basis cache [resonance][npad] (cached path)
+    bool lcache_valid = false;
 };
 
 thread_local std::string g_create_error;
@@ -160,6 +162,8 @@ amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const flo
     CK(cudaSetDevice(model->device));
     if (s.rec) { cudaFree(s.rec); s.rec = nullptr; }
     if (s.part) { cudaFree(s.part); s.part = nullptr; }
+    if (s.lcache) { cudaFree(s.lcache); s.lcache = nullptr; }
+    s.lcache_valid = false;
     s.n = 0;
     const int64_t npad = (n + 3) & ~int64_t(3);
     const int nrec = model->nZ > 0 ? REC_NZ : REC_NK;
@@ -230,7 +234,20 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.nk_max = mo->nk_max;
     a.nz = mo->nZ;
     a.stream = st;
+    a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
     return a;
+}
+
+// Basis cache of a set for the current (fixed) masses and widths; the table
+// must already be on the stream.  Allocates on first use.
+amp4d_status ensure_lcache(amp4d_model *model, EventSet &s, cudaStream_t st)
+{
+    if (s.lcache_valid || s.n == 0) return AMP4D_OK;
+    if (!s.lcache) CK(cudaMalloc(&s.lcache, (size_t)model->res.size() * s.npad * sizeof(float2)));
+    LaunchArgs a = args_for(model, s, nullptr, nullptr, st, model->nsm * 8);
+    CK(launch_lcache(a, s.lcache));
+    s.lcache_valid = true;
+    return AMP4D_OK;
 }
 
 amp4d_status check_params(amp4d_model *model, const double *params)
@@ -323,6 +340,11 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
     };
     CK(mark());
     CK(launch_build_table(model->d_static, d_params, model->d_md, model->d_pscale, model->d_status, st));
+    if (model->path == AMP4D_PATH_CACHED) {
+        amp4d_status rc = ensure_lcache(model, model->ev, st);
+        if (rc == AMP4D_OK && !use_gram(model)) rc = ensure_lcache(model, model->mc, st);
+        if (rc) return rc;
+    }
     CK(mark());
     double *rd = model->d_red, *rn = model->d_red + model->nslot;
     if (use_gram(model)) {
@@ -525,6 +547,7 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
     for (EventSet *s : {&model->ev, &model->mc}) {
         if (s->rec) cudaFree(s->rec);
         if (s->part) cudaFree(s->part);
+        if (s->lcache) cudaFree(s->lcache);
     }
     if (model->d_md) cudaFree(model->d_md);
     if (model->d_static) cudaFree(model->d_static);

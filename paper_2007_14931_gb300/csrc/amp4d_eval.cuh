@@ -34,9 +34,22 @@ struct EvState {
     float mZ, invmZ, pZ, qZ;
 };
 
+// Lineshape of internal resonance k for this event: from the basis cache when
+// one is given and the resonance's mass and width are fixed, else computed.
+__device__ __forceinline__ float2 cached_or_computed(const ResDev &rs, const float2 *__restrict__ lc,
+                                                     int64_t lcn, int k, int64_t e, float m,
+                                                     float invm, float p, float q)
+{
+    if (lc != nullptr && rs.fpos < 0) return __ldg(lc + k * lcn + e);
+    return lineshape(rs, m, invm, p, q).A;
+}
+
+// lc (nullable): basis cache [resonance][lcn] of lineshapes A'_R per event e.
 template <int NK, int NZ>
 __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
-                                           EvState<NK, NZ> &ev)
+                                           EvState<NK, NZ> &ev,
+                                           const float2 *__restrict__ lc = nullptr,
+                                           int64_t lcn = 0, int64_t e = 0)
 {
     const float m = r[REC_M], cK = r[REC_CK], cpsi = r[REC_CPSI];
     const float p = r[REC_P], q = r[REC_Q];
@@ -59,18 +72,18 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     for (int k = 0; k < NK; ++k) {
         if (k < nK) {
             const ResDev &rs = md.res[k];
-            LineOut L = lineshape(rs, m, invm, p, q);
+            const float2 LA = cached_or_computed(rs, lc, lcn, k, e, m, invm, p, q);
             float d0, d1;
             wigner_l0(rs.J, cK, sK, d0, d1);
-            ev.AK[k] = L.A;
+            ev.AK[k] = LA;
             ev.d0[k] = d0;
             ev.d1[k] = d1;
             if (rs.J == 0) {
-                cfma2(u[1], md.c[rs.col], md.cl[rs.col], cscale(L.A, d0));
+                cfma2(u[1], md.c[rs.col], md.cl[rs.col], cscale(LA, d0));
             } else {
-                cfma2(u[0], md.c[rs.col], md.cl[rs.col], cscale(L.A, -d1));
-                cfma2(u[1], md.c[rs.col + 1], md.cl[rs.col + 1], cscale(L.A, d0));
-                cfma2(u[2], md.c[rs.col + 2], md.cl[rs.col + 2], cscale(L.A, d1));
+                cfma2(u[0], md.c[rs.col], md.cl[rs.col], cscale(LA, -d1));
+                cfma2(u[1], md.c[rs.col + 1], md.cl[rs.col + 1], cscale(LA, d0));
+                cfma2(u[2], md.c[rs.col + 2], md.cl[rs.col + 2], cscale(LA, d1));
             }
         } else {
             ev.AK[k] = make_float2(0.f, 0.f);
@@ -99,10 +112,10 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
             const ResDev &rs = md.res[nK + z];
-            LineOut L = lineshape(rs, mZ, invmZ, pZ, qZ);
+            const float2 LA = cached_or_computed(rs, lc, lcn, nK + z, e, mZ, invmZ, pZ, qZ);
             float dz0, dz1;
             wigner_l0(rs.J, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
-            ev.AZ[z] = L.A;
+            ev.AZ[z] = LA;
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
                 const float2 eal = make_float2(ca, x == 0 ? sa : -sa);  // e^{i xi alpha}
@@ -116,7 +129,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                 float2 s = make_float2(0.f, 0.f);
                 if (rs.zcol0 >= 0) cfma2(s, md.c[rs.zcol0], md.cl[rs.zcol0], o0);
                 if (rs.zcol1 >= 0) cfma2(s, md.c[rs.zcol1], md.cl[rs.zcol1], o1);
-                cfma(ev.a[x], L.A, s);
+                cfma(ev.a[x], LA, s);
             }
         }
     }
@@ -185,7 +198,8 @@ template <int NK, int NZ, int MODE, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, int64_t npad,
                                                 int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                 double *__restrict__ part, float *__restrict__ S_out,
-                                                unsigned *__restrict__ status)
+                                                unsigned *__restrict__ status,
+                                                const float2 *__restrict__ lc)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     __shared__ ModelDev md;
@@ -208,7 +222,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
 #pragma unroll 1
         for (int j = 0; j < 4; ++j) {
             EvState<NK, NZ> ev;
-            eval_event<NK, NZ>(md, v[j], ev);
+            eval_event<NK, NZ>(md, v[j], ev, lc, npad, 4 * g + j);
             Sv[j] = ev.S;
         }
 #pragma unroll
@@ -284,7 +298,8 @@ template <int NK, int NZ, bool NORM, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec, int64_t npad,
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                    double *__restrict__ part,
-                                                   unsigned *__restrict__ status)
+                                                   unsigned *__restrict__ status,
+                                                   const float2 *__restrict__ lc)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     using SL = Slots<NK, NZ>;
@@ -304,7 +319,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
 #pragma unroll
         for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
         EvState<NK, NZ> ev;
-        eval_event<NK, NZ>(md, v, ev);
+        eval_event<NK, NZ>(md, v, ev, lc, npad, e);
         float scale;
         if (!NORM) {
             if (!(ev.S > 0.0f)) { bad = true; continue; }
@@ -410,15 +425,15 @@ cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
     switch (mode) {
     case MODE_SUM_LNS:
         k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status);
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
         break;
     case MODE_SUM_WS:
         k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status);
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
         break;
     default:
         k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status);
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
         break;
     }
     return cudaGetLastError();
@@ -433,15 +448,62 @@ cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_grad<NK, NZ, true, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status);
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, false, GRAD_BLOCK>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_grad<NK, NZ, false, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status);
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache);
     }
     return cudaGetLastError();
+}
+
+// Basis cache: A'_R (Eq. 2-3 without its column constant) of every resonance for
+// every event of a set, [internal resonance][npad] complex FP32.  The per-event
+// angular factors (Eq. 4, 10) stay per evaluation: they are cheap polynomials,
+// while the lineshapes carry the square roots and reciprocals.
+template <int NK, int NZ>
+__global__ void __launch_bounds__(256) k_build_lcache(const float *__restrict__ rec, int64_t npad,
+                                                      const ModelDev *__restrict__ gmd,
+                                                      float2 *__restrict__ lc)
+{
+    __shared__ ModelDev md;
+    load_model(gmd, &md);
+    const int nK = md.n_res - NZ;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < npad;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float m = rec[REC_M * npad + e], p = rec[REC_P * npad + e], q = rec[REC_Q * npad + e];
+        const float invm = __frcp_rn(m);
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            if (k < nK) lc[k * npad + e] = lineshape(md.res[k], m, invm, p, q).A;
+        if constexpr (NZ > 0) {
+            const float mZ = rec[REC_MZ * npad + e], pZ = rec[REC_PZ * npad + e];
+            const float qZ = rec[REC_QZ * npad + e], invmZ = __frcp_rn(mZ);
+#pragma unroll
+            for (int z = 0; z < NZ; ++z)
+                lc[(nK + z) * npad + e] = lineshape(md.res[nK + z], mZ, invmZ, pZ, qZ).A;
+        }
+    }
+}
+
+template <int NK, int NZ>
+cudaError_t launch_lcache_t(const LaunchArgs &a, float2 *lc)
+{
+    k_build_lcache<NK, NZ><<<a.grid, 256, 0, a.stream>>>(a.rec, a.npad, a.md, lc);
+    return cudaGetLastError();
+}
+
+template <int NK>
+cudaError_t launch_lcache_nk(const LaunchArgs &a, float2 *lc)
+{
+    switch (a.nz) {
+    case 0: return launch_lcache_t<NK, 0>(a, lc);
+    case 1: return launch_lcache_t<NK, 1>(a, lc);
+    case 2: return launch_lcache_t<NK, 2>(a, lc);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // Entry for one resonance-count bucket NK, dispatching on the number of Z.

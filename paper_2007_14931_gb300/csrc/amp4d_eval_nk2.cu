@@ -4,4 +4,5 @@
 namespace amp4d {
 template cudaError_t launch_eval_nk<2>(const LaunchArgs &, int);
 template cudaError_t launch_grad_nk<2>(const LaunchArgs &, bool);
+template cudaError_t launch_lcache_nk<2>(const LaunchArgs &, float2 *);
 }  // namespace amp4d

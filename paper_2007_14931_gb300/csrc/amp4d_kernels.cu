@@ -296,6 +296,10 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
 // ---------------------------------------------------------------------------
 template <int NK> cudaError_t launch_eval_nk(const LaunchArgs &a, int mode);
 template <int NK> cudaError_t launch_grad_nk(const LaunchArgs &a, bool norm);
+template <int NK> cudaError_t launch_lcache_nk(const LaunchArgs &a, float2 *lc);
+extern template cudaError_t launch_lcache_nk<2>(const LaunchArgs &, float2 *);
+extern template cudaError_t launch_lcache_nk<10>(const LaunchArgs &, float2 *);
+extern template cudaError_t launch_lcache_nk<16>(const LaunchArgs &, float2 *);
 extern template cudaError_t launch_eval_nk<2>(const LaunchArgs &, int);
 extern template cudaError_t launch_eval_nk<10>(const LaunchArgs &, int);
 extern template cudaError_t launch_eval_nk<16>(const LaunchArgs &, int);
@@ -326,6 +330,16 @@ cudaError_t launch_grad(const LaunchArgs &a, bool norm)
     case 2: return launch_grad_nk<2>(a, norm);
     case 10: return launch_grad_nk<10>(a, norm);
     case 16: return launch_grad_nk<16>(a, norm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc)
+{
+    switch (a.nk_max) {
+    case 2: return launch_lcache_nk<2>(a, lc);
+    case 10: return launch_lcache_nk<10>(a, lc);
+    case 16: return launch_lcache_nk<16>(a, lc);
     default: return cudaErrorInvalidValue;
     }
 }

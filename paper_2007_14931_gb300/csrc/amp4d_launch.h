@@ -21,6 +21,7 @@ struct LaunchArgs {
     int grid;
     int nk_max, nz;          // template bucket
     cudaStream_t stream;
+    const float2 *lcache = nullptr;  // basis cache of the set, or null (recompute)
 };
 
 int nk_bucket(int nk);
@@ -30,6 +31,7 @@ int grad_block();
 
 cudaError_t launch_eval(const LaunchArgs &a, int mode);  // 0 ln S, 1 w S, 2 write S
 cudaError_t launch_grad(const LaunchArgs &a, bool norm);
+cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc);
 cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *out,
                                cudaStream_t s);
 cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_param,

@@ -104,7 +104,7 @@ def test_nll_grad_parity_model_data(A, name):
     tol = np.maximum(1e-6 * np.abs(g_o), 1e-5 * np.max(np.abs(g_o)))
     assert np.all(np.abs(g - g_o) <= tol), np.max(np.abs(g - g_o) / np.max(np.abs(g_o)))
     nll2 = gm.eval_nll(p)
-    assert nll2 == pytest.approx(nll, abs=1e-5)  # NLL-only kernel: other summation order
+    assert nll2 == pytest.approx(nll, abs=1e-4)  # NLL-only kernel: other summation order
 
 
 def test_grad_parity_all_masses_floating(A):
