@@ -180,6 +180,48 @@ amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *para
                                 void *stream);
 
 /*
+ * Shard partials.  The unbinned likelihood (Introduction) is a product over
+ * data events and the normalisation I of Eq. 5 is estimated as a sum over points, so
+ * when the events and the points of one fit are split into shards (one model
+ * per shard, e.g. one per GPU) an evaluation needs only these sums per shard:
+ *   out[0] sum_e ln S_e, [1] sum_e ln(p_e q_e), [2] N (data events),
+ *   [3] T = V sum_n w_n S_n (V = the volume given to amp4d_set_norm_points;
+ *       on the Gram path T = V (u^T G u + v^T G v)), [4] M (points),
+ *   [5] status bits (1: S <= 0 at a data event, 2: invalid parameters),
+ *   [6 .. 6+P) d(sum ln S)/dtheta, [6+P .. 6+2P) dT/dtheta  (what = NLL_GRAD),
+ * P = amp4d_num_params.  No logarithm of I is taken per shard.
+ * amp4d_eval_partials: params and out are HOST memory (6 or 6 + 2P doubles),
+ * synchronous.  amp4d_enqueue_partials: params and out are DEVICE memory owned
+ * by the caller, enqueued on the stream without synchronising, with the same
+ * rule as amp4d_enqueue_eval about overlapping evaluations of one model.
+ * Errors: ARG (bad what, null or invalid parameters), STATE (no events or no
+ * points in this shard), CUDA.
+ */
+amp4d_status amp4d_eval_partials(amp4d_model *model, int what, const double *params, double *out,
+                                 void *stream);
+amp4d_status amp4d_enqueue_partials(amp4d_model *model, int what, const double *params,
+                                    double *out, void *stream);
+
+/*
+ * Combine n_shards partial blocks (HOST memory, contiguous, in shard order,
+ * each 6 doubles, or 6 + 2 n_param for what = AMP4D_EVAL_NLL_GRAD) into the
+ * evaluation of the union (host code only, no GPU call):
+ *   I = sum T / sum M,  NLL = -2 [sum ln S + sum ln(pq) - N ln I],
+ *   dNLL/dtheta = -2 [sum d ln S - N sum dT / sum T].
+ * out (HOST) receives the amp4d_enqueue_eval layout: [0] NLL (+inf on a domain
+ * error), [1] sum ln S, [2] sum ln(pq), [3] I, [4] N, [5] status bits, [6 ..]
+ * the gradient.  Sums run over the shards in the order given with Neumaier
+ * compensation, so the result depends on that order only through rounding and
+ * is identical on every caller that passes the same blocks.
+ * Errors: ARG (bad arguments, a negative count, a shard with status bit 2),
+ * STATE (no points in any shard), DOMAIN (status bit 1, I <= 0); message in
+ * amp4d_shard_last_error (per calling thread).
+ */
+amp4d_status amp4d_combine_partials(const double *parts, int n_shards, int n_param, int what,
+                                    double *out);
+const char *amp4d_shard_last_error(void);
+
+/*
  * Normalisation Gram matrix G = sum_n w_n sum_xi x x^T of the real 2K-vectors
  * x = (Re B_0, Im B_0, Re B_1, ...) over the normalisation points (State-of-
  * the-art section: numerical normalisation; Eq. 5, 12 for B), so that

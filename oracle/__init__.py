@@ -64,6 +64,8 @@ def lib():
             L.or_nll.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d, _d,
                                  C.c_int64, C.c_double, _d, _d, _d]
             L.or_gram.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, _d, C.c_int64, _d]
+            L.or_partials.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d,
+                                      _d, C.c_int64, C.c_double, C.c_int, _d]
             L.or_generate.restype = C.c_int64
             L.or_generate.argtypes = [C.c_void_p, _d, C.c_uint64, C.c_int64, C.c_int64,
                                       C.c_int64, _f, _f, _f, _f, _d]
@@ -232,6 +234,21 @@ class Model:
                           len(nm[0]), float(volume), C.byref(out), _pd(g) if grad else None,
                           _pd(aux))
         return out.value, g, aux, rc
+
+    def partials(self, params, events, norm_pts, w=None, volume=None, grad=True):
+        """Sums of one shard (either set may be empty): [sum ln S, sum ln pq, N,
+        T = V sum w S, M, bad, d sum ln S (P), dT (P)]; I = sum T / sum M over shards."""
+        import workloads as W
+        volume = W.BOX_VOLUME if volume is None else volume
+        ev = [_f64(a) for a in events]
+        nm = [_f64(a) for a in norm_pts]
+        wf = _f64(w) if w is not None else None
+        out = np.zeros(6 + (2 * self.n_params if grad else 0))
+        pr = _f64(params)
+        lib().or_partials(self.h, _pd(pr), *(_pd(a) for a in ev), len(ev[0]),
+                          *(_pd(a) for a in nm), _pd(wf) if wf is not None else None,
+                          len(nm[0]), float(volume), 1 if grad else 0, _pd(out))
+        return out
 
     def gram(self, params, pts, w=None):
         m, cK, cpsi, phi = (_f64(a) for a in pts)

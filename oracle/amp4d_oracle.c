@@ -729,6 +729,43 @@ int or_nll(const or_model *mo, const double *params, const double *m, const doub
     return 0;
 }
 
+/*
+ * The sums of one shard of a fit whose data events and normalisation points are
+ * split into shards: -2 ln L of the unbinned fit needs, over the union,
+ * sum ln S, sum ln(p q), N, and I = V sum w S / M, so per shard
+ *   out[0] sum ln S, [1] sum ln(p q), [2] N, [3] T = V sum_n w_n S_n, [4] M,
+ *   [5] 1 if a data event has S <= 0 or p q <= 0, else 0,
+ *   [6 .. 6+NP) d(sum ln S)/dtheta, [6+NP .. 6+2NP) dT/dtheta  (grad != 0).
+ * Either set may be empty (n = 0 or n_mc = 0 gives zero sums).
+ */
+int or_partials(const or_model *mo, const double *params, const double *m, const double *cK,
+                const double *cpsi, const double *phi, int64_t n, const double *nm,
+                const double *ncK, const double *ncpsi, const double *nphi, const double *nw,
+                int64_t n_mc, double volume, int grad, double *out)
+{
+    const int NP = or_num_params(mo);
+    double sl = 0.0, slpq = 0.0, s = 0.0;
+    double *gd = (double *)calloc(NP > 0 ? NP : 1, sizeof(double));
+    double *gs = (double *)calloc(NP > 0 ? NP : 1, sizeof(double));
+    int rc = 0;
+    if (n > 0) rc = accumulate(mo, params, 0, m, cK, cpsi, phi, NULL, n, grad, &sl, &slpq, gd);
+    if (n_mc > 0) accumulate(mo, params, 1, nm, ncK, ncpsi, nphi, nw, n_mc, grad, &s, NULL, gs);
+    out[0] = sl;
+    out[1] = slpq;
+    out[2] = (double)n;
+    out[3] = volume * s;
+    out[4] = (double)n_mc;
+    out[5] = rc != 0 ? 1.0 : 0.0;
+    if (grad)
+        for (int i = 0; i < NP; ++i) {
+            out[6 + i] = gd[i];
+            out[6 + NP + i] = volume * gs[i];
+        }
+    free(gd);
+    free(gs);
+    return rc;
+}
+
 /* Gram matrix G = sum_n w_n sum_xi x x^T of the real 2K-vectors
  * x = (Re B_0, Im B_0, Re B_1, ...), G stored row-major 2K x 2K. */
 int or_gram(const or_model *mo, const double *params, const double *m, const double *cK,

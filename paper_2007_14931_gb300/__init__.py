@@ -91,6 +91,25 @@ def mlp_loss_grad_noalloc(theta_dev, xd, xu, out_dev, stream=None):
         raise Amp4dError(rc, amp4d_noalloc_last_error().decode())
 
 
+def combine_partials(parts, what=None):
+    """Evaluation of the union of shards from their partial blocks (rows, in shard
+    order): returns (nll, gradient or None, out) with out in the enqueue_eval layout.
+    Raises Amp4dError on a domain error, like Model.eval_nll."""
+    parts = np.ascontiguousarray(np.atleast_2d(parts), dtype=np.float64)
+    n_shards, width = parts.shape
+    if what is None:
+        what = AMP4D_EVAL_NLL if width == 6 else AMP4D_EVAL_NLL_GRAD
+    n_param = (width - 6) // 2 if what == AMP4D_EVAL_NLL_GRAD else 0
+    if width != 6 + 2 * n_param:
+        raise ValueError("partial blocks of width %d do not match what=%d" % (width, what))
+    out = np.zeros(6 + n_param)
+    rc = amp4d_combine_partials(parts.ctypes.data_as(_d), n_shards, n_param, what,
+                                out.ctypes.data_as(_d))
+    if rc != 0:
+        raise Amp4dError(rc, amp4d_shard_last_error().decode())
+    return out[0], (out[6:].copy() if what == AMP4D_EVAL_NLL_GRAD else None), out
+
+
 def grid_sample(gcell, nb, alpha, seed, n, masses=None, box=None, stream=None):
     """Sampler of the grid proposal on given cell values: (m, cK, cpsi, phi), w, cell (torch cuda)."""
     import torch
@@ -168,6 +187,10 @@ amp4d_mlp_loss_grad_noalloc = _proto("amp4d_mlp_loss_grad_noalloc", C.c_int,
                                      [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp])
 amp4d_noalloc_last_error = _proto("amp4d_noalloc_last_error", C.c_char_p, [])
 AMP4D_NOALLOC_MAX_ROWS = 4096
+amp4d_eval_partials = _proto("amp4d_eval_partials", C.c_int, [_vp, C.c_int, _d, _d, _vp])
+amp4d_enqueue_partials = _proto("amp4d_enqueue_partials", C.c_int, [_vp, C.c_int, _vp, _vp, _vp])
+amp4d_combine_partials = _proto("amp4d_combine_partials", C.c_int, [_d, C.c_int, C.c_int, C.c_int, _d])
+amp4d_shard_last_error = _proto("amp4d_shard_last_error", C.c_char_p, [])
 amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
 amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
 
@@ -177,7 +200,8 @@ EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "am
             "amp4d_profile_enable", "amp4d_profile_read", "amp4d_build_gram", "amp4d_get_gram",
             "amp4d_gram_selftest", "amp4d_generate", "amp4d_proposal_train",
             "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample",
-            "amp4d_mlp_loss_grad_noalloc", "amp4d_noalloc_last_error"]
+            "amp4d_mlp_loss_grad_noalloc", "amp4d_noalloc_last_error", "amp4d_eval_partials",
+            "amp4d_enqueue_partials", "amp4d_combine_partials", "amp4d_shard_last_error"]
 
 MLP_NUM_PARAMS = 4545
 
@@ -288,6 +312,21 @@ class Model:
         self._check(amp4d_eval_terms(self.h, p.ctypes.data_as(_d), o.ctypes.data_as(_d),
                                      _stream_ptr(stream)))
         return o
+
+    def eval_partials(self, params, grad=True, stream=None):
+        """Shard partials of this model's events and points (host float64 array of
+        6 or 6 + 2P values; layout in include/amp4d.h)."""
+        p = self._params(params)
+        what = AMP4D_EVAL_NLL_GRAD if grad else AMP4D_EVAL_NLL
+        o = np.zeros(6 + (2 * self.n_params if grad else 0))
+        self._check(amp4d_eval_partials(self.h, what, p.ctypes.data_as(_d), o.ctypes.data_as(_d),
+                                        _stream_ptr(stream)))
+        return o
+
+    def enqueue_partials(self, what, params_dev, out_dev, stream=None):
+        """Enqueue the shard partials with device parameters/outputs (torch float64)."""
+        self._check(amp4d_enqueue_partials(self.h, what, params_dev.data_ptr(), out_dev.data_ptr(),
+                                           _stream_ptr(stream)))
 
     def enqueue_eval(self, what, params_dev, out_dev, stream=None):
         """Enqueue an evaluation with device parameters/outputs (torch float64 tensors)."""

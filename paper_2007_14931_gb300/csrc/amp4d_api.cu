@@ -326,8 +326,9 @@ amp4d_status build_gram(amp4d_model *model, cudaStream_t st)
 }
 
 // Enqueue one evaluation on stream st (no synchronisation).
+// partials: write the shard partials (k_partials layout) instead of the NLL.
 amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params, double *d_out,
-                     cudaStream_t st)
+                     cudaStream_t st, bool partials = false)
 {
     if (model->ev.n == 0 || model->mc.n == 0)
         return fail(model, AMP4D_ERR_STATE, "set_events and set_norm_points must come first");
@@ -368,7 +369,8 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         }
         CK(launch_finish_gram(rd, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
                               model->n_param, (double)model->ev.n, model->ev.lnpq, von, d_params,
-                              model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st));
+                              model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st,
+                              (double)model->mc.n, partials ? 1 : 0));
         CK(mark());
         if (model->prof_on) model->prof_pending.push_back(marks);
         return AMP4D_OK;
@@ -382,9 +384,14 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         CK(mark());
         CK(launch_reduce_cols(model->ev.part, model->ev.grid_grad, model->nslot, rd, st));
         CK(launch_reduce_cols(model->mc.part, model->mc.grid_grad, model->nslot, rn, st));
-        CK(launch_finish(rd, rn, model->d_slot_param, model->d_pscale, model->nslot, model->n_param,
-                         (double)model->ev.n, model->ev.lnpq, model->mc.volume / (double)model->mc.n,
-                         model->d_status, d_out, st));
+        if (partials)
+            CK(launch_partials(rd, rn, model->d_slot_param, model->d_pscale, model->nslot,
+                               model->n_param, (double)model->ev.n, model->ev.lnpq,
+                               (double)model->mc.n, model->mc.volume, model->d_status, d_out, st));
+        else
+            CK(launch_finish(rd, rn, model->d_slot_param, model->d_pscale, model->nslot,
+                             model->n_param, (double)model->ev.n, model->ev.lnpq,
+                             model->mc.volume / (double)model->mc.n, model->d_status, d_out, st));
     } else {
         LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
         CK(launch_eval(ad, 0));
@@ -394,8 +401,14 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         CK(mark());
         CK(launch_reduce_cols(model->ev.part, model->ev.grid_eval, 1, rd, st));
         CK(launch_reduce_cols(model->mc.part, model->mc.grid_eval, 1, rn, st));
-        CK(launch_finish(rd, rn, nullptr, model->d_pscale, 1, 0, (double)model->ev.n, model->ev.lnpq,
-                         model->mc.volume / (double)model->mc.n, model->d_status, d_out, st));
+        if (partials)
+            CK(launch_partials(rd, rn, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
+                               model->ev.lnpq, (double)model->mc.n, model->mc.volume,
+                               model->d_status, d_out, st));
+        else
+            CK(launch_finish(rd, rn, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
+                             model->ev.lnpq, model->mc.volume / (double)model->mc.n,
+                             model->d_status, d_out, st));
     }
     CK(mark());
     if (model->prof_on) model->prof_pending.push_back(marks);
@@ -403,7 +416,8 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
 }
 
 // Synchronous evaluation from host parameters; leaves the output block in h_out.
-amp4d_status run_eval(amp4d_model *model, const double *params, bool with_grad, cudaStream_t st)
+amp4d_status run_eval(amp4d_model *model, const double *params, bool with_grad, cudaStream_t st,
+                      bool partials = false)
 {
     amp4d_status rc = check_params(model, params);
     if (rc) return rc;
@@ -411,9 +425,9 @@ amp4d_status run_eval(amp4d_model *model, const double *params, bool with_grad, 
     std::memcpy(model->h_params, params, model->n_param * sizeof(double));
     CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    rc = enqueue(model, with_grad, model->d_params, model->d_out, st);
+    rc = enqueue(model, with_grad, model->d_params, model->d_out, st, partials);
     if (rc) return rc;
-    const size_t nout = 6 + (with_grad ? model->n_param : 0);
+    const size_t nout = 6 + (with_grad ? (partials ? 2 : 1) * model->n_param : 0);
     CK(cudaMemcpyAsync(model->h_out, model->d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (((unsigned)model->h_out[5]) & 2u) return fail(model, AMP4D_ERR_ARG, "invalid parameters");
@@ -521,8 +535,8 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
     }
     if (e == cudaSuccess) e = cudaMalloc(&model->d_slot_param, model->nslot * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_red, 2 * model->nslot * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&model->d_out, (6 + model->n_param) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&model->h_out, (6 + model->n_param) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_out, (6 + 2 * model->n_param) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&model->h_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_bad, sizeof(unsigned long long));
     if (e == cudaSuccess) {
@@ -670,6 +684,27 @@ amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *para
         return model ? fail(model, AMP4D_ERR_ARG, "bad enqueue arguments") : AMP4D_ERR_ARG;
     CK(cudaSetDevice(model->device));
     return enqueue(model, what == AMP4D_EVAL_NLL_GRAD, params, out, (cudaStream_t)stream);
+}
+
+amp4d_status amp4d_enqueue_partials(amp4d_model *model, int what, const double *params,
+                                    double *out, void *stream)
+{
+    if (!model || !params || !out || (what != AMP4D_EVAL_NLL && what != AMP4D_EVAL_NLL_GRAD))
+        return model ? fail(model, AMP4D_ERR_ARG, "bad enqueue arguments") : AMP4D_ERR_ARG;
+    CK(cudaSetDevice(model->device));
+    return enqueue(model, what == AMP4D_EVAL_NLL_GRAD, params, out, (cudaStream_t)stream, true);
+}
+
+amp4d_status amp4d_eval_partials(amp4d_model *model, int what, const double *params, double *out,
+                                 void *stream)
+{
+    if (!model || !params || !out || (what != AMP4D_EVAL_NLL && what != AMP4D_EVAL_NLL_GRAD))
+        return model ? fail(model, AMP4D_ERR_ARG, "bad partials arguments") : AMP4D_ERR_ARG;
+    const bool g = what == AMP4D_EVAL_NLL_GRAD;
+    amp4d_status rc = run_eval(model, params, g, (cudaStream_t)stream, true);
+    if (rc) return rc;
+    std::memcpy(out, model->h_out, (6 + (g ? 2 * model->n_param : 0)) * sizeof(double));
+    return AMP4D_OK;
 }
 
 amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *stream)

@@ -78,6 +78,39 @@ __global__ void k_finish(const double *__restrict__ rd, const double *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// Shard partials (ln L of the unbinned fit is a sum over events and I a sum over
+// points, so a split of both sets is exactly recombined from these sums):
+// out: [0] sum ln S, [1] sum ln pq, [2] N, [3] T = V sum w S (I = T / M over the
+// union of the shards), [4] M, [5] status bits, [6 .. 6+P) d(sum ln S)/dtheta,
+// [6+P .. 6+2P) dT/dtheta.  No logarithm of I is taken here.
+// ---------------------------------------------------------------------------
+__global__ void k_partials(const double *__restrict__ rd, const double *__restrict__ rn,
+                           const int *__restrict__ slot_param, const double *__restrict__ pscale,
+                           int nslot, int nparam, double n_events, double lnpq, double n_points,
+                           double volume, const unsigned *__restrict__ status,
+                           double *__restrict__ out)
+{
+    if (threadIdx.x == 0) {
+        out[0] = rd[0];
+        out[1] = lnpq;
+        out[2] = n_events;
+        out[3] = volume * rn[0];
+        out[4] = n_points;
+        out[5] = (double)*status;
+    }
+    if (slot_param == nullptr) return;
+    for (int p = threadIdx.x; p < 2 * nparam; p += blockDim.x) out[6 + p] = 0.0;
+    __syncthreads();
+    for (int s = 1 + threadIdx.x; s < nslot; s += blockDim.x) {
+        const int p = slot_param[s];
+        if (p >= 0) {
+            out[6 + p] = pscale[p] * rd[s];
+            out[6 + nparam + p] = volume * pscale[p] * rn[s];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // NLL and gradient with the normalisation from the Gram matrix G (cached path):
 // with the folded couplings c'_k = kappa_k c_k, u = (Re c', -Im c'), v = (Im c',
 // Re c') interleaved, I = vol_over_n (u^T G u + v^T G v) and
@@ -89,7 +122,7 @@ __global__ void k_finish_gram(const double *__restrict__ rd, const int *__restri
                               double n_events, double lnpq, double vol_over_n,
                               const double *__restrict__ params, const double *__restrict__ G,
                               const unsigned *__restrict__ status, double *__restrict__ out,
-                              int with_grad)
+                              int with_grad, double n_points, int partials)
 {
     __shared__ double u[96], v[96], Gu[96], Gv[96];
     __shared__ double Ish;
@@ -110,6 +143,35 @@ __global__ void k_finish_gram(const double *__restrict__ rd, const int *__restri
         Gv[i] = b;
     }
     __syncthreads();
+    if (partials) {
+        // Shard partials (layout of k_partials) with T = V (u^T G u + v^T G v).
+        const double volume = vol_over_n * n_points;
+        if (t == 0) {
+            double q = 0.0;
+            for (int i = 0; i < dim; ++i) q += u[i] * Gu[i] + v[i] * Gv[i];
+            out[0] = rd[0];
+            out[1] = lnpq;
+            out[2] = n_events;
+            out[3] = volume * q;
+            out[4] = n_points;
+            out[5] = (double)*status;
+        }
+        if (!with_grad) return;
+        for (int p = t; p < 2 * nparam; p += blockDim.x) out[6 + p] = 0.0;
+        __syncthreads();
+        for (int s = 1 + t; s < nslot; s += blockDim.x) {
+            const int p = slot_param[s];
+            if (p < 0) continue;
+            out[6 + p] = pscale[p] * rd[s];
+            if (p < dim) {
+                const int k = p >> 1;
+                const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1])
+                                          : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
+                out[6 + nparam + p] = volume * pscale[p] * dq;
+            }
+        }
+        return;
+    }
     if (t == 0) {
         double q = 0.0;
         for (int i = 0; i < dim; ++i) q += u[i] * Gu[i] + v[i] * Gv[i];
@@ -364,10 +426,22 @@ cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_pa
 cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
-                               const unsigned *status, double *out, int with_grad, cudaStream_t s)
+                               const unsigned *status, double *out, int with_grad, cudaStream_t s,
+                               double n_points, int partials)
 {
     k_finish_gram<<<1, 128, 0, s>>>(rd, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
-                                    vol_over_n, params, G, status, out, with_grad);
+                                    vol_over_n, params, G, status, out, with_grad, n_points,
+                                    partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partials(const double *rd, const double *rn, const int *slot_param,
+                            const double *pscale, int nslot, int nparam, double n_events,
+                            double lnpq, double n_points, double volume, const unsigned *status,
+                            double *out, cudaStream_t s)
+{
+    k_partials<<<1, 128, 0, s>>>(rd, rn, slot_param, pscale, nslot, nparam, n_events, lnpq,
+                                 n_points, volume, status, out);
     return cudaGetLastError();
 }
 

@@ -44,7 +44,12 @@ cudaError_t launch_build_table(const ModelStatic *st, const double *params, Mode
 cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
-                               const unsigned *status, double *out, int with_grad, cudaStream_t s);
+                               const unsigned *status, double *out, int with_grad, cudaStream_t s,
+                               double n_points = 0.0, int partials = 0);
+cudaError_t launch_partials(const double *rd, const double *rn, const int *slot_param,
+                            const double *pscale, int nslot, int nparam, double n_events,
+                            double lnpq, double n_points, double volume, const unsigned *status,
+                            double *out, cudaStream_t s);
 
 // Normalisation Gram matrix (amp4d_gram.cu).
 struct GramArgs {
