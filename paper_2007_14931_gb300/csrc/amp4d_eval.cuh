@@ -34,13 +34,13 @@ struct EvState {
     float mZ, invmZ, pZ, qZ;
 };
 
-// Lineshape of internal resonance k for this event: from the basis cache when
-// one is given and the resonance's mass and width are fixed, else computed.
-__device__ __forceinline__ float2 cached_or_computed(const ResDev &rs, const float2 *__restrict__ lc,
-                                                     int64_t lcn, int k, int64_t e, float m,
-                                                     float invm, float p, float q)
+// Lineshape of a resonance for this event: the basis-cache value (loaded up
+// front) when a cache is given and the resonance's mass and width are fixed,
+// else computed.
+__device__ __forceinline__ float2 cached_or_computed(const ResDev &rs, bool have_lc, float2 cached,
+                                                     float m, float invm, float p, float q)
 {
-    if (lc != nullptr && rs.fpos < 0) return __ldg(lc + k * lcn + e);
+    if (have_lc && rs.fpos < 0) return cached;
     return lineshape(rs, m, invm, p, q).A;
 }
 
@@ -68,11 +68,23 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     }
     float2 u[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     const int nK = md.n_res - NZ;
+    // Every cached lineshape of the event is requested before any is used, so
+    // the loads overlap instead of waiting one after another behind the
+    // per-resonance branches.
+    const bool have_lc = lc != nullptr;
+    float2 LK[NK], LZ[NZ > 0 ? NZ : 1];
+    if (have_lc) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            LK[k] = k < nK ? __ldg(lc + k * lcn + e) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) LZ[z] = __ldg(lc + (nK + z) * lcn + e);
+    }
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         if (k < nK) {
             const ResDev &rs = md.res[k];
-            const float2 LA = cached_or_computed(rs, lc, lcn, k, e, m, invm, p, q);
+            const float2 LA = cached_or_computed(rs, have_lc, LK[k], m, invm, p, q);
             float d0, d1;
             wigner_l0(rs.J, cK, sK, d0, d1);
             ev.AK[k] = LA;
@@ -112,7 +124,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
             const ResDev &rs = md.res[nK + z];
-            const float2 LA = cached_or_computed(rs, lc, lcn, nK + z, e, mZ, invmZ, pZ, qZ);
+            const float2 LA = cached_or_computed(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
             float dz0, dz1;
             wigner_l0(rs.J, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
             ev.AZ[z] = LA;
