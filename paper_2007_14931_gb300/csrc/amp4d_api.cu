@@ -125,8 +125,8 @@ void build_slot_map(const amp4d_model *mo, std::vector<int> &map)
             }
         }
         if (r.float_mg) {
-            map[MG0 + 2 * i] = 2 * mo->n_col + 2 * mo->res_fpos[u];
-            map[MG0 + 2 * i + 1] = 2 * mo->n_col + 2 * mo->res_fpos[u] + 1;
+            map[MG0 + 2 * mo->res_fpos[u]] = 2 * mo->n_col + 2 * mo->res_fpos[u];
+            map[MG0 + 2 * mo->res_fpos[u] + 1] = 2 * mo->n_col + 2 * mo->res_fpos[u] + 1;
         }
     }
     for (int z = 0; z < mo->nZ; ++z) {
@@ -137,8 +137,8 @@ void build_slot_map(const amp4d_model *mo, std::vector<int> &map)
         if (eta == 1) { map[Z0 + 4 * z] = 2 * c; map[Z0 + 4 * z + 1] = 2 * c + 1; ++c; }
         if (r.J >= 1) { map[Z0 + 4 * z + 2] = 2 * c; map[Z0 + 4 * z + 3] = 2 * c + 1; }
         if (r.float_mg) {
-            map[MG0 + 2 * (NK + z)] = 2 * mo->n_col + 2 * mo->res_fpos[u];
-            map[MG0 + 2 * (NK + z) + 1] = 2 * mo->n_col + 2 * mo->res_fpos[u] + 1;
+            map[MG0 + 2 * mo->res_fpos[u]] = 2 * mo->n_col + 2 * mo->res_fpos[u];
+            map[MG0 + 2 * mo->res_fpos[u] + 1] = 2 * mo->n_col + 2 * mo->res_fpos[u] + 1;
         }
     }
 }
@@ -235,6 +235,7 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.nz = mo->nZ;
     a.stream = st;
     a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
+    a.nslot = mo->nslot;
     return a;
 }
 
@@ -521,7 +522,7 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
     model->nK = n_res - nz;
     model->n_param = 2 * model->n_col + 2 * model->n_float;
     model->nk_max = nk_bucket(model->nK);
-    model->nslot = grad_num_slots(model->nk_max, nz);
+    model->nslot = grad_num_slots(model->nk_max, nz, model->n_float);
     cudaError_t e = cudaGetDevice(&model->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&model->nsm, cudaDevAttrMultiProcessorCount, model->device);
     if (e == cudaSuccess) e = cudaMalloc(&model->d_md, sizeof(ModelDev));

@@ -50,6 +50,8 @@ struct ResDev {
     float dNhi, dNlo; // d ln(sqrt(KB KR))/dM, KB = P_LB(r^2 p0^2), KR = P_LR(r^2 q0^2)
     float dGhi, dGlo; // d ln(M Gamma)/dM at fixed m
     float iGhi, iGlo; // 1 / G0
+    float pd0[5];     // P_J(c) = sum_i pd0[i] c^i          (d^J_00)
+    float pd1[4];     // P_J'(c) = sum_i pd1[i] c^i         (d1 = -sin P_J')
     int chain, J, LB, LR;
     int col;          // first basis column
     int fpos;         // index among floated resonances, -1 if fixed
@@ -74,8 +76,15 @@ struct ModelStatic {
 struct ModelDev {
     int n_res, n_col, n_float, n_param;
     ResDev res[AMP4D_MAX_RES];
-    float2 c[3 * AMP4D_MAX_RES];   // folded couplings, high part
-    float2 cl[3 * AMP4D_MAX_RES];  // folded couplings, low part
+    float2 c[3 * AMP4D_MAX_RES];   // folded couplings by column, high part
+    float2 cl[3 * AMP4D_MAX_RES];  // folded couplings by column, low part
+    // The same couplings by internal resonance, so that a loop unrolled over
+    // resonances addresses them at fixed offsets: K* k at kc[k][l + 1] for
+    // l = -1, 0, +1 (J = 0: kc[k][1] only); Z z at zc[z][0] (l' = 0) and
+    // zc[z][1] (l' = +-1).  Absent columns hold 0.
+    ResDev zr[2];                  // the Z resonances, res[n_res - NZ + z]
+    float2 kc[AMP4D_MAX_RES][3], kcl[AMP4D_MAX_RES][3];
+    float2 zc[2][2], zcl[2][2];
 };
 
 // ----------------------------------------------------------------------------
@@ -133,30 +142,17 @@ __device__ __forceinline__ float ipow(float x, int n)
 }
 
 // ----------------------------------------------------------------------------
-// Wigner d for J <= 4 from Legendre closed forms, without irrational factors:
+// Wigner d for J <= 4 from the Legendre polynomials, without irrational factors:
 //   d0 = d^J_{00}(c) = P_J(c),
 //   d1 = -s P_J'(c) = sqrt(J (J+1)) d^J_{10}(c),  d^J_{-1,0} = -d^J_{10}.
-// The 1/sqrt(J (J+1)) is folded into the l = +-1 couplings.
+// The 1/sqrt(J (J+1)) is folded into the l = +-1 couplings.  Both polynomials
+// are evaluated by Horner from the resonance's coefficients, so the same
+// instructions serve every J (no branch on the spin).
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void wigner_l0(int J, float c, float s, float &d0, float &d1)
+__device__ __forceinline__ void wigner_l0(const ResDev &r, float c, float s, float &d0, float &d1)
 {
-    const float c2 = c * c;
-    switch (J) {
-    case 0: d0 = 1.0f; d1 = 0.0f; break;
-    case 1: d0 = c; d1 = -s; break;
-    case 2:
-        d0 = fmaf(1.5f, c2, -0.5f);
-        d1 = -s * (3.0f * c);
-        break;
-    case 3:
-        d0 = c * fmaf(2.5f, c2, -1.5f);
-        d1 = -s * fmaf(7.5f, c2, -1.5f);
-        break;
-    default:
-        d0 = fmaf(fmaf(4.375f, c2, -3.75f), c2, 0.375f);
-        d1 = -s * (c * fmaf(17.5f, c2, -7.5f));
-        break;
-    }
+    d0 = fmaf(fmaf(fmaf(fmaf(r.pd0[4], c, r.pd0[3]), c, r.pd0[2]), c, r.pd0[1]), c, r.pd0[0]);
+    d1 = -s * fmaf(fmaf(fmaf(r.pd1[3], c, r.pd1[2]), c, r.pd1[1]), c, r.pd1[0]);
 }
 
 // d^1_{l xi}(theta) for l in {-1, 0, 1}, xi in {+1 (x=0), -1 (x=1)}; the l = 0

@@ -13,11 +13,52 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "amp4d_device.cuh"
 #include "amp4d_launch.h"
 
 namespace amp4d {
+
+// The per-evaluation table as the per-event kernels read it: in the constant
+// bank, so that every field of a resonance of a loop unrolled over resonances
+// is an operand at a fixed address (no shared-memory load per use).  Each
+// translation unit has its own copy; with_const_table fills it on the stream
+// right before a launch.
+static __constant__ ModelDev c_md;
+
+struct ConstTableSync {
+    std::mutex mu;
+    cudaEvent_t done[64] = {};
+};
+static ConstTableSync &const_table_sync()
+{
+    static ConstTableSync s;
+    return s;
+}
+
+// Copies the device table gmd (written by k_build_table on the same stream)
+// into c_md and enqueues launch().  There is one c_md per device, so launches
+// from different streams are serialised: each waits for the previous user's
+// kernels before overwriting the table.
+template <typename Launch>
+static cudaError_t with_const_table(const ModelDev *gmd, cudaStream_t st, Launch &&launch)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    ConstTableSync &sy = const_table_sync();
+    std::lock_guard<std::mutex> lock(sy.mu);
+    if (!sy.done[dev]) e = cudaEventCreateWithFlags(&sy.done[dev], cudaEventDisableTiming);
+    else e = cudaStreamWaitEvent(st, sy.done[dev], 0);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbolAsync(c_md, gmd, sizeof(ModelDev), 0, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = launch();
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(sy.done[dev], st);
+}
 
 
 // Resonances internal order: K* first (at most NK), then Z (exactly NZ).
@@ -25,12 +66,12 @@ template <int NK, int NZ>
 struct EvState {
     float2 a[2];
     float S;
-    float2 AK[NK];
-    float d0[NK], d1[NK];
+    float2 B0[NK], B1[NK];        // K* k: A_k d0 and A_k d1 (l = 0 and l = +1; l = -1 is -B1)
     float2 Psi[3][2];
     float2 AZ[NZ > 0 ? NZ : 1];
     float2 Om0[NZ > 0 ? NZ : 1][2], Om1[NZ > 0 ? NZ : 1][2];
     float m, invm, p, q;          // kept to recompute lineshapes for mass/width derivatives
+    float cK, sK;                 // and the K* helicity angle, for d^J of floated states
     float mZ, invmZ, pZ, qZ;
 };
 
@@ -56,6 +97,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     const float invm = __frcp_rn(m);
     ev.m = m; ev.invm = invm; ev.p = p; ev.q = q;
     const float sK = sqrtf(fmaxf(0.0f, fmaf(-cK, cK, 1.0f)));
+    ev.cK = cK; ev.sK = sK;
     const float spsi = sqrtf(fmaxf(0.0f, fmaf(-cpsi, cpsi, 1.0f)));
     const float cph = r[REC_CPHI], sph = r[REC_SPHI];   // e^{i phi}, FP64 at ingest
     float d1p[3][2];
@@ -86,20 +128,16 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
             const ResDev &rs = md.res[k];
             const float2 LA = cached_or_computed(rs, have_lc, LK[k], m, invm, p, q);
             float d0, d1;
-            wigner_l0(rs.J, cK, sK, d0, d1);
-            ev.AK[k] = LA;
-            ev.d0[k] = d0;
-            ev.d1[k] = d1;
-            if (rs.J == 0) {
-                cfma2(u[1], md.c[rs.col], md.cl[rs.col], cscale(LA, d0));
-            } else {
-                cfma2(u[0], md.c[rs.col], md.cl[rs.col], cscale(LA, -d1));
-                cfma2(u[1], md.c[rs.col + 1], md.cl[rs.col + 1], cscale(LA, d0));
-                cfma2(u[2], md.c[rs.col + 2], md.cl[rs.col + 2], cscale(LA, d1));
-            }
+            wigner_l0(rs, cK, sK, d0, d1);
+            const float2 b0 = cscale(LA, d0), b1 = cscale(LA, d1);
+            ev.B0[k] = b0;
+            ev.B1[k] = b1;
+            // J = 0: the l = +-1 couplings are 0 and d1 = 0, so no branch on J.
+            cfma2(u[0], md.kc[k][0], md.kcl[k][0], make_float2(-b1.x, -b1.y));
+            cfma2(u[1], md.kc[k][1], md.kcl[k][1], b0);
+            cfma2(u[2], md.kc[k][2], md.kcl[k][2], b1);
         } else {
-            ev.AK[k] = make_float2(0.f, 0.f);
-            ev.d0[k] = ev.d1[k] = 0.f;
+            ev.B0[k] = ev.B1[k] = make_float2(0.f, 0.f);
         }
     }
 #pragma unroll
@@ -123,10 +161,10 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
         wigner_1(ctz, stz, d1t);
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
-            const ResDev &rs = md.res[nK + z];
+            const ResDev &rs = md.zr[z];
             const float2 LA = cached_or_computed(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
             float dz0, dz1;
-            wigner_l0(rs.J, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
+            wigner_l0(rs, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
             ev.AZ[z] = LA;
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
@@ -139,8 +177,8 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                 ev.Om0[z][x] = o0;
                 ev.Om1[z][x] = o1;
                 float2 s = make_float2(0.f, 0.f);
-                if (rs.zcol0 >= 0) cfma2(s, md.c[rs.zcol0], md.cl[rs.zcol0], o0);
-                if (rs.zcol1 >= 0) cfma2(s, md.c[rs.zcol1], md.cl[rs.zcol1], o1);
+                if (rs.zcol0 >= 0) cfma2(s, md.zc[z][0], md.zcl[z][0], o0);
+                if (rs.zcol1 >= 0) cfma2(s, md.zc[z][1], md.zcl[z][1], o1);
                 cfma(ev.a[x], LA, s);
             }
         }
@@ -214,9 +252,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
                                                 const float2 *__restrict__ lc)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
-    __shared__ ModelDev md;
+    const ModelDev &md = c_md;   // gmd is its source (copied by with_const_table)
     __shared__ double red[BLOCK / 32];
-    load_model(gmd, &md);
     Kahan acc;
     int esum = 0;
     bool bad = false;
@@ -272,15 +309,15 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
 // Adjoint gradient.  Slots (internal order), after slot 0 = ln S or w S sum:
 //   K* k:  1 + 6k + {0..5}   dS/d(Re, Im) c for l = -1, 0, +1
 //   Z z:   1 + 6NK + 4z + {0..3}  dS/d(Re, Im) c for the l' = 0 and l' = +-1 columns
-//   R:     1 + 6NK + 4NZ + 2R + {0, 1}  dS/dM, dS/dG0 (internal resonance index R)
+//   R:     1 + 6NK + 4NZ + 2 fpos + {0, 1}  dS/dM, dS/dG0 of the floated resonance
+//          with index fpos among the floated ones (no slots for fixed resonances)
 // Every slot is scaled by 1/S (data) or w (normalisation).
 // ---------------------------------------------------------------------------
 template <int NK, int NZ>
 struct Slots {
     static constexpr int K0 = 1;
     static constexpr int Z0 = 1 + 6 * NK;
-    static constexpr int MG0 = 1 + 6 * NK + 4 * NZ;
-    static constexpr int N = 1 + 6 * NK + 4 * NZ + 2 * (NK + NZ);
+    static constexpr int MG0 = 1 + 6 * NK + 4 * NZ;   // + 2 fpos for a floated resonance
 };
 
 // dA/dM and dA/dG0 from Eq. 2-3: A = N / D, D = M^2 - m^2 - i M Gamma(m).  The
@@ -311,16 +348,15 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                    double *__restrict__ part,
                                                    unsigned *__restrict__ status,
-                                                   const float2 *__restrict__ lc)
+                                                   const float2 *__restrict__ lc, int nslot)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     using SL = Slots<NK, NZ>;
-    __shared__ ModelDev md;
+    const ModelDev &md = c_md;   // gmd is its source (copied by with_const_table)
     __shared__ double red[BLOCK / 32];
-    extern __shared__ float gsl[];   // [SL::N][BLOCK]
-    load_model(gmd, &md);
+    extern __shared__ float gsl[];   // [nslot][BLOCK]
     const int tid = threadIdx.x;
-    for (int i = 1; i < SL::N; ++i) gsl[i * BLOCK + tid] = 0.f;
+    for (int i = 1; i < nslot; ++i) gsl[i * BLOCK + tid] = 0.f;
     float *g = gsl + tid;            // g[s * BLOCK] = slot s of this thread
     Kahan acc0;
     int esum = 0;
@@ -346,65 +382,79 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
             acc0.add(w * ev.S);
             scale = 2.0f * w;
         }
-        // v_l = sum_xi conj(a_xi) Psi_{l xi}
-        float2 vl[3];
+        // The scaled amplitudes as_xi = scale a_xi carry the 1/S (data) or w
+        // (normalisation) factor, so every slot update below is two FMAs.
+        float2 as[2];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) as[x] = cscale(ev.a[x], scale);
+        // w_l = sum_xi conj(as_xi) Psi_{l xi}
+        float2 wl[3];
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
             float2 t = make_float2(0.f, 0.f);
-            cfma_conj(t, ev.a[0], ev.Psi[l][0]);
-            cfma_conj(t, ev.a[1], ev.Psi[l][1]);
-            vl[l] = t;
+            cfma_conj(t, as[0], ev.Psi[l][0]);
+            cfma_conj(t, as[1], ev.Psi[l][1]);
+            wl[l] = t;
         }
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             if (k >= nK) continue;
             const ResDev &rs = md.res[k];
-            // z for l = -1, 0, +1: A d_l v_l with d_{-1} = -d1, d_0 = d0, d_{+1} = d1
-            const float dl[3] = {-ev.d1[k], ev.d0[k], ev.d1[k]};
-            float2 y = make_float2(0.f, 0.f);
+            // scale dS/d(Re, Im) c_{k,l} = (Re, -Im) of B_l w_l, with B_{-1} = -B1,
+            // B_0 = B0, B_{+1} = B1 (unused slots of a J = 0 state receive 0).
+            const float2 Bl[3] = {make_float2(-ev.B1[k].x, -ev.B1[k].y), ev.B0[k], ev.B1[k]};
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                if (rs.J == 0 && l != 1) continue;
-                const float2 t = cscale(vl[l], dl[l]);
-                const float2 z = cmul(ev.AK[k], t);
-                g[(SL::K0 + 6 * k + 2 * l) * BLOCK] += scale * z.x;
-                g[(SL::K0 + 6 * k + 2 * l + 1) * BLOCK] -= scale * z.y;
-                if (rs.fpos >= 0) cfma(y, md.c[rs.J == 0 ? rs.col : rs.col + l], t);
+                float &gr = g[(SL::K0 + 6 * k + 2 * l) * BLOCK];
+                float &gi = g[(SL::K0 + 6 * k + 2 * l + 1) * BLOCK];
+                gr = fmaf(Bl[l].x, wl[l].x, fmaf(-Bl[l].y, wl[l].y, gr));
+                gi = fmaf(-Bl[l].x, wl[l].y, fmaf(-Bl[l].y, wl[l].x, gi));
             }
             if (rs.fpos >= 0) {
+                // y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
+                float d0, d1;
+                wigner_l0(rs, ev.cK, ev.sK, d0, d1);
+                float2 y = make_float2(0.f, 0.f);
+                cfma(y, md.kc[k][0], cscale(wl[0], -d1));
+                cfma(y, md.kc[k][1], cscale(wl[1], d0));
+                cfma(y, md.kc[k][2], cscale(wl[2], d1));
                 const LineOut L = lineshape(rs, ev.m, ev.invm, ev.p, ev.q);
                 float2 dM, dG;
                 lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
                 const float2 a = cmul(dM, y), b = cmul(dG, y);
-                g[(SL::MG0 + 2 * k) * BLOCK] += scale * a.x;
-                g[(SL::MG0 + 2 * k + 1) * BLOCK] += scale * b.x;
+                g[(SL::MG0 + 2 * rs.fpos) * BLOCK] += a.x;
+                g[(SL::MG0 + 2 * rs.fpos + 1) * BLOCK] += b.x;
             }
         }
         if constexpr (NZ > 0) {
 #pragma unroll
             for (int z = 0; z < NZ; ++z) {
-                const ResDev &rs = md.res[nK + z];
+                const ResDev &rs = md.zr[z];
                 float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int x = 0; x < 2; ++x) {
-                    cfma_conj(w0, ev.a[x], ev.Om0[z][x]);
-                    cfma_conj(w1, ev.a[x], ev.Om1[z][x]);
+                    cfma_conj(w0, as[x], ev.Om0[z][x]);
+                    cfma_conj(w1, as[x], ev.Om1[z][x]);
                 }
-                const float2 z0 = cmul(ev.AZ[z], w0), z1 = cmul(ev.AZ[z], w1);
-                g[(SL::Z0 + 4 * z + 0) * BLOCK] += scale * z0.x;
-                g[(SL::Z0 + 4 * z + 1) * BLOCK] -= scale * z0.y;
-                g[(SL::Z0 + 4 * z + 2) * BLOCK] += scale * z1.x;
-                g[(SL::Z0 + 4 * z + 3) * BLOCK] -= scale * z1.y;
+                const float2 A = ev.AZ[z];
+                float &g0r = g[(SL::Z0 + 4 * z + 0) * BLOCK];
+                float &g0i = g[(SL::Z0 + 4 * z + 1) * BLOCK];
+                float &g1r = g[(SL::Z0 + 4 * z + 2) * BLOCK];
+                float &g1i = g[(SL::Z0 + 4 * z + 3) * BLOCK];
+                g0r = fmaf(A.x, w0.x, fmaf(-A.y, w0.y, g0r));
+                g0i = fmaf(-A.x, w0.y, fmaf(-A.y, w0.x, g0i));
+                g1r = fmaf(A.x, w1.x, fmaf(-A.y, w1.y, g1r));
+                g1i = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1i));
                 if (rs.fpos >= 0) {
                     float2 y = make_float2(0.f, 0.f);
-                    if (rs.zcol0 >= 0) cfma(y, md.c[rs.zcol0], w0);
-                    if (rs.zcol1 >= 0) cfma(y, md.c[rs.zcol1], w1);
+                    if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
+                    if (rs.zcol1 >= 0) cfma(y, md.zc[z][1], w1);
                     const LineOut L = lineshape(rs, ev.mZ, ev.invmZ, ev.pZ, ev.qZ);
                     float2 dM, dG;
                     lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
                     const float2 a = cmul(dM, y), b = cmul(dG, y);
-                    g[(SL::MG0 + 2 * (NK + z)) * BLOCK] += scale * a.x;
-                    g[(SL::MG0 + 2 * (NK + z) + 1) * BLOCK] += scale * b.x;
+                    g[(SL::MG0 + 2 * rs.fpos) * BLOCK] += a.x;
+                    g[(SL::MG0 + 2 * rs.fpos + 1) * BLOCK] += b.x;
                 }
             }
         }
@@ -418,13 +468,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
     if (tid == 0) {
         double t = 0.0;
         for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww];
-        part[(int64_t)blockIdx.x * SL::N] = t;
+        part[(int64_t)blockIdx.x * nslot] = t;
     }
     // Block sums of every gradient slot in FP64, in thread order.
-    for (int s2 = 1 + tid; s2 < SL::N; s2 += BLOCK) {
+    for (int s2 = 1 + tid; s2 < nslot; s2 += BLOCK) {
         double t = 0.0;
         for (int j = 0; j < BLOCK; ++j) t += (double)gsl[s2 * BLOCK + j];
-        part[(int64_t)blockIdx.x * SL::N + s2] = t;
+        part[(int64_t)blockIdx.x * nslot + s2] = t;
     }
 }
 
@@ -434,41 +484,43 @@ constexpr int GRAD_BLOCK = 128;
 template <int NK, int NZ>
 cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
 {
-    switch (mode) {
-    case MODE_SUM_LNS:
-        k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
-        break;
-    case MODE_SUM_WS:
-        k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
-        break;
-    default:
-        k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
-        break;
-    }
-    return cudaGetLastError();
+    return with_const_table(a.md, a.stream, [&]() {
+        switch (mode) {
+        case MODE_SUM_LNS:
+            k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
+            break;
+        case MODE_SUM_WS:
+            k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
+            break;
+        default:
+            k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
+            break;
+        }
+        return cudaGetLastError();
+    });
+}
+
+template <int NK, int NZ, bool NORM>
+cudaError_t launch_grad_k(const LaunchArgs &a)
+{
+    const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, NORM, GRAD_BLOCK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return with_const_table(a.md, a.stream, [&]() {
+        k_grad<NK, NZ, NORM, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
+            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache, a.nslot);
+        return cudaGetLastError();
+    });
 }
 
 template <int NK, int NZ>
 cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
 {
-    const size_t smem = (size_t)Slots<NK, NZ>::N * GRAD_BLOCK * sizeof(float);
-    if (norm) {
-        cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, true, GRAD_BLOCK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_grad<NK, NZ, true, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, false, GRAD_BLOCK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_grad<NK, NZ, false, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache);
-    }
-    return cudaGetLastError();
+    return norm ? launch_grad_k<NK, NZ, true>(a) : launch_grad_k<NK, NZ, false>(a);
 }
 
 // Basis cache: A'_R (Eq. 2-3 without its column constant) of every resonance for

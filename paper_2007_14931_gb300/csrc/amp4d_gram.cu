@@ -181,12 +181,12 @@ __device__ __forceinline__ void for_each_basis(const ModelDev &md, const float *
     for (int k = 0; k < NK; ++k) {
         if (k >= nK) continue;
         const ResDev &rs = md.res[k];
-        const float dl[3] = {-ev.d1[k], ev.d0[k], ev.d1[k]};
+        const float2 Bl[3] = {make_float2(-ev.B1[k].x, -ev.B1[k].y), ev.B0[k], ev.B1[k]};
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
             if (rs.J == 0 && l != 1) continue;
             const int col = rs.J == 0 ? rs.col : rs.col + l;
-            const float2 t = cscale(ev.AK[k], dl[l]);
+            const float2 t = Bl[l];
             fn(col, 0, cmul(t, ev.Psi[l][0]));
             fn(col, 1, cmul(t, ev.Psi[l][1]));
         }
@@ -194,7 +194,7 @@ __device__ __forceinline__ void for_each_basis(const ModelDev &md, const float *
     if constexpr (NZ > 0) {
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
-            const ResDev &rs = md.res[nK + z];
+            const ResDev &rs = md.zr[z];
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
                 if (rs.zcol0 >= 0) fn(rs.zcol0, x, cmul(ev.AZ[z], ev.Om0[z][x]));

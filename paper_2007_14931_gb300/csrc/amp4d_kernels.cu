@@ -8,7 +8,7 @@
 
 namespace amp4d {
 
-int grad_num_slots(int nk_max, int nz) { return 1 + 6 * nk_max + 4 * nz + 2 * (nk_max + nz); }
+int grad_num_slots(int nk_max, int nz, int n_float) { return 1 + 6 * nk_max + 4 * nz + 2 * n_float; }
 
 // ---------------------------------------------------------------------------
 // Deterministic column sums of per-block partials: block j sums column j over
@@ -307,6 +307,17 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         d.dNhi = (float)dN; d.dNlo = (float)(dN - (double)d.dNhi);
         d.dGhi = (float)dG; d.dGlo = (float)(dG - (double)d.dGhi);
         d.iGhi = (float)iG; d.iGlo = (float)(iG - (double)d.iGhi);
+        // Legendre coefficients of P_J and P_J' (exact in FP32), lowest power first.
+        {
+            const float P[5][5] = {{1.f, 0.f, 0.f, 0.f, 0.f},
+                                   {0.f, 1.f, 0.f, 0.f, 0.f},
+                                   {-0.5f, 0.f, 1.5f, 0.f, 0.f},
+                                   {0.f, -1.5f, 0.f, 2.5f, 0.f},
+                                   {0.375f, 0.f, -3.75f, 0.f, 4.375f}};
+            const int J = r.J < 0 ? 0 : (r.J > 4 ? 4 : r.J);
+            for (int i = 0; i < 5; ++i) d.pd0[i] = P[J][i];
+            for (int i = 0; i < 4; ++i) d.pd1[i] = (float)(i + 1) * P[J][i + 1];
+        }
         d.chain = r.chain;
         d.J = r.J;
         d.LB = r.LB;
@@ -317,6 +328,15 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         d.zcol0 = r.zcol0;
         d.zcol1 = r.zcol1;
         md->res[t] = d;
+        int zi = -1;   // index among the Z resonances (internal order: K* first)
+        if (r.chain == AMP4D_CHAIN_Z) {
+            zi = 0;
+            for (int i = 0; i < t; ++i) zi += st->res[i].chain == AMP4D_CHAIN_Z ? 1 : 0;
+            md->zr[zi] = d;
+            for (int j = 0; j < 2; ++j) md->zc[zi][j] = md->zcl[zi][j] = make_float2(0.f, 0.f);
+        } else {
+            for (int j = 0; j < 3; ++j) md->kc[t][j] = md->kcl[t][j] = make_float2(0.f, 0.f);
+        }
         // Column constants: sqrt(KB KR) m_B^-LB times 1/sqrt(2) for the l = 0 J/psi
         // factor d^1_{0 xi}, or 1/sqrt(J (J+1)) for the l = +-1 factor d^J_{+-1 0}.
         const double base = sqrt(KB * KR) / powi_d(mB, r.LB);
@@ -339,6 +359,15 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         for (int j = 0; j < ncols; ++j) {
             const int k = cols[j];
             split_store(params[2 * k] * kap[j], params[2 * k + 1] * kap[j], md->c[k], md->cl[k]);
+            if (zi < 0) {
+                const int sl = r.J == 0 ? 1 : j;
+                md->kc[t][sl] = md->c[k];
+                md->kcl[t][sl] = md->cl[k];
+            } else {
+                const int sl = k == r.zcol0 ? 0 : 1;
+                md->zc[zi][sl] = md->c[k];
+                md->zcl[zi][sl] = md->cl[k];
+            }
             pscale[2 * k] = kap[j];
             pscale[2 * k + 1] = kap[j];
         }

@@ -22,10 +22,13 @@ struct LaunchArgs {
     int nk_max, nz;          // template bucket
     cudaStream_t stream;
     const float2 *lcache = nullptr;  // basis cache of the set, or null (recompute)
+    int nslot = 0;                   // gradient slots (grad_num_slots)
 };
 
 int nk_bucket(int nk);
-int grad_num_slots(int nk_max, int nz);
+// Gradient slots: ln S (or w S), 6 per K* of the bucket, 4 per Z, and 2 (mass,
+// width) per floated resonance, in the order of their parameters.
+int grad_num_slots(int nk_max, int nz, int n_float);
 int eval_block();
 int grad_block();
 
