@@ -166,6 +166,16 @@ amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int wh
                                 float *S_out, void *stream);
 
 /*
+ * Normalised PDF of every data event, P(e) = S(e) p(e) q(e) / I (Eq. 5 with
+ * the phase-space density p q; I over the current normalisation points), for
+ * parity checks.  pdf_out is DEVICE memory of n_events FP32 values owned by
+ * the caller.  Synchronous.  Errors: ARG, STATE (no events or points), DOMAIN
+ * (I <= 0), CUDA.
+ */
+amp4d_status amp4d_eval_pdf(amp4d_model *model, const double *params, float *pdf_out,
+                            void *stream);
+
+/*
  * Enqueue one evaluation on the stream without synchronising (same arithmetic
  * as amp4d_eval_nll / amp4d_eval_nll_grad).  params: DEVICE memory,
  * amp4d_num_params doubles.  out: DEVICE memory of 6 + amp4d_num_params doubles

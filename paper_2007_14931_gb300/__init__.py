@@ -169,6 +169,7 @@ amp4d_eval_nll_grad = _proto("amp4d_eval_nll_grad", C.c_int, [_vp, _d, _d, _d, _
 amp4d_eval_terms = _proto("amp4d_eval_terms", C.c_int, [_vp, _d, _d, _vp])
 amp4d_eval_density = _proto("amp4d_eval_density", C.c_int, [_vp, _d, C.c_int, _vp, _vp])
 amp4d_enqueue_eval = _proto("amp4d_enqueue_eval", C.c_int, [_vp, C.c_int, _vp, _vp, _vp])
+amp4d_eval_pdf = _proto("amp4d_eval_pdf", C.c_int, [_vp, _d, _vp, _vp])
 amp4d_build_gram = _proto("amp4d_build_gram", C.c_int, [_vp, _d, _vp])
 amp4d_get_gram = _proto("amp4d_get_gram", C.c_int, [_vp, _d, _vp])
 amp4d_gram_selftest = _proto("amp4d_gram_selftest", C.c_int, [_vp, C.c_int64, _vp, _vp])
@@ -201,7 +202,8 @@ EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "am
             "amp4d_gram_selftest", "amp4d_generate", "amp4d_proposal_train",
             "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample",
             "amp4d_mlp_loss_grad_noalloc", "amp4d_noalloc_last_error", "amp4d_eval_partials",
-            "amp4d_enqueue_partials", "amp4d_combine_partials", "amp4d_shard_last_error"]
+            "amp4d_enqueue_partials", "amp4d_combine_partials", "amp4d_shard_last_error",
+            "amp4d_eval_pdf"]
 
 MLP_NUM_PARAMS = 4545
 
@@ -387,4 +389,13 @@ class Model:
             out = torch.empty(n, dtype=torch.float32, device="cuda")
         self._check(amp4d_eval_density(self.h, p.ctypes.data_as(_d), which, out.data_ptr(),
                                        _stream_ptr(stream)))
+        return out
+
+    def eval_pdf(self, params, out=None, stream=None):
+        """Normalised PDF S p q / I of every data event (torch cuda float32)."""
+        import torch
+        p = self._params(params)
+        if out is None:
+            out = torch.empty(self.n_events, dtype=torch.float32, device="cuda")
+        self._check(amp4d_eval_pdf(self.h, p.ctypes.data_as(_d), out.data_ptr(), _stream_ptr(stream)))
         return out

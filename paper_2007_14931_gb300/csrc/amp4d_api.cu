@@ -678,6 +678,21 @@ amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int wh
     return AMP4D_OK;
 }
 
+amp4d_status amp4d_eval_pdf(amp4d_model *model, const double *params, float *pdf_out, void *stream)
+{
+    if (!model || !params || !pdf_out) return AMP4D_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    amp4d_status rc = run_eval(model, params, false, st);   // I over the current points
+    if (rc) return rc;
+    const double I = model->h_out[3];
+    if (!(I > 0.0) || !std::isfinite(I)) return fail(model, AMP4D_ERR_DOMAIN, "I <= 0");
+    rc = amp4d_eval_density(model, params, 0, pdf_out, stream);
+    if (rc) return rc;
+    CK(launch_pdf_scale(model->ev.rec, model->ev.npad, model->ev.n, 1.0 / I, pdf_out, st));
+    CK(cudaStreamSynchronize(st));
+    return AMP4D_OK;
+}
+
 amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *params, double *out,
                                 void *stream)
 {

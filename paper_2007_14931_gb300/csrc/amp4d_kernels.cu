@@ -1,5 +1,6 @@
 // Reductions, the final NLL/gradient assembly, the per-evaluation resonance
 // table, and the dispatch of the per-event kernels to their instantiations.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -433,6 +434,24 @@ cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc)
     case 16: return launch_lcache_nk<16>(a, lc);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// PDF of Eq. 5 with the phase-space density: P(e) = S(e) p(e) q(e) / I, in
+// place over S (FP32, n events).
+__global__ void k_pdf_scale(const float *__restrict__ rec, int64_t npad, int64_t n, float inv_I,
+                            float *__restrict__ S)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        S[e] = S[e] * rec[REC_P * npad + e] * rec[REC_Q * npad + e] * inv_I;
+}
+
+cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double inv_I, float *S,
+                             cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_pdf_scale<<<(int)std::max<int64_t>(1, blocks), 256, 0, s>>>(rec, npad, n, (float)inv_I, S);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *out,

@@ -37,6 +37,8 @@ cudaError_t launch_grad(const LaunchArgs &a, bool norm);
 cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc);
 cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *out,
                                cudaStream_t s);
+cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double inv_I, float *S,
+                             cudaStream_t s);
 cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_param,
                           const double *pscale, int nslot, int nparam, double n_events,
                           double lnpq, double vol_over_n, const unsigned *status, double *out,

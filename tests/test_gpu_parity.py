@@ -247,3 +247,21 @@ def test_density_bias(A):
     sem = np.sqrt(np.sum((rel - bias) ** 2 * w * w)) / np.sum(w)
     print("weighted S bias %.3e +- %.1e, unweighted %.3e" % (bias, sem, rel.mean()))
     assert abs(bias) < 5e-9 + 4 * sem
+
+
+@pytest.mark.parametrize("name", ["tiny", "kstar10_z"])
+def test_pdf_parity(A, name):
+    """P(e) = S p q / I per data event (Eq. 5 with the phase-space density): the
+    oracle's S and p q over its own I, per event, with the per-event density
+    tolerance and I to 1e-8."""
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, name, 20_003, 40_009)
+    P = gm.eval_pdf(p).cpu().numpy().astype(np.float64)
+    S_o, pq_o = om.density(p, ev)
+    I_o = om.norm(p, nm)
+    P_o = S_o * pq_o / I_o
+    B, _ = om.basis(p, ev)
+    mag = np.sum(np.sum(np.abs(c[None, :, None] * B), axis=1) ** 2, axis=1)
+    good = mag / S_o <= 100
+    err = np.abs(P - P_o)
+    assert np.all(err[good] <= 2e-5 * P_o[good]), np.max(err[good] / P_o[good])
+    assert np.all(err[~good] <= 2e-5 * mag[~good] * pq_o[~good] / I_o)

@@ -418,6 +418,26 @@ def test_gradient_phase_and_scale_identities():
     assert abs(np.sum(c.real * gr + c.imag * gi)) < 1e-10 * scale
 
 
+def test_nll_sums_match_exact_serial_sums():
+    """The compensated, blocked OpenMP reduction of sum ln S, sum ln(p q) and
+    sum p q S against correctly rounded serial sums (math.fsum) of the per-event
+    values, and -2 ln L written from those sums (the unbinned likelihood of the
+    Introduction with I = V/N sum w S)."""
+    mo, c, p, ev, nm = _setup(n=9001, n_mc=12007)
+    nll, _, aux, rc = mo.nll(p, ev, nm)
+    assert rc == 0
+    S, pq = mo.density(p, ev)
+    Sn, pqn = mo.density(p, nm)
+    l_exact = math.fsum(np.log(S))
+    lpq_exact = math.fsum(np.log(pq))
+    I_exact = W.BOX_VOLUME / len(nm[0]) * math.fsum(pqn * Sn)
+    assert aux[0] == pytest.approx(l_exact, rel=1e-14, abs=1e-9)
+    assert aux[1] == pytest.approx(lpq_exact, rel=1e-14, abs=1e-9)
+    assert aux[2] == pytest.approx(I_exact, rel=1e-14)
+    nll_exact = -2.0 * (l_exact + lpq_exact - len(ev[0]) * math.log(I_exact))
+    assert nll == pytest.approx(nll_exact, rel=1e-13)
+
+
 def test_nll_domain_error_on_zero_density():
     mo, c, p, ev, nm = _setup("tiny", n=50, n_mc=100, float_names=())
     p0 = np.zeros_like(p)
