@@ -78,6 +78,7 @@ struct amp4d_model {
     int *d_gram_err = nullptr;
     int gram_grid = 0;
     bool gram_valid = false;
+    bool table_built = false;    // one full table build enqueued (all masses fixed)
     // learned proposal
     float *d_th = nullptr, *d_am = nullptr, *d_av = nullptr;   // FP32 master weights, Adam moments
     __nv_bfloat16 *d_wb = nullptr;                              // BF16 weights
@@ -218,6 +219,17 @@ amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const flo
     return AMP4D_OK;
 }
 
+// The per-evaluation table: a full FP64 build the first time, and always when a
+// mass or width floats; afterwards only the folded couplings are rewritten.
+cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t st)
+{
+    const bool fast = mo->n_float == 0 && mo->table_built;
+    cudaError_t e = launch_build_table(mo->d_static, d_params, mo->d_md, mo->d_pscale, mo->d_status,
+                                       st, fast);
+    if (e == cudaSuccess && mo->n_float == 0) mo->table_built = true;
+    return e;
+}
+
 LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cudaStream_t st,
                     int grid)
 {
@@ -297,8 +309,7 @@ amp4d_status build_gram(amp4d_model *model, cudaStream_t st)
         CK(cudaMalloc(&model->d_gram_err, sizeof(int)));
     }
     CK(cudaMemsetAsync(model->d_gram_err, 0, sizeof(int), st));
-    CK(launch_build_table(model->d_static, model->d_params, model->d_md, model->d_pscale,
-                          model->d_status, st));
+    CK(enqueue_table(model, model->d_params, st));
     GramArgs g{};
     g.rec = model->mc.rec;
     g.npad = model->mc.npad;
@@ -341,7 +352,7 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         return cudaEventRecord(e, st);
     };
     CK(mark());
-    CK(launch_build_table(model->d_static, d_params, model->d_md, model->d_pscale, model->d_status, st));
+    CK(enqueue_table(model, d_params, st));
     if (model->path == AMP4D_PATH_CACHED) {
         amp4d_status rc = ensure_lcache(model, model->ev, st);
         if (rc == AMP4D_OK && !use_gram(model)) rc = ensure_lcache(model, model->mc, st);
@@ -671,7 +682,7 @@ amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int wh
     std::memcpy(model->h_params, params, model->n_param * sizeof(double));
     CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    CK(launch_build_table(model->d_static, model->d_params, model->d_md, model->d_pscale, model->d_status, st));
+    CK(enqueue_table(model, model->d_params, st));
     LaunchArgs a = args_for(model, s, s.part, S_out, st, s.grid_eval);
     CK(launch_eval(a, 2));
     CK(cudaStreamSynchronize(st));
@@ -795,8 +806,7 @@ amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t s
     std::memcpy(model->h_params, params, model->n_param * sizeof(double));
     CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    CK(launch_build_table(model->d_static, model->d_params, model->d_md, model->d_pscale,
-                          model->d_status, st));
+    CK(enqueue_table(model, model->d_params, st));
     const int64_t B = 1 << 22, nscan = 1 << 20;
     const int nrec = model->nZ > 0 ? REC_NZ : REC_NK;
     const int nblk = (int)((B + gen_tile() - 1) / gen_tile());

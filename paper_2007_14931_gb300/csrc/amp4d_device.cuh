@@ -85,6 +85,9 @@ struct ModelDev {
     ResDev zr[2];                  // the Z resonances, res[n_res - NZ + z]
     float2 kc[AMP4D_MAX_RES][3], kcl[AMP4D_MAX_RES][3];
     float2 zc[2][2], zcl[2][2];
+    // Where column k's coupling is copied: K* (t << 2 | slot) or Z (0x100 | z << 2 | slot).
+    int col_dst[3 * AMP4D_MAX_RES];
+    int static_bad;                // a fixed resonance has no valid pole constants
 };
 
 // ----------------------------------------------------------------------------

@@ -118,38 +118,56 @@ __global__ void k_partials(const double *__restrict__ rd, const double *__restri
 // dI/dRe c'_k = 2 vol_over_n ((Gu)_2k + (Gv)_2k+1),
 // dI/dIm c'_k = 2 vol_over_n ((Gv)_2k - (Gu)_2k+1).  One block; fixed order.
 // ---------------------------------------------------------------------------
-__global__ void k_finish_gram(const double *__restrict__ rd, const int *__restrict__ slot_param,
-                              const double *__restrict__ pscale, int nslot, int ncol, int nparam,
-                              double n_events, double lnpq, double vol_over_n,
-                              const double *__restrict__ params, const double *__restrict__ G,
-                              const unsigned *__restrict__ status, double *__restrict__ out,
-                              int with_grad, double n_points, int partials)
+__global__ void __launch_bounds__(256) k_finish_gram(
+    const double *__restrict__ rd, const int *__restrict__ slot_param,
+    const double *__restrict__ pscale, int nslot, int ncol, int nparam, double n_events,
+    double lnpq, double vol_over_n, const double *__restrict__ params, const double *__restrict__ G,
+    const unsigned *__restrict__ status, double *__restrict__ out, int with_grad, double n_points,
+    int partials)
 {
+    extern __shared__ double sG[];   // dim x dim, staged once with independent loads
     __shared__ double u[96], v[96], Gu[96], Gv[96];
-    __shared__ double Ish;
+    __shared__ double qsh, Ish;
     const int dim = 2 * ncol, t = threadIdx.x;
+    for (int i = t; i < dim * dim; i += blockDim.x) sG[i] = G[i];
     for (int k = t; k < ncol; k += blockDim.x) {
         const double re = pscale[2 * k] * params[2 * k], im = pscale[2 * k] * params[2 * k + 1];
         u[2 * k] = re; u[2 * k + 1] = -im;
         v[2 * k] = im; v[2 * k + 1] = re;
     }
     __syncthreads();
-    for (int i = t; i < dim; i += blockDim.x) {
+    // (Gu)_i and (Gv)_i: 8 lanes per row, fixed lane-strided order, reduced by
+    // shuffles over the 8 lanes; the loop count is uniform across the block.
+    const int lane8 = t & 7, rows_per_pass = blockDim.x >> 3;
+    for (int base = 0; base < dim; base += rows_per_pass) {
+        const int i = base + (t >> 3);
         double a = 0.0, b = 0.0;
-        for (int j = 0; j < dim; ++j) {
-            a += G[i * dim + j] * u[j];
-            b += G[i * dim + j] * v[j];
+        if (i < dim)
+            for (int j = lane8; j < dim; j += 8) {
+                a = fma(sG[i * dim + j], u[j], a);
+                b = fma(sG[i * dim + j], v[j], b);
+            }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        Gu[i] = a;
-        Gv[i] = b;
+        if (i < dim && lane8 == 0) { Gu[i] = a; Gv[i] = b; }
     }
     __syncthreads();
+    if (t < 32) {
+        double q = 0.0;
+        for (int i = t; i < dim; i += 32) q = fma(u[i], Gu[i], fma(v[i], Gv[i], q));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (t == 0) qsh = q;
+    }
+    __syncthreads();
+    const double q = qsh;
     if (partials) {
         // Shard partials (layout of k_partials) with T = V (u^T G u + v^T G v).
         const double volume = vol_over_n * n_points;
         if (t == 0) {
-            double q = 0.0;
-            for (int i = 0; i < dim; ++i) q += u[i] * Gu[i] + v[i] * Gv[i];
             out[0] = rd[0];
             out[1] = lnpq;
             out[2] = n_events;
@@ -174,8 +192,6 @@ __global__ void k_finish_gram(const double *__restrict__ rd, const int *__restri
         return;
     }
     if (t == 0) {
-        double q = 0.0;
-        for (int i = 0; i < dim; ++i) q += u[i] * Gu[i] + v[i] * Gv[i];
         const double I = vol_over_n * q;
         unsigned st = *status;
         const double nll = -2.0 * (rd[0] + lnpq - n_events * log(I));
@@ -188,17 +204,17 @@ __global__ void k_finish_gram(const double *__restrict__ rd, const int *__restri
         out[5] = (double)st;
         Ish = st ? 0.0 : I;
     }
-    __syncthreads();
     if (!with_grad) return;
-    const double I = Ish;
+    __syncthreads();
+    const double Iv = Ish;
     for (int p = t; p < nparam; p += blockDim.x) out[6 + p] = 0.0;
     __syncthreads();
     for (int s = 1 + t; s < nslot; s += blockDim.x) {
         const int p = slot_param[s];
-        if (p < 0 || p >= dim || I == 0.0) continue;
+        if (p < 0 || p >= dim || Iv == 0.0) continue;
         const int k = p >> 1;
         const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1]) : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
-        out[6 + p] = -2.0 * pscale[p] * (rd[s] - n_events * vol_over_n * dq / I);
+        out[6 + p] = -2.0 * pscale[p] * (rd[s] - n_events * vol_over_n * dq / Iv);
     }
 }
 
@@ -259,8 +275,8 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
                               unsigned *__restrict__ status)
 {
     const int t = threadIdx.x;
-    __shared__ int bad;
-    if (t == 0) bad = 0;
+    __shared__ int bad, sbad;   // any invalid input; invalid pole constants of a fixed resonance
+    if (t == 0) bad = sbad = 0;
     __syncthreads();
     const int nres = st->n_res, ncol = st->n_col, npar = st->n_param;
     for (int i = t; i < npar; i += blockDim.x) {
@@ -276,6 +292,7 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         }
         if (!(M > 0.0) || !(G0 > 0.0)) {
             atomicOr(&bad, 1);
+            if (r.fpos < 0) atomicOr(&sbad, 1);
             M = r.M;
             G0 = r.G0;
         }
@@ -284,7 +301,10 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         if (r.chain == AMP4D_CHAIN_KSTAR) { d1 = st->mK; d2 = st->mpi; sp = st->mpsi; }
         else { d1 = st->mpsi; d2 = st->mpi; sp = st->mK; }
         const double p0 = two_body_d(mB, M, sp), q0 = two_body_d(M, d1, d2);
-        if (!(q0 > 0.0)) atomicOr(&bad, 1);
+        if (!(q0 > 0.0)) {
+            atomicOr(&bad, 1);
+            if (r.fpos < 0) atomicOr(&sbad, 1);
+        }
         const double r2 = r.r * r.r;
         const double z0B = r2 * p0 * p0, z0R = r2 * q0 * q0;
         const double KB = bw_poly_d(r.LB, z0B), KR = bw_poly_d(r.LR, z0R);
@@ -364,10 +384,12 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
                 const int sl = r.J == 0 ? 1 : j;
                 md->kc[t][sl] = md->c[k];
                 md->kcl[t][sl] = md->cl[k];
+                md->col_dst[k] = (t << 2) | sl;
             } else {
                 const int sl = k == r.zcol0 ? 0 : 1;
                 md->zc[zi][sl] = md->c[k];
                 md->zcl[zi][sl] = md->cl[k];
+                md->col_dst[k] = 0x100 | (zi << 2) | sl;
             }
             pscale[2 * k] = kap[j];
             pscale[2 * k + 1] = kap[j];
@@ -380,7 +402,44 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         md->n_param = npar;
     }
     __syncthreads();
-    if (t == 0) *status = bad ? 2u : 0u;
+    if (t == 0) {
+        md->static_bad = sbad;
+        *status = bad ? 2u : 0u;
+    }
+}
+
+// Per-evaluation update when no mass or width floats: every pole constant and
+// column constant kappa_k (kept in pscale) is unchanged since the last full
+// build, so only the folded couplings c'_k = kappa_k c_k are rewritten, in the
+// same FP64 arithmetic as k_build_table (identical bits).
+__global__ void k_update_couplings(const ModelStatic *__restrict__ st, const double *__restrict__ params,
+                                   ModelDev *__restrict__ md, const double *__restrict__ pscale,
+                                   unsigned *__restrict__ status)
+{
+    const int t = threadIdx.x;
+    __shared__ int bad;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    const int ncol = st->n_col, npar = st->n_param;
+    for (int i = t; i < npar; i += blockDim.x)
+        if (!isfinite(params[i])) atomicOr(&bad, 1);
+    for (int k = t; k < ncol; k += blockDim.x) {
+        const double kap = pscale[2 * k];
+        float2 hi, lo;
+        split_store(params[2 * k] * kap, params[2 * k + 1] * kap, hi, lo);
+        md->c[k] = hi;
+        md->cl[k] = lo;
+        const int dst = md->col_dst[k], sl = dst & 3;
+        if (dst & 0x100) {
+            md->zc[(dst >> 2) & 3][sl] = hi;
+            md->zcl[(dst >> 2) & 3][sl] = lo;
+        } else {
+            md->kc[dst >> 2][sl] = hi;
+            md->kcl[dst >> 2][sl] = lo;
+        }
+    }
+    __syncthreads();
+    if (t == 0) *status = (bad || md->static_bad) ? 2u : 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -477,9 +536,15 @@ cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const do
                                const unsigned *status, double *out, int with_grad, cudaStream_t s,
                                double n_points, int partials)
 {
-    k_finish_gram<<<1, 128, 0, s>>>(rd, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
-                                    vol_over_n, params, G, status, out, with_grad, n_points,
-                                    partials);
+    const size_t smem = (size_t)4 * ncol * ncol * sizeof(double);   // dim x dim
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_finish_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_finish_gram<<<1, 256, smem, s>>>(rd, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
+                                       vol_over_n, params, G, status, out, with_grad, n_points,
+                                       partials);
     return cudaGetLastError();
 }
 
@@ -494,9 +559,13 @@ cudaError_t launch_partials(const double *rd, const double *rn, const int *slot_
 }
 
 cudaError_t launch_build_table(const ModelStatic *st, const double *params, ModelDev *md,
-                               double *pscale, unsigned *status, cudaStream_t s)
+                               double *pscale, unsigned *status, cudaStream_t s,
+                               bool couplings_only)
 {
-    k_build_table<<<1, 64, 0, s>>>(st, params, md, pscale, status);
+    if (couplings_only)
+        k_update_couplings<<<1, 64, 0, s>>>(st, params, md, pscale, status);
+    else
+        k_build_table<<<1, 64, 0, s>>>(st, params, md, pscale, status);
     return cudaGetLastError();
 }
 

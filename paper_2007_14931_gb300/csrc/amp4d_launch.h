@@ -44,8 +44,11 @@ cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_pa
                           double lnpq, double vol_over_n, const unsigned *status, double *out,
                           cudaStream_t s);
 
+// couplings_only: refresh the folded couplings of a table whose masses and
+// widths are all fixed and which has had one full build.
 cudaError_t launch_build_table(const ModelStatic *st, const double *params, ModelDev *md,
-                               double *pscale, unsigned *status, cudaStream_t s);
+                               double *pscale, unsigned *status, cudaStream_t s,
+                               bool couplings_only = false);
 cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
