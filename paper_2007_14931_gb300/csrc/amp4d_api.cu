@@ -208,10 +208,9 @@ amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const flo
         return fail(model, AMP4D_ERR_INPUT, buf);
     }
     s.lnpq = lnpq;
-    const int64_t ngroups = npad / 4;
-    s.grid_eval = (int)std::max<int64_t>(1, std::min<int64_t>((ngroups + eval_block() - 1) / eval_block(),
+    s.grid_eval = (int)std::max<int64_t>(1, std::min<int64_t>((n + eval_block() - 1) / eval_block(),
                                                               (int64_t)model->nsm * 4));
-    s.grid_grad = (int)std::max<int64_t>(1, std::min<int64_t>((ngroups + grad_block() - 1) / grad_block(),
+    s.grid_grad = (int)std::max<int64_t>(1, std::min<int64_t>((n + grad_block() - 1) / grad_block(),
                                                               (int64_t)model->nsm * 4));
     s.part_cap = (size_t)std::max(s.grid_eval, s.grid_grad) * model->nslot;
     CK(cudaMalloc(&s.part, s.part_cap * sizeof(double)));

@@ -1,8 +1,8 @@
 // Per-event amplitude, likelihood and adjoint-gradient kernel templates.
 //
-// One thread handles four consecutive events per step (float4 loads of every
+// One thread handles one event per iteration (coalesced scalar loads of every
 // record), grid-stride over the event set.  Per event, in FP32 registers:
-//   lineshapes A_R (Eq. 2-3) with the resonance table in shared memory,
+//   lineshapes A_R (Eq. 2-3), from the basis cache for fixed resonances,
 //   d^J_{l0}(theta_K*), e^{i l phi} d^1_{l xi}(theta_psi) (Eq. 4),
 //   the Z-chain factors (Eq. 10-11) from precomputed Z-frame angles,
 //   a_xi = sum_k c_k B_k,xi and S = |a_+|^2 + |a_-|^2 (Eq. 5, 12).
@@ -229,17 +229,6 @@ __device__ __forceinline__ void load_model(const ModelDev *g, ModelDev *s)
     __syncthreads();
 }
 
-template <int NREC>
-__device__ __forceinline__ void load4(const float *__restrict__ rec, int64_t npad, int64_t g,
-                                      float v[4][NREC])
-{
-#pragma unroll
-    for (int k = 0; k < NREC; ++k) {
-        const float4 t = __ldg(reinterpret_cast<const float4 *>(rec + k * npad) + g);
-        v[0][k] = t.x; v[1][k] = t.y; v[2][k] = t.z; v[3][k] = t.w;
-    }
-}
-
 // MODE_SUM_LNS: data sum of ln S; MODE_SUM_WS: normalisation sum of w S;
 // MODE_WRITE: S per event to out.
 enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
@@ -257,45 +246,25 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
     Kahan acc;
     int esum = 0;
     bool bad = false;
-    const int64_t ngroups = npad >> 2;
-    for (int64_t g = blockIdx.x * (int64_t)BLOCK + threadIdx.x; g < ngroups;
-         g += (int64_t)gridDim.x * BLOCK) {
-        float v[4][NREC];
-        load4<NREC>(rec, npad, g, v);
-        float wv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (MODE == MODE_SUM_WS) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(rec + wrec * npad) + g);
-            wv[0] = t.x; wv[1] = t.y; wv[2] = t.z; wv[3] = t.w;
-        }
-        float Sv[4];
-#pragma unroll 1
-        for (int j = 0; j < 4; ++j) {
-            EvState<NK, NZ> ev;
-            eval_event<NK, NZ>(md, v[j], ev, lc, npad, 4 * g + j);
-            Sv[j] = ev.S;
-        }
+    // One event per thread and iteration, coalesced scalar loads of every record.
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * BLOCK) {
+        float v[NREC];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t e = 4 * g + j;
-            if (e >= n) break;
-            if (MODE == MODE_SUM_LNS) {
-                if (!(Sv[j] > 0.0f)) { bad = true; continue; }
-                int ex;
-                float mant = frexpf(Sv[j], &ex);
-                if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
-                acc.add(logf(mant));
-                esum += ex;
-            } else if (MODE == MODE_SUM_WS) {
-                acc.add(wv[j] * Sv[j]);
-            }
-        }
-        if (MODE == MODE_WRITE) {
-            if (4 * g + 3 < n) {
-                reinterpret_cast<float4 *>(S_out)[g] = make_float4(Sv[0], Sv[1], Sv[2], Sv[3]);
-            } else {
-                for (int j = 0; j < 4; ++j)
-                    if (4 * g + j < n) S_out[4 * g + j] = Sv[j];
-            }
+        for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
+        EvState<NK, NZ> ev;
+        eval_event<NK, NZ>(md, v, ev, lc, npad, e);
+        if (MODE == MODE_SUM_LNS) {
+            if (!(ev.S > 0.0f)) { bad = true; continue; }
+            int ex;
+            float mant = frexpf(ev.S, &ex);
+            if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
+            acc.add(logf(mant));
+            esum += ex;
+        } else if (MODE == MODE_SUM_WS) {
+            acc.add(__ldg(rec + wrec * npad + e) * ev.S);
+        } else {
+            S_out[e] = ev.S;
         }
     }
     if (MODE == MODE_WRITE) return;
@@ -311,14 +280,10 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
 //   Z z:   1 + 6NK + 4z + {0..3}  dS/d(Re, Im) c for the l' = 0 and l' = +-1 columns
 //   R:     1 + 6NK + 4NZ + 2 fpos + {0, 1}  dS/dM, dS/dG0 of the floated resonance
 //          with index fpos among the floated ones (no slots for fixed resonances)
-// Every slot is scaled by 1/S (data) or w (normalisation).
+// Every slot is scaled by 1/S (data) or w (normalisation).  In slot pairs
+// (below): K* k, l at pair 3k + l; Z z at pairs 3NK + 2z + {0, 1}; a floated
+// resonance at pair 3NK + 2NZ + fpos.
 // ---------------------------------------------------------------------------
-template <int NK, int NZ>
-struct Slots {
-    static constexpr int K0 = 1;
-    static constexpr int Z0 = 1 + 6 * NK;
-    static constexpr int MG0 = 1 + 6 * NK + 4 * NZ;   // + 2 fpos for a floated resonance
-};
 
 // dA/dM and dA/dG0 from Eq. 2-3: A = N / D, D = M^2 - m^2 - i M Gamma(m).  The
 // per-resonance derivative constants are double-float: a systematic FP32
@@ -339,9 +304,11 @@ __device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, flo
     dAdG = make_float2(-g.y * s, g.x * s);
 }
 
-// Per-thread gradient accumulators live in shared memory, one column per thread
-// (slot-major: slot s of thread t at s * BLOCK + t, so a warp's accesses hit 32
-// distinct banks), which keeps the register count low enough for 4 blocks/SM.
+// Per-thread gradient accumulators live in shared memory, which keeps the
+// register count low enough for 4 blocks/SM.  Slots come in (Re, Im) or
+// (M, Gamma0) pairs, slots 1 + 2p and 2 + 2p forming pair p; pair p of thread t
+// is one float2 at p * BLOCK + t, so each update is one 64-bit load and store
+// and a warp's accesses cover every bank twice (two wavefronts, no conflict).
 // Events are read one per iteration with coalesced scalar loads.
 template <int NK, int NZ, bool NORM, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec, int64_t npad,
@@ -351,13 +318,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                                                    const float2 *__restrict__ lc, int nslot)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
-    using SL = Slots<NK, NZ>;
     const ModelDev &md = c_md;   // gmd is its source (copied by with_const_table)
     __shared__ double red[BLOCK / 32];
-    extern __shared__ float gsl[];   // [nslot][BLOCK]
+    extern __shared__ float2 gsl[];  // [(nslot - 1) / 2][BLOCK]
     const int tid = threadIdx.x;
-    for (int i = 1; i < nslot; ++i) gsl[i * BLOCK + tid] = 0.f;
-    float *g = gsl + tid;            // g[s * BLOCK] = slot s of this thread
+    const int npair = (nslot - 1) >> 1;
+    for (int i = 0; i < npair; ++i) gsl[i * BLOCK + tid] = make_float2(0.f, 0.f);
+    float2 *g = gsl + tid;           // g[p * BLOCK] = slot pair p of this thread
     Kahan acc0;
     int esum = 0;
     bool bad = false;
@@ -405,10 +372,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
             const float2 Bl[3] = {make_float2(-ev.B1[k].x, -ev.B1[k].y), ev.B0[k], ev.B1[k]};
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
-                float &gr = g[(SL::K0 + 6 * k + 2 * l) * BLOCK];
-                float &gi = g[(SL::K0 + 6 * k + 2 * l + 1) * BLOCK];
-                gr = fmaf(Bl[l].x, wl[l].x, fmaf(-Bl[l].y, wl[l].y, gr));
-                gi = fmaf(-Bl[l].x, wl[l].y, fmaf(-Bl[l].y, wl[l].x, gi));
+                float2 gp = g[(3 * k + l) * BLOCK];
+                gp.x = fmaf(Bl[l].x, wl[l].x, fmaf(-Bl[l].y, wl[l].y, gp.x));
+                gp.y = fmaf(-Bl[l].x, wl[l].y, fmaf(-Bl[l].y, wl[l].x, gp.y));
+                g[(3 * k + l) * BLOCK] = gp;
             }
             if (rs.fpos >= 0) {
                 // y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
@@ -422,8 +389,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                 float2 dM, dG;
                 lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
                 const float2 a = cmul(dM, y), b = cmul(dG, y);
-                g[(SL::MG0 + 2 * rs.fpos) * BLOCK] += a.x;
-                g[(SL::MG0 + 2 * rs.fpos + 1) * BLOCK] += b.x;
+                float2 &gm = g[(3 * NK + 2 * NZ + rs.fpos) * BLOCK];
+                gm.x += a.x;
+                gm.y += b.x;
             }
         }
         if constexpr (NZ > 0) {
@@ -437,14 +405,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                     cfma_conj(w1, as[x], ev.Om1[z][x]);
                 }
                 const float2 A = ev.AZ[z];
-                float &g0r = g[(SL::Z0 + 4 * z + 0) * BLOCK];
-                float &g0i = g[(SL::Z0 + 4 * z + 1) * BLOCK];
-                float &g1r = g[(SL::Z0 + 4 * z + 2) * BLOCK];
-                float &g1i = g[(SL::Z0 + 4 * z + 3) * BLOCK];
-                g0r = fmaf(A.x, w0.x, fmaf(-A.y, w0.y, g0r));
-                g0i = fmaf(-A.x, w0.y, fmaf(-A.y, w0.x, g0i));
-                g1r = fmaf(A.x, w1.x, fmaf(-A.y, w1.y, g1r));
-                g1i = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1i));
+                float2 g0 = g[(3 * NK + 2 * z) * BLOCK], g1 = g[(3 * NK + 2 * z + 1) * BLOCK];
+                g0.x = fmaf(A.x, w0.x, fmaf(-A.y, w0.y, g0.x));
+                g0.y = fmaf(-A.x, w0.y, fmaf(-A.y, w0.x, g0.y));
+                g1.x = fmaf(A.x, w1.x, fmaf(-A.y, w1.y, g1.x));
+                g1.y = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1.y));
+                g[(3 * NK + 2 * z) * BLOCK] = g0;
+                g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
                 if (rs.fpos >= 0) {
                     float2 y = make_float2(0.f, 0.f);
                     if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
@@ -453,8 +420,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                     float2 dM, dG;
                     lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
                     const float2 a = cmul(dM, y), b = cmul(dG, y);
-                    g[(SL::MG0 + 2 * rs.fpos) * BLOCK] += a.x;
-                    g[(SL::MG0 + 2 * rs.fpos + 1) * BLOCK] += b.x;
+                    float2 &gm = g[(3 * NK + 2 * NZ + rs.fpos) * BLOCK];
+                    gm.x += a.x;
+                    gm.y += b.x;
                 }
             }
         }
@@ -473,7 +441,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
     // Block sums of every gradient slot in FP64, in thread order.
     for (int s2 = 1 + tid; s2 < nslot; s2 += BLOCK) {
         double t = 0.0;
-        for (int j = 0; j < BLOCK; ++j) t += (double)gsl[s2 * BLOCK + j];
+        const float *col = reinterpret_cast<const float *>(gsl + ((s2 - 1) >> 1) * BLOCK) + ((s2 - 1) & 1);
+        for (int j = 0; j < BLOCK; ++j) t += (double)col[2 * j];
         part[(int64_t)blockIdx.x * nslot + s2] = t;
     }
 }
