@@ -143,6 +143,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per data event of the cached adjoint kernel, from one
+# ncu capture of the current kernel on 4e6 events of the same model
+# (profiles/k_grad_cached_kstar10_z_4M_events.md: 608.64 MB read + 6.64 MB written).
+# Scaled by events to the launch; None when the kernel has changed since.
+K_GRAD_DRAM_BYTES_PER_EVENT = (608.638208e6 + 6.641920e6) / 4e6
+
+
 def bytes_per_event(res_list, cached=True):
     """Algorithmic bytes read per data event by the adjoint kernel: the FP32 event
     records (17 with a Z, 8 without) and, on the cached path, one complex FP32
@@ -351,7 +358,13 @@ def main():
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": frac_alu,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (of nominal)"}
-    roof.update({"kernel": "k_grad data (adjoint, basis cache)", "traffic": None,
+    same_model = (not cfg.float_mg and [r.name for r in res] ==
+                  [r.name for r in W.CONFIGS["large"].resonances])
+    traffic = (K_GRAD_DRAM_BYTES_PER_EVENT * units
+               if (K_GRAD_DRAM_BYTES_PER_EVENT and same_model and dom == 1) else None)
+    roof.update({"kernel": "k_grad data (adjoint, basis cache)", "traffic": traffic,
+                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum on 4e6 events, "
+                                   "scaled by events",
                  "units_per_launch": units, "flops_per_event": fpe, "alu_frac": frac_alu,
                  "hbm_frac": frac_hbm})
     line = {
