@@ -50,8 +50,9 @@ struct ResDev {
     float dNhi, dNlo; // d ln(sqrt(KB KR))/dM, KB = P_LB(r^2 p0^2), KR = P_LR(r^2 q0^2)
     float dGhi, dGlo; // d ln(M Gamma)/dM at fixed m
     float iGhi, iGlo; // 1 / G0
-    float pd0[5];     // P_J(c) = sum_i pd0[i] c^i          (d^J_00)
-    float pd1[4];     // P_J'(c) = sum_i pd1[i] c^i         (d1 = -sin P_J')
+    // Horner pairs for P_J(c) = sum_i a_i c^i (d^J_00) and P_J'(c) = sum_i b_i c^i
+    // (d1 = -sin P_J'): hp[0] = (a_4, 0), hp[j] = (a_{4-j}, b_{4-j}) for j = 1..4.
+    float2 hp[5];
     int chain, J, LB, LR;
     int col;          // first basis column
     int fpos;         // index among floated resonances, -1 if fixed
@@ -85,6 +86,11 @@ struct ModelDev {
     ResDev zr[2];                  // the Z resonances, res[n_res - NZ + z]
     float2 kc[AMP4D_MAX_RES][3], kcl[AMP4D_MAX_RES][3];
     float2 zc[2][2], zcl[2][2];
+    // The same couplings as pre-broadcast pairs for packed FP32x2 products (see
+    // cfma2p): {(h.x, h.x), (-h.y, h.y), (l.x, l.x), (-l.y, l.y)} for h + l = c';
+    // the K* l = -1 entry holds -c' (its basis factor is -A d1).
+    float2 kp[AMP4D_MAX_RES][3][4];
+    float2 zp[2][2][4];
     // Where column k's coupling is copied: K* (t << 2 | slot) or Z (0x100 | z << 2 | slot).
     int col_dst[3 * AMP4D_MAX_RES];
     int static_bad;                // a fixed resonance has no valid pole constants
@@ -109,15 +115,22 @@ __device__ __forceinline__ void cfma_conj(float2 &a, float2 b, float2 c)
     a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
     a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
 }
-// a += (hi + lo) * c: the low part enters the same FMA chain as the high-part
+// a += (hi + lo) * c, with the low part inside the FMA chain of the high-part
 // product, so the constant hi + lo is applied before each term is rounded (an
-// addition after the rounding would drop it whenever it is below half an ulp).
-__device__ __forceinline__ void cfma2(float2 &a, float2 hi, float2 lo, float2 c)
+// addition after the rounding would drop it whenever it is below half an ulp):
+//   tx = fma(hi.x, c.x, fma(-hi.y, c.y, fma(lo.x, c.x, -lo.y c.y))),
+//   ty = fma(hi.x, c.y, fma(hi.y, c.x, fma(lo.x, c.y, lo.y c.x))),  a += t.
+// Evaluated with packed FP32x2 operations on pre-broadcast pairs
+// q = {(hi.x, hi.x), (-hi.y, hi.y), (lo.x, lo.x), (-lo.y, lo.y)} and the swapped
+// factor cs = (c.y, c.x): each component follows the scalar chain above in the
+// same order, in half the instructions.
+__device__ __forceinline__ void cfma2p(float2 &a, const float2 *q, float2 c, float2 cs)
 {
-    const float tx = fmaf(hi.x, c.x, fmaf(-hi.y, c.y, fmaf(lo.x, c.x, -lo.y * c.y)));
-    const float ty = fmaf(hi.x, c.y, fmaf(hi.y, c.x, fmaf(lo.x, c.y, lo.y * c.x)));
-    a.x += tx;
-    a.y += ty;
+    float2 t = __fmul2_rn(q[3], cs);
+    t = __ffma2_rn(q[2], c, t);
+    t = __ffma2_rn(q[1], cs, t);
+    t = __ffma2_rn(q[0], c, t);
+    a = __fadd2_rn(a, t);
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -152,10 +165,17 @@ __device__ __forceinline__ float ipow(float x, int n)
 // are evaluated by Horner from the resonance's coefficients, so the same
 // instructions serve every J (no branch on the spin).
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void wigner_l0(const ResDev &r, float c, float s, float &d0, float &d1)
+// Both polynomials run as one packed Horner chain over cc = (c, c); the P_J'
+// lane starts at 0, so its first step returns b_3 exactly.
+__device__ __forceinline__ void wigner_l0(const ResDev &r, float2 cc, float s, float &d0, float &d1)
 {
-    d0 = fmaf(fmaf(fmaf(fmaf(r.pd0[4], c, r.pd0[3]), c, r.pd0[2]), c, r.pd0[1]), c, r.pd0[0]);
-    d1 = -s * fmaf(fmaf(fmaf(r.pd1[3], c, r.pd1[2]), c, r.pd1[1]), c, r.pd1[0]);
+    float2 h = r.hp[0];
+    h = __ffma2_rn(h, cc, r.hp[1]);
+    h = __ffma2_rn(h, cc, r.hp[2]);
+    h = __ffma2_rn(h, cc, r.hp[3]);
+    h = __ffma2_rn(h, cc, r.hp[4]);
+    d0 = h.x;
+    d1 = -s * h.y;
 }
 
 // d^1_{l xi}(theta) for l in {-1, 0, 1}, xi in {+1 (x=0), -1 (x=1)}; the l = 0

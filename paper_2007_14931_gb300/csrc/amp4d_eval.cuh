@@ -97,6 +97,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     const float invm = __frcp_rn(m);
     ev.m = m; ev.invm = invm; ev.p = p; ev.q = q;
     const float sK = sqrtf(fmaxf(0.0f, fmaf(-cK, cK, 1.0f)));
+    const float2 cc = make_float2(cK, cK);
     ev.cK = cK; ev.sK = sK;
     const float spsi = sqrtf(fmaxf(0.0f, fmaf(-cpsi, cpsi, 1.0f)));
     const float cph = r[REC_CPHI], sph = r[REC_SPHI];   // e^{i phi}, FP64 at ingest
@@ -128,14 +129,16 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
             const ResDev &rs = md.res[k];
             const float2 LA = cached_or_computed(rs, have_lc, LK[k], m, invm, p, q);
             float d0, d1;
-            wigner_l0(rs, cK, sK, d0, d1);
+            wigner_l0(rs, cc, sK, d0, d1);
             const float2 b0 = cscale(LA, d0), b1 = cscale(LA, d1);
             ev.B0[k] = b0;
             ev.B1[k] = b1;
             // J = 0: the l = +-1 couplings are 0 and d1 = 0, so no branch on J.
-            cfma2(u[0], md.kc[k][0], md.kcl[k][0], make_float2(-b1.x, -b1.y));
-            cfma2(u[1], md.kc[k][1], md.kcl[k][1], b0);
-            cfma2(u[2], md.kc[k][2], md.kcl[k][2], b1);
+            // kp[k][0] holds -c'_{k,-1}: the l = -1 factor is -A d1.
+            const float2 b0s = make_float2(b0.y, b0.x), b1s = make_float2(b1.y, b1.x);
+            cfma2p(u[0], md.kp[k][0], b1, b1s);
+            cfma2p(u[1], md.kp[k][1], b0, b0s);
+            cfma2p(u[2], md.kp[k][2], b1, b1s);
         } else {
             ev.B0[k] = ev.B1[k] = make_float2(0.f, 0.f);
         }
@@ -164,7 +167,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
             const ResDev &rs = md.zr[z];
             const float2 LA = cached_or_computed(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
             float dz0, dz1;
-            wigner_l0(rs, cZ, sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
+            wigner_l0(rs, make_float2(cZ, cZ), sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
             ev.AZ[z] = LA;
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
@@ -177,8 +180,8 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                 ev.Om0[z][x] = o0;
                 ev.Om1[z][x] = o1;
                 float2 s = make_float2(0.f, 0.f);
-                if (rs.zcol0 >= 0) cfma2(s, md.zc[z][0], md.zcl[z][0], o0);
-                if (rs.zcol1 >= 0) cfma2(s, md.zc[z][1], md.zcl[z][1], o1);
+                if (rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
+                if (rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
                 cfma(ev.a[x], LA, s);
             }
         }
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
             if (rs.fpos >= 0) {
                 // y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
                 float d0, d1;
-                wigner_l0(rs, ev.cK, ev.sK, d0, d1);
+                wigner_l0(rs, make_float2(ev.cK, ev.cK), ev.sK, d0, d1);
                 float2 y = make_float2(0.f, 0.f);
                 cfma(y, md.kc[k][0], cscale(wl[0], -d1));
                 cfma(y, md.kc[k][1], cscale(wl[1], d0));

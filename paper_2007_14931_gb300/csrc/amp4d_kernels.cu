@@ -270,6 +270,15 @@ __device__ __forceinline__ void split_store(double re, double im, float2 &hi, fl
     lo = make_float2((float)(re - (double)hi.x), (float)(im - (double)hi.y));
 }
 
+// Pre-broadcast pairs of sg (hi + lo) for cfma2p (sg = +-1, exact).
+__device__ __forceinline__ void pack_pairs(float2 hi, float2 lo, float sg, float2 *q)
+{
+    q[0] = make_float2(sg * hi.x, sg * hi.x);
+    q[1] = make_float2(-sg * hi.y, sg * hi.y);
+    q[2] = make_float2(sg * lo.x, sg * lo.x);
+    q[3] = make_float2(-sg * lo.y, sg * lo.y);
+}
+
 __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *__restrict__ params,
                               ModelDev *__restrict__ md, double *__restrict__ pscale,
                               unsigned *__restrict__ status)
@@ -336,8 +345,9 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
                                    {0.f, -1.5f, 0.f, 2.5f, 0.f},
                                    {0.375f, 0.f, -3.75f, 0.f, 4.375f}};
             const int J = r.J < 0 ? 0 : (r.J > 4 ? 4 : r.J);
-            for (int i = 0; i < 5; ++i) d.pd0[i] = P[J][i];
-            for (int i = 0; i < 4; ++i) d.pd1[i] = (float)(i + 1) * P[J][i + 1];
+            d.hp[0] = make_float2(P[J][4], 0.f);
+            for (int j = 1; j < 5; ++j)
+                d.hp[j] = make_float2(P[J][4 - j], (float)(5 - j) * P[J][5 - j]);
         }
         d.chain = r.chain;
         d.J = r.J;
@@ -354,9 +364,15 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
             zi = 0;
             for (int i = 0; i < t; ++i) zi += st->res[i].chain == AMP4D_CHAIN_Z ? 1 : 0;
             md->zr[zi] = d;
-            for (int j = 0; j < 2; ++j) md->zc[zi][j] = md->zcl[zi][j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < 2; ++j) {
+                md->zc[zi][j] = md->zcl[zi][j] = make_float2(0.f, 0.f);
+                for (int i = 0; i < 4; ++i) md->zp[zi][j][i] = make_float2(0.f, 0.f);
+            }
         } else {
-            for (int j = 0; j < 3; ++j) md->kc[t][j] = md->kcl[t][j] = make_float2(0.f, 0.f);
+            for (int j = 0; j < 3; ++j) {
+                md->kc[t][j] = md->kcl[t][j] = make_float2(0.f, 0.f);
+                for (int i = 0; i < 4; ++i) md->kp[t][j][i] = make_float2(0.f, 0.f);
+            }
         }
         // Column constants: sqrt(KB KR) m_B^-LB times 1/sqrt(2) for the l = 0 J/psi
         // factor d^1_{0 xi}, or 1/sqrt(J (J+1)) for the l = +-1 factor d^J_{+-1 0}.
@@ -384,11 +400,13 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
                 const int sl = r.J == 0 ? 1 : j;
                 md->kc[t][sl] = md->c[k];
                 md->kcl[t][sl] = md->cl[k];
+                pack_pairs(md->c[k], md->cl[k], sl == 0 ? -1.f : 1.f, md->kp[t][sl]);
                 md->col_dst[k] = (t << 2) | sl;
             } else {
                 const int sl = k == r.zcol0 ? 0 : 1;
                 md->zc[zi][sl] = md->c[k];
                 md->zcl[zi][sl] = md->cl[k];
+                pack_pairs(md->c[k], md->cl[k], 1.f, md->zp[zi][sl]);
                 md->col_dst[k] = 0x100 | (zi << 2) | sl;
             }
             pscale[2 * k] = kap[j];
@@ -433,9 +451,11 @@ __global__ void k_update_couplings(const ModelStatic *__restrict__ st, const dou
         if (dst & 0x100) {
             md->zc[(dst >> 2) & 3][sl] = hi;
             md->zcl[(dst >> 2) & 3][sl] = lo;
+            pack_pairs(hi, lo, 1.f, md->zp[(dst >> 2) & 3][sl]);
         } else {
             md->kc[dst >> 2][sl] = hi;
             md->kcl[dst >> 2][sl] = lo;
+            pack_pairs(hi, lo, sl == 0 ? -1.f : 1.f, md->kp[dst >> 2][sl]);
         }
     }
     __syncthreads();
