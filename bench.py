@@ -145,17 +145,21 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per data event of the cached adjoint kernel, from one
 # ncu capture of the current kernel on 4e6 events of the same model
-# (profiles/k_grad_cached_kstar10_z_4M_events.md: 608.64 MB read + 6.64 MB written).
+# (profiles/k_grad_cached_kstar10_z_4M_events.md: 512.08 MB read + 3.57 MB written).
 # Scaled by events to the launch; None when the kernel has changed since.
-K_GRAD_DRAM_BYTES_PER_EVENT = (608.638208e6 + 6.641920e6) / 4e6
+K_GRAD_DRAM_BYTES_PER_EVENT = (512.0768e6 + 3.565824e6) / 4e6
 
 
-def bytes_per_event(res_list, cached=True):
+def bytes_per_event(res_list, cached=True, float_names=()):
     """Algorithmic bytes read per data event by the adjoint kernel: the FP32 event
-    records (17 with a Z, 8 without) and, on the cached path, one complex FP32
-    lineshape per resonance."""
+    records it reads and, on the cached path, one complex FP32 lineshape per
+    resonance.  Records: 17 with a Z, 8 without; when every lineshape comes from
+    the cache the masses, momenta and phi (7 with a Z, 4 without) are not read."""
     has_z = any(r.chain == W.CHAIN_Z for r in res_list)
-    return 4 * (17 if has_z else 8) + (8 * len(res_list) if cached else 0)
+    nrec = 17 if has_z else 8
+    if cached and not float_names:
+        nrec -= 7 if has_z else 4
+    return 4 * nrec + (8 * len(res_list) if cached else 0)
 
 
 def make_workload(cfg, rank=0):
@@ -344,7 +348,7 @@ def main():
     dom = int(np.argmax(prof_ms))
     units = cfg.n_events if dom in (1, 0, 3) else cfg.n_norm
     fpe = flops_per_event(res, cfg.float_mg, grad=True, cached=True)
-    bpe = bytes_per_event(res, cached=True)
+    bpe = bytes_per_event(res, cached=True, float_names=cfg.float_mg)
     mean_launch_s = prof_ms[dom] / max(1, prof_n[dom]) / 1e3
     achieved_tf = fpe * units / mean_launch_s / 1e12
     achieved_gbs = bpe * units / mean_launch_s / 1e9

@@ -28,7 +28,7 @@ struct EventSet {
     int nrec = 0, wrec = -1;
     double lnpq = 0.0;
     double volume = 0.0;
-    int grid_eval = 0, grid_grad = 0;
+    int grid_eval = 0, grid_grad = 0, grid_grad_cached = 0;
     double *part = nullptr;     // per-block partials (grid_grad x nslot)
     size_t part_cap = 0;
     float2 *lcache = nullptr;   // basis cache [resonance][npad] (cached path)
@@ -211,8 +211,10 @@ amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const flo
     s.grid_eval = (int)std::max<int64_t>(1, std::min<int64_t>((n + eval_block() - 1) / eval_block(),
                                                               (int64_t)model->nsm * 4));
     s.grid_grad = (int)std::max<int64_t>(1, std::min<int64_t>((n + grad_block() - 1) / grad_block(),
-                                                              (int64_t)model->nsm * 4));
-    s.part_cap = (size_t)std::max(s.grid_eval, s.grid_grad) * model->nslot;
+                                                              (int64_t)model->nsm * GRAD_CTAS_PER_SM));
+    s.grid_grad_cached = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n + grad_block() - 1) / grad_block(), (int64_t)model->nsm * GRAD_CTAS_PER_SM_CACHED));
+    s.part_cap = (size_t)std::max(s.grid_eval, std::max(s.grid_grad, s.grid_grad_cached)) * model->nslot;
     CK(cudaMalloc(&s.part, s.part_cap * sizeof(double)));
     s.n = n;
     return AMP4D_OK;
@@ -227,6 +229,13 @@ cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t 
                                        st, fast);
     if (e == cudaSuccess && mo->n_float == 0) mo->table_built = true;
     return e;
+}
+
+// Grid of the adjoint kernel over a set: one full wave of the variant that runs.
+int grad_grid(const amp4d_model *mo, const EventSet &s)
+{
+    const bool cached = mo->path == AMP4D_PATH_CACHED && s.lcache_valid && mo->n_float == 0;
+    return cached ? s.grid_grad_cached : s.grid_grad;
 }
 
 LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cudaStream_t st,
@@ -247,6 +256,7 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.stream = st;
     a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
     a.nslot = mo->nslot;
+    a.all_fixed = mo->n_float == 0;
     return a;
 }
 
@@ -366,11 +376,11 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         }
         const double von = model->mc.volume / (double)model->mc.n;
         if (with_grad) {
-            LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_grad);
+            LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
             CK(launch_grad(ad, false));
             CK(mark());
             CK(mark());
-            CK(launch_reduce_cols(model->ev.part, model->ev.grid_grad, model->nslot, rd, st));
+            CK(launch_reduce_cols(model->ev.part, grad_grid(model, model->ev), model->nslot, rd, st));
         } else {
             LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
             CK(launch_eval(ad, 0));
@@ -387,14 +397,14 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         return AMP4D_OK;
     }
     if (with_grad) {
-        LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_grad);
+        LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
         CK(launch_grad(ad, false));
         CK(mark());
-        LaunchArgs an = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_grad);
+        LaunchArgs an = args_for(model, model->mc, model->mc.part, nullptr, st, grad_grid(model, model->mc));
         CK(launch_grad(an, true));
         CK(mark());
-        CK(launch_reduce_cols(model->ev.part, model->ev.grid_grad, model->nslot, rd, st));
-        CK(launch_reduce_cols(model->mc.part, model->mc.grid_grad, model->nslot, rn, st));
+        CK(launch_reduce_cols(model->ev.part, grad_grid(model, model->ev), model->nslot, rd, st));
+        CK(launch_reduce_cols(model->mc.part, grad_grid(model, model->mc), model->nslot, rn, st));
         if (partials)
             CK(launch_partials(rd, rn, model->d_slot_param, model->d_pscale, model->nslot,
                                model->n_param, (double)model->ev.n, model->ev.lnpq,

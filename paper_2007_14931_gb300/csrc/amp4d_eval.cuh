@@ -86,15 +86,20 @@ __device__ __forceinline__ float2 cached_or_computed(const ResDev &rs, bool have
 }
 
 // lc (nullable): basis cache [resonance][lcn] of lineshapes A'_R per event e.
-template <int NK, int NZ>
+// FX: every resonance is fixed and lc is given, so every lineshape comes from
+// the cache and the masses and momenta (records M, P, Q, MZ, PZ, QZ) are unused.
+template <int NK, int NZ, bool FX = false>
 __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                                            EvState<NK, NZ> &ev,
                                            const float2 *__restrict__ lc = nullptr,
                                            int64_t lcn = 0, int64_t e = 0)
 {
-    const float m = r[REC_M], cK = r[REC_CK], cpsi = r[REC_CPSI];
-    const float p = r[REC_P], q = r[REC_Q];
-    const float invm = __frcp_rn(m);
+    const float cK = r[REC_CK], cpsi = r[REC_CPSI];
+    float m = 0.f, p = 0.f, q = 0.f, invm = 0.f;
+    if constexpr (!FX) {
+        m = r[REC_M]; p = r[REC_P]; q = r[REC_Q];
+        invm = __frcp_rn(m);
+    }
     ev.m = m; ev.invm = invm; ev.p = p; ev.q = q;
     const float sK = sqrtf(fmaxf(0.0f, fmaf(-cK, cK, 1.0f)));
     const float2 cc = make_float2(cK, cK);
@@ -114,7 +119,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     // Every cached lineshape of the event is requested before any is used, so
     // the loads overlap instead of waiting one after another behind the
     // per-resonance branches.
-    const bool have_lc = lc != nullptr;
+    const bool have_lc = FX || lc != nullptr;
     float2 LK[NK], LZ[NZ > 0 ? NZ : 1];
     if (have_lc) {
 #pragma unroll
@@ -127,7 +132,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     for (int k = 0; k < NK; ++k) {
         if (k < nK) {
             const ResDev &rs = md.res[k];
-            const float2 LA = cached_or_computed(rs, have_lc, LK[k], m, invm, p, q);
+            const float2 LA = FX ? LK[k] : cached_or_computed(rs, have_lc, LK[k], m, invm, p, q);
             float d0, d1;
             wigner_l0(rs, cc, sK, d0, d1);
             const float2 b0 = cscale(LA, d0), b1 = cscale(LA, d1);
@@ -152,11 +157,14 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
         ev.a[x] = a;
     }
     if constexpr (NZ > 0) {
-        const float mZ = r[REC_MZ], pZ = r[REC_PZ], qZ = r[REC_QZ];
+        float mZ = 0.f, pZ = 0.f, qZ = 0.f, invmZ = 0.f;
+        if constexpr (!FX) {
+            mZ = r[REC_MZ]; pZ = r[REC_PZ]; qZ = r[REC_QZ];
+            invmZ = __frcp_rn(mZ);
+        }
         const float cZ = r[REC_CZ], ctz = r[REC_CTZ];
         const float2 ephz = make_float2(r[REC_CPZ], r[REC_SPZ]);
         const float ca = r[REC_CA], sa = r[REC_SA];
-        const float invmZ = __frcp_rn(mZ);
         ev.mZ = mZ; ev.invmZ = invmZ; ev.pZ = pZ; ev.qZ = qZ;
         const float sZ = sqrtf(fmaxf(0.0f, fmaf(-cZ, cZ, 1.0f)));
         const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
@@ -165,7 +173,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
             const ResDev &rs = md.zr[z];
-            const float2 LA = cached_or_computed(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
+            const float2 LA = FX ? LZ[z] : cached_or_computed(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
             float dz0, dz1;
             wigner_l0(rs, make_float2(cZ, cZ), sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
             ev.AZ[z] = LA;
@@ -236,7 +244,16 @@ __device__ __forceinline__ void load_model(const ModelDev *g, ModelDev *s)
 // MODE_WRITE: S per event to out.
 enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
 
-template <int NK, int NZ, int MODE, int BLOCK>
+// Records read by eval_event<.., FX>: all of them, or without the masses and
+// momenta when every lineshape comes from the cache.
+template <bool FX>
+__device__ __forceinline__ constexpr bool record_used(int k)
+{
+    return !FX || !(k == REC_M || k == REC_PHI || k == REC_P || k == REC_Q || k == REC_MZ ||
+                    k == REC_PZ || k == REC_QZ);
+}
+
+template <int NK, int NZ, int MODE, int BLOCK, bool FX>
 __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, int64_t npad,
                                                 int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                 double *__restrict__ part, float *__restrict__ S_out,
@@ -254,9 +271,9 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
          e += (int64_t)gridDim.x * BLOCK) {
         float v[NREC];
 #pragma unroll
-        for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
+        for (int k = 0; k < NREC; ++k) v[k] = record_used<FX>(k) ? __ldg(rec + k * npad + e) : 0.f;
         EvState<NK, NZ> ev;
-        eval_event<NK, NZ>(md, v, ev, lc, npad, e);
+        eval_event<NK, NZ, FX>(md, v, ev, lc, npad, e);
         if (MODE == MODE_SUM_LNS) {
             if (!(ev.S > 0.0f)) { bad = true; continue; }
             int ex;
@@ -308,13 +325,13 @@ __device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, flo
 }
 
 // Per-thread gradient accumulators live in shared memory, which keeps the
-// register count low enough for 4 blocks/SM.  Slots come in (Re, Im) or
+// register count low enough for 4 blocks/SM (5 when every lineshape is cached).  Slots come in (Re, Im) or
 // (M, Gamma0) pairs, slots 1 + 2p and 2 + 2p forming pair p; pair p of thread t
 // is one float2 at p * BLOCK + t, so each update is one 64-bit load and store
 // and a warp's accesses cover every bank twice (two wavefronts, no conflict).
 // Events are read one per iteration with coalesced scalar loads.
-template <int NK, int NZ, bool NORM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec, int64_t npad,
+template <int NK, int NZ, bool NORM, int BLOCK, bool FX>
+__global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTAS_PER_SM) k_grad(const float *__restrict__ rec, int64_t npad,
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                    double *__restrict__ part,
                                                    unsigned *__restrict__ status,
@@ -335,9 +352,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
     for (int64_t e = blockIdx.x * (int64_t)BLOCK + tid; e < n; e += (int64_t)gridDim.x * BLOCK) {
         float v[NREC];
 #pragma unroll
-        for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
+        for (int k = 0; k < NREC; ++k) v[k] = record_used<FX>(k) ? __ldg(rec + k * npad + e) : 0.f;
         EvState<NK, NZ> ev;
-        eval_event<NK, NZ>(md, v, ev, lc, npad, e);
+        eval_event<NK, NZ, FX>(md, v, ev, lc, npad, e);
         float scale;
         if (!NORM) {
             if (!(ev.S > 0.0f)) { bad = true; continue; }
@@ -380,7 +397,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                 gp.y = fmaf(-Bl[l].x, wl[l].y, fmaf(-Bl[l].y, wl[l].x, gp.y));
                 g[(3 * k + l) * BLOCK] = gp;
             }
-            if (rs.fpos >= 0) {
+            if (!FX && rs.fpos >= 0) {
                 // y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
                 float d0, d1;
                 wigner_l0(rs, make_float2(ev.cK, ev.cK), ev.sK, d0, d1);
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
                 g1.y = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1.y));
                 g[(3 * NK + 2 * z) * BLOCK] = g0;
                 g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
-                if (rs.fpos >= 0) {
+                if (!FX && rs.fpos >= 0) {
                     float2 y = make_float2(0.f, 0.f);
                     if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
                     if (rs.zcol1 >= 0) cfma(y, md.zc[z][1], w1);
@@ -453,21 +470,21 @@ __global__ void __launch_bounds__(BLOCK, 4) k_grad(const float *__restrict__ rec
 constexpr int EVAL_BLOCK = 256;
 constexpr int GRAD_BLOCK = 128;
 
-template <int NK, int NZ>
-cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
+template <int NK, int NZ, bool FX>
+cudaError_t launch_eval_fx(const LaunchArgs &a, int mode)
 {
     return with_const_table(a.md, a.stream, [&]() {
         switch (mode) {
         case MODE_SUM_LNS:
-            k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+            k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
                 a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
             break;
         case MODE_SUM_WS:
-            k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+            k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
                 a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
             break;
         default:
-            k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+            k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
                 a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
             break;
         }
@@ -475,15 +492,24 @@ cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
     });
 }
 
-template <int NK, int NZ, bool NORM>
+template <int NK, int NZ>
+cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
+{
+    return (a.lcache && a.all_fixed) ? launch_eval_fx<NK, NZ, true>(a, mode)
+                                     : launch_eval_fx<NK, NZ, false>(a, mode);
+}
+
+template <int NK, int NZ, bool NORM, bool FX>
 cudaError_t launch_grad_k(const LaunchArgs &a)
 {
     const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, NORM, GRAD_BLOCK>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (smem > 48 * 1024) {   // above the default dynamic shared-memory limit
+        cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, NORM, GRAD_BLOCK, FX>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     return with_const_table(a.md, a.stream, [&]() {
-        k_grad<NK, NZ, NORM, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
+        k_grad<NK, NZ, NORM, GRAD_BLOCK, FX><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
             a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache, a.nslot);
         return cudaGetLastError();
     });
@@ -492,7 +518,9 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
 template <int NK, int NZ>
 cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
 {
-    return norm ? launch_grad_k<NK, NZ, true>(a) : launch_grad_k<NK, NZ, false>(a);
+    const bool fx = a.lcache && a.all_fixed;
+    if (norm) return fx ? launch_grad_k<NK, NZ, true, true>(a) : launch_grad_k<NK, NZ, true, false>(a);
+    return fx ? launch_grad_k<NK, NZ, false, true>(a) : launch_grad_k<NK, NZ, false, false>(a);
 }
 
 // Basis cache: A'_R (Eq. 2-3 without its column constant) of every resonance for

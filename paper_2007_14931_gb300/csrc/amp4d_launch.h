@@ -23,7 +23,13 @@ struct LaunchArgs {
     cudaStream_t stream;
     const float2 *lcache = nullptr;  // basis cache of the set, or null (recompute)
     int nslot = 0;                   // gradient slots (grad_num_slots)
+    bool all_fixed = false;          // no mass or width floats (with lcache: all lineshapes cached)
 };
+
+// Resident CTAs per SM of the adjoint kernel (its __launch_bounds__): the
+// variant whose lineshapes all come from the basis cache needs fewer registers.
+constexpr int GRAD_CTAS_PER_SM = 4;
+constexpr int GRAD_CTAS_PER_SM_CACHED = 5;
 
 int nk_bucket(int nk);
 // Gradient slots: ln S (or w S), 6 per K* of the bucket, 4 per Z, and 2 (mass,
