@@ -145,9 +145,9 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per data event of the cached adjoint kernel, from one
 # ncu capture of the current kernel on 4e6 events of the same model
-# (profiles/k_grad_cached_kstar10_z_4M_events.md: 512.08 MB read + 3.57 MB written).
+# (profiles/k_grad_cached_kstar10_z_4M_events.md: 512.07 MB read + 3.88 MB written).
 # Scaled by events to the launch; None when the kernel has changed since.
-K_GRAD_DRAM_BYTES_PER_EVENT = (512.0768e6 + 3.565824e6) / 4e6
+K_GRAD_DRAM_BYTES_PER_EVENT = (512.068608e6 + 3.87584e6) / 4e6
 
 
 def bytes_per_event(res_list, cached=True, float_names=()):

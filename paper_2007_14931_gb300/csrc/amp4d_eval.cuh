@@ -349,10 +349,30 @@ __global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTA
     int esum = 0;
     bool bad = false;
     const int nK = md.n_res - NZ;
-    for (int64_t e = blockIdx.x * (int64_t)BLOCK + tid; e < n; e += (int64_t)gridDim.x * BLOCK) {
-        float v[NREC];
+    const int64_t estride = (int64_t)gridDim.x * BLOCK;
+    // All-cached variant: the next event's records are loaded one iteration
+    // ahead (registers), so their latency overlaps the current event's
+    // arithmetic.  The generic variant has no registers to spare for it.
+    float vn[FX ? NREC : 1];
+    if constexpr (FX) {
+        const int64_t e0 = blockIdx.x * (int64_t)BLOCK + tid;
 #pragma unroll
-        for (int k = 0; k < NREC; ++k) v[k] = record_used<FX>(k) ? __ldg(rec + k * npad + e) : 0.f;
+        for (int k = 0; k < NREC; ++k)
+            vn[k] = (record_used<FX>(k) && e0 < n) ? __ldg(rec + k * npad + e0) : 0.f;
+    }
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + tid; e < n; e += estride) {
+        float v[NREC];
+        if constexpr (FX) {
+#pragma unroll
+            for (int k = 0; k < NREC; ++k) v[k] = vn[k];
+            const int64_t en = e + estride;
+#pragma unroll
+            for (int k = 0; k < NREC; ++k)
+                vn[k] = (record_used<FX>(k) && en < n) ? __ldg(rec + k * npad + en) : 0.f;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
+        }
         EvState<NK, NZ> ev;
         eval_event<NK, NZ, FX>(md, v, ev, lc, npad, e);
         float scale;
