@@ -145,9 +145,9 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per data event of the cached adjoint kernel, from one
 # ncu capture of the current kernel on 4e6 events of the same model
-# (profiles/k_grad_cached_kstar10_z_4M_events.md: 512.07 MB read + 3.88 MB written).
+# (profiles/k_grad_cached_kstar10_z_4M_events.md: 512.16 MB read + 3.42 MB written).
 # Scaled by events to the launch; None when the kernel has changed since.
-K_GRAD_DRAM_BYTES_PER_EVENT = (512.068608e6 + 3.87584e6) / 4e6
+K_GRAD_DRAM_BYTES_PER_EVENT = (512.161792e6 + 3.41504e6) / 4e6
 
 
 def bytes_per_event(res_list, cached=True, float_names=()):
@@ -366,7 +366,8 @@ def main():
                   [r.name for r in W.CONFIGS["large"].resonances])
     traffic = (K_GRAD_DRAM_BYTES_PER_EVENT * units
                if (K_GRAD_DRAM_BYTES_PER_EVENT and same_model and dom == 1) else None)
-    roof.update({"kernel": "k_grad data (adjoint, basis cache)", "traffic": traffic,
+    roof.update({"kernel": "k_grad_fx data (adjoint, all lineshapes from the basis cache)",
+                 "traffic": traffic,
                  "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum on 4e6 events, "
                                    "scaled by events",
                  "units_per_launch": units, "flops_per_event": fpe, "alu_frac": frac_alu,

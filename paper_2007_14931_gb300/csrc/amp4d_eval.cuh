@@ -197,6 +197,123 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     ev.S = cabs2(ev.a[0]) + cabs2(ev.a[1]);
 }
 
+// All-cached evaluation of NE events at once (FX only): the per-resonance
+// constants are read once for all NE events.  r[j] holds the records of event
+// e[j]; lc is the basis cache [resonance][lcn].
+template <int NK, int NZ, int NE>
+__device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
+                                               EvState<NK, NZ> (&ev)[NE],
+                                               const float2 *__restrict__ lc, int64_t lcn,
+                                               const int64_t (&e)[NE])
+{
+    const int nK = md.n_res - NZ;
+    float2 cc[NE];
+    float sK[NE];
+    float2 u[NE][3];
+    float2 LK[NE][NK], LZ[NE][NZ > 0 ? NZ : 1];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            LK[j][k] = k < nK ? __ldg(lc + k * lcn + e[j]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) LZ[j][z] = __ldg(lc + (nK + z) * lcn + e[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+        const float cK = r[j][REC_CK], cpsi = r[j][REC_CPSI];
+        sK[j] = sqrtf(fmaxf(0.0f, fmaf(-cK, cK, 1.0f)));
+        cc[j] = make_float2(cK, cK);
+        ev[j].cK = cK; ev[j].sK = sK[j];
+        const float spsi = sqrtf(fmaxf(0.0f, fmaf(-cpsi, cpsi, 1.0f)));
+        const float cph = r[j][REC_CPHI], sph = r[j][REC_SPHI];
+        float d1p[3][2];
+        wigner_1(cpsi, spsi, d1p);
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            ev[j].Psi[0][x] = make_float2(cph * d1p[0][x], -sph * d1p[0][x]);
+            ev[j].Psi[1][x] = make_float2(d1p[1][x], 0.0f);
+            ev[j].Psi[2][x] = make_float2(cph * d1p[2][x], sph * d1p[2][x]);
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l) u[j][l] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        if (k < nK) {
+            const ResDev &rs = md.res[k];
+#pragma unroll
+            for (int j = 0; j < NE; ++j) {
+                float d0, d1;
+                wigner_l0(rs, cc[j], sK[j], d0, d1);
+                const float2 b0 = cscale(LK[j][k], d0), b1 = cscale(LK[j][k], d1);
+                ev[j].B0[k] = b0;
+                ev[j].B1[k] = b1;
+                const float2 b0s = make_float2(b0.y, b0.x), b1s = make_float2(b1.y, b1.x);
+                cfma2p(u[j][0], md.kp[k][0], b1, b1s);
+                cfma2p(u[j][1], md.kp[k][1], b0, b0s);
+                cfma2p(u[j][2], md.kp[k][2], b1, b1s);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NE; ++j) ev[j].B0[k] = ev[j].B1[k] = make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j)
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            float2 a = make_float2(0.f, 0.f);
+            cfma(a, ev[j].Psi[0][x], u[j][0]);
+            cfma(a, ev[j].Psi[1][x], u[j][1]);
+            cfma(a, ev[j].Psi[2][x], u[j][2]);
+            ev[j].a[x] = a;
+        }
+    if constexpr (NZ > 0) {
+        float2 ephz[NE];
+        float cZ[NE], sZ[NE], ca[NE], sa[NE];
+        float d1t[NE][3][2];
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+            cZ[j] = r[j][REC_CZ];
+            const float ctz = r[j][REC_CTZ];
+            ephz[j] = make_float2(r[j][REC_CPZ], r[j][REC_SPZ]);
+            ca[j] = r[j][REC_CA]; sa[j] = r[j][REC_SA];
+            sZ[j] = sqrtf(fmaxf(0.0f, fmaf(-cZ[j], cZ[j], 1.0f)));
+            const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
+            wigner_1(ctz, stz, d1t[j]);
+        }
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) {
+            const ResDev &rs = md.zr[z];
+#pragma unroll
+            for (int j = 0; j < NE; ++j) {
+                const float2 LA = LZ[j][z];
+                float dz0, dz1;
+                wigner_l0(rs, make_float2(cZ[j], cZ[j]), sZ[j], dz0, dz1);
+                ev[j].AZ[z] = LA;
+#pragma unroll
+                for (int x = 0; x < 2; ++x) {
+                    const float2 eal = make_float2(ca[j], x == 0 ? sa[j] : -sa[j]);
+                    float2 o0 = cscale(eal, dz0 * d1t[j][1][x]);
+                    float2 t = cscale(ephz[j], -dz1 * d1t[j][2][x]);
+                    const float2 ephm = make_float2(ephz[j].x, -ephz[j].y);
+                    t = cadd(t, cscale(ephm, (float)rs.eta * dz1 * d1t[j][0][x]));
+                    float2 o1 = cmul(t, eal);
+                    ev[j].Om0[z][x] = o0;
+                    ev[j].Om1[z][x] = o1;
+                    float2 s = make_float2(0.f, 0.f);
+                    if (rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
+                    if (rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
+                    cfma(ev[j].a[x], LA, s);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) ev[j].S = cabs2(ev[j].a[0]) + cabs2(ev[j].a[1]);
+}
+
 // Compensated FP32 accumulator.
 struct Kahan {
     float s = 0.f, c = 0.f;
@@ -324,14 +441,167 @@ __device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, flo
     dAdG = make_float2(-g.y * s, g.x * s);
 }
 
+// End of an adjoint CTA: FP64 block sum of ln S (or w S), compensated FP32 block
+// sums of every gradient slot in thread order, one partial row per CTA.
+template <bool NORM, int BLOCK>
+__device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, bool bad,
+                                                unsigned *__restrict__ status, double *red,
+                                                const float2 *gsl, double *__restrict__ part,
+                                                int nslot)
+{
+    const int tid = threadIdx.x;
+    if (bad) atomicOr(status, 1u);
+    double t0 = acc0.value();
+    if (!NORM) t0 += (double)esum * 0.69314718055994530942;
+    t0 = warp_sum(t0);
+    if ((tid & 31) == 0) red[tid >> 5] = t0;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww];
+        part[(int64_t)blockIdx.x * nslot] = t;
+    }
+    // Block sums of every gradient slot, in thread order, as compensated FP32
+    // (Neumaier) sums written once in FP64: the FP32 slot values are summed to
+    // about 2^-48 of sum |x| without the FP64 pipe, which on this GPU runs at a
+    // small fraction of the FP32 rate.
+    for (int s2 = 1 + tid; s2 < nslot; s2 += BLOCK) {
+        const float *col = reinterpret_cast<const float *>(gsl + ((s2 - 1) >> 1) * BLOCK) + ((s2 - 1) & 1);
+        float sm = 0.f, cm = 0.f;
+        for (int j = 0; j < BLOCK; ++j) {
+            const float x = col[2 * j];
+            const float t = sm + x;
+            cm += (fabsf(sm) >= fabsf(x)) ? (sm - t) + x : (x - t) + sm;
+            sm = t;
+        }
+        part[(int64_t)blockIdx.x * nslot + s2] = (double)sm + (double)cm;
+    }
+}
+
+// All-cached adjoint kernel with NE events per thread and iteration: event e and
+// e + stride, ... (each load of a warp stays coalesced).  The constants of a
+// resonance and each gradient slot pair are read once for the NE events.  An
+// event index beyond n repeats a valid event with zero weight.
+template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS>
+__global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
+                                                         int64_t n, int wrec,
+                                                         double *__restrict__ part,
+                                                         unsigned *__restrict__ status,
+                                                         const float2 *__restrict__ lc, int nslot)
+{
+    constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
+    const ModelDev &md = c_md;
+    __shared__ double red[BLOCK / 32];
+    extern __shared__ float2 gsl[];  // [(nslot - 1) / 2][BLOCK]
+    const int tid = threadIdx.x;
+    const int npair = (nslot - 1) >> 1;
+    for (int i = 0; i < npair; ++i) gsl[i * BLOCK + tid] = make_float2(0.f, 0.f);
+    float2 *g = gsl + tid;
+    Kahan acc0;
+    int esum = 0;
+    bool bad = false;
+    const int nK = md.n_res - NZ;
+    const int64_t estride = (int64_t)gridDim.x * BLOCK;
+    for (int64_t e0 = blockIdx.x * (int64_t)BLOCK + tid; e0 < n; e0 += NE * estride) {
+        int64_t e[NE];
+        bool valid[NE];
+        float v[NE][NREC];
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+            const int64_t ej = e0 + j * estride;
+            valid[j] = ej < n;
+            e[j] = valid[j] ? ej : e0;
+#pragma unroll
+            for (int k = 0; k < NREC; ++k)
+                v[j][k] = record_used<true>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
+        }
+        EvState<NK, NZ> ev[NE];
+        eval_events_fx<NK, NZ, NE>(md, v, ev, lc, npad, e);
+        float2 as[NE][2];
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+            float scale = 0.f;
+            if (valid[j]) {
+                if (!NORM) {
+                    if (!(ev[j].S > 0.0f)) {
+                        bad = true;
+                    } else {
+                        int ex;
+                        float mant = frexpf(ev[j].S, &ex);
+                        if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
+                        acc0.add(logf(mant));
+                        esum += ex;
+                        scale = 2.0f * __frcp_rn(ev[j].S);
+                    }
+                } else {
+                    const float w = __ldg(rec + wrec * npad + e[j]);
+                    acc0.add(w * ev[j].S);
+                    scale = 2.0f * w;
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 2; ++x) as[j][x] = cscale(ev[j].a[x], scale);
+        }
+        float2 wl[NE][3];
+#pragma unroll
+        for (int j = 0; j < NE; ++j)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                float2 t = make_float2(0.f, 0.f);
+                cfma_conj(t, as[j][0], ev[j].Psi[l][0]);
+                cfma_conj(t, as[j][1], ev[j].Psi[l][1]);
+                wl[j][l] = t;
+            }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            if (k >= nK) continue;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                float2 gp = g[(3 * k + l) * BLOCK];
+#pragma unroll
+                for (int j = 0; j < NE; ++j) {
+                    const float2 B = l == 0 ? make_float2(-ev[j].B1[k].x, -ev[j].B1[k].y)
+                                            : (l == 1 ? ev[j].B0[k] : ev[j].B1[k]);
+                    gp.x = fmaf(B.x, wl[j][l].x, fmaf(-B.y, wl[j][l].y, gp.x));
+                    gp.y = fmaf(-B.x, wl[j][l].y, fmaf(-B.y, wl[j][l].x, gp.y));
+                }
+                g[(3 * k + l) * BLOCK] = gp;
+            }
+        }
+        if constexpr (NZ > 0) {
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) {
+                float2 g0 = g[(3 * NK + 2 * z) * BLOCK], g1 = g[(3 * NK + 2 * z + 1) * BLOCK];
+#pragma unroll
+                for (int j = 0; j < NE; ++j) {
+                    float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int x = 0; x < 2; ++x) {
+                        cfma_conj(w0, as[j][x], ev[j].Om0[z][x]);
+                        cfma_conj(w1, as[j][x], ev[j].Om1[z][x]);
+                    }
+                    const float2 A = ev[j].AZ[z];
+                    g0.x = fmaf(A.x, w0.x, fmaf(-A.y, w0.y, g0.x));
+                    g0.y = fmaf(-A.x, w0.y, fmaf(-A.y, w0.x, g0.y));
+                    g1.x = fmaf(A.x, w1.x, fmaf(-A.y, w1.y, g1.x));
+                    g1.y = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1.y));
+                }
+                g[(3 * NK + 2 * z) * BLOCK] = g0;
+                g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
+            }
+        }
+    }
+    grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, part, nslot);
+}
+
 // Per-thread gradient accumulators live in shared memory, which keeps the
-// register count low enough for 4 blocks/SM (5 when every lineshape is cached).  Slots come in (Re, Im) or
+// register count low enough for 4 blocks/SM.  Slots come in (Re, Im) or
 // (M, Gamma0) pairs, slots 1 + 2p and 2 + 2p forming pair p; pair p of thread t
 // is one float2 at p * BLOCK + t, so each update is one 64-bit load and store
 // and a warp's accesses cover every bank twice (two wavefronts, no conflict).
 // Events are read one per iteration with coalesced scalar loads.
-template <int NK, int NZ, bool NORM, int BLOCK, bool FX>
-__global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTAS_PER_SM) k_grad(const float *__restrict__ rec, int64_t npad,
+template <int NK, int NZ, bool NORM, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *__restrict__ rec, int64_t npad,
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                    double *__restrict__ part,
                                                    unsigned *__restrict__ status,
@@ -349,32 +619,12 @@ __global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTA
     int esum = 0;
     bool bad = false;
     const int nK = md.n_res - NZ;
-    const int64_t estride = (int64_t)gridDim.x * BLOCK;
-    // All-cached variant: the next event's records are loaded one iteration
-    // ahead (registers), so their latency overlaps the current event's
-    // arithmetic.  The generic variant has no registers to spare for it.
-    float vn[FX ? NREC : 1];
-    if constexpr (FX) {
-        const int64_t e0 = blockIdx.x * (int64_t)BLOCK + tid;
-#pragma unroll
-        for (int k = 0; k < NREC; ++k)
-            vn[k] = (record_used<FX>(k) && e0 < n) ? __ldg(rec + k * npad + e0) : 0.f;
-    }
-    for (int64_t e = blockIdx.x * (int64_t)BLOCK + tid; e < n; e += estride) {
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + tid; e < n; e += (int64_t)gridDim.x * BLOCK) {
         float v[NREC];
-        if constexpr (FX) {
 #pragma unroll
-            for (int k = 0; k < NREC; ++k) v[k] = vn[k];
-            const int64_t en = e + estride;
-#pragma unroll
-            for (int k = 0; k < NREC; ++k)
-                vn[k] = (record_used<FX>(k) && en < n) ? __ldg(rec + k * npad + en) : 0.f;
-        } else {
-#pragma unroll
-            for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
-        }
+        for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
         EvState<NK, NZ> ev;
-        eval_event<NK, NZ, FX>(md, v, ev, lc, npad, e);
+        eval_event<NK, NZ>(md, v, ev, lc, npad, e);
         float scale;
         if (!NORM) {
             if (!(ev.S > 0.0f)) { bad = true; continue; }
@@ -417,7 +667,7 @@ __global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTA
                 gp.y = fmaf(-Bl[l].x, wl[l].y, fmaf(-Bl[l].y, wl[l].x, gp.y));
                 g[(3 * k + l) * BLOCK] = gp;
             }
-            if (!FX && rs.fpos >= 0) {
+            if (rs.fpos >= 0) {
                 // y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
                 float d0, d1;
                 wigner_l0(rs, make_float2(ev.cK, ev.cK), ev.sK, d0, d1);
@@ -452,7 +702,7 @@ __global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTA
                 g1.y = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1.y));
                 g[(3 * NK + 2 * z) * BLOCK] = g0;
                 g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
-                if (!FX && rs.fpos >= 0) {
+                if (rs.fpos >= 0) {
                     float2 y = make_float2(0.f, 0.f);
                     if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
                     if (rs.zcol1 >= 0) cfma(y, md.zc[z][1], w1);
@@ -467,32 +717,7 @@ __global__ void __launch_bounds__(BLOCK, FX ? GRAD_CTAS_PER_SM_CACHED : GRAD_CTA
             }
         }
     }
-    if (bad) atomicOr(status, 1u);
-    double t0 = acc0.value();
-    if (!NORM) t0 += (double)esum * 0.69314718055994530942;
-    t0 = warp_sum(t0);
-    if ((tid & 31) == 0) red[tid >> 5] = t0;
-    __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww];
-        part[(int64_t)blockIdx.x * nslot] = t;
-    }
-    // Block sums of every gradient slot, in thread order, as compensated FP32
-    // (Neumaier) sums written once in FP64: the FP32 slot values are summed to
-    // about 2^-48 of sum |x| without the FP64 pipe, which on this GPU runs at a
-    // small fraction of the FP32 rate.
-    for (int s2 = 1 + tid; s2 < nslot; s2 += BLOCK) {
-        const float *col = reinterpret_cast<const float *>(gsl + ((s2 - 1) >> 1) * BLOCK) + ((s2 - 1) & 1);
-        float sm = 0.f, cm = 0.f;
-        for (int j = 0; j < BLOCK; ++j) {
-            const float x = col[2 * j];
-            const float t = sm + x;
-            cm += (fabsf(sm) >= fabsf(x)) ? (sm - t) + x : (x - t) + sm;
-            sm = t;
-        }
-        part[(int64_t)blockIdx.x * nslot + s2] = (double)sm + (double)cm;
-    }
+    grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, part, nslot);
 }
 
 constexpr int EVAL_BLOCK = 256;
@@ -531,16 +756,29 @@ template <int NK, int NZ, bool NORM, bool FX>
 cudaError_t launch_grad_k(const LaunchArgs &a)
 {
     const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
-    if (smem > 48 * 1024) {   // above the default dynamic shared-memory limit
-        cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, NORM, GRAD_BLOCK, FX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    if constexpr (FX) {
+        auto kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, GRAD_EVENTS_PER_THREAD_CACHED, GRAD_CTAS_PER_SM_CACHED>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        return with_const_table(a.md, a.stream, [&]() {
+            kern<<<a.grid, GRAD_BLOCK, smem, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.part, a.status,
+                                                         a.lcache, a.nslot);
+            return cudaGetLastError();
+        });
+    } else {
+        if (smem > 48 * 1024) {   // above the default dynamic shared-memory limit
+            cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, NORM, GRAD_BLOCK>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        return with_const_table(a.md, a.stream, [&]() {
+            k_grad<NK, NZ, NORM, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
+                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache, a.nslot);
+            return cudaGetLastError();
+        });
     }
-    return with_const_table(a.md, a.stream, [&]() {
-        k_grad<NK, NZ, NORM, GRAD_BLOCK, FX><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-            a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache, a.nslot);
-        return cudaGetLastError();
-    });
 }
 
 template <int NK, int NZ>

@@ -26,10 +26,13 @@ struct LaunchArgs {
     bool all_fixed = false;          // no mass or width floats (with lcache: all lineshapes cached)
 };
 
-// Resident CTAs per SM of the adjoint kernel (its __launch_bounds__): the
-// variant whose lineshapes all come from the basis cache needs fewer registers.
+// Resident CTAs per SM of the adjoint kernels (their __launch_bounds__).  The
+// all-cached variant (k_grad_fx) evaluates two events per thread in lock-step,
+// reading each resonance's constants and each gradient slot once for both, and
+// holds the state of both in about 150 registers: 3 CTAs per SM.
 constexpr int GRAD_CTAS_PER_SM = 4;
-constexpr int GRAD_CTAS_PER_SM_CACHED = 5;
+constexpr int GRAD_CTAS_PER_SM_CACHED = 3;
+constexpr int GRAD_EVENTS_PER_THREAD_CACHED = 2;
 
 int nk_bucket(int nk);
 // Gradient slots: ln S (or w S), 6 per K* of the bucket, 4 per Z, and 2 (mass,
