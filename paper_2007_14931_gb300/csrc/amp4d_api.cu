@@ -64,7 +64,7 @@ struct amp4d_model {
     double prof_ms[4] = {0, 0, 0, 0};
     int64_t prof_n[4] = {0, 0, 0, 0};
     int *d_slot_param = nullptr;
-    double *d_red = nullptr;     // 2 x nslot
+    unsigned long long *d_acc = nullptr;   // 128-bit sums: [data, points][nslot][hi, lo]
     double *d_out = nullptr, *h_out = nullptr;
     unsigned *d_status = nullptr;
     unsigned long long *d_bad = nullptr;
@@ -226,7 +226,7 @@ cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t 
 {
     const bool fast = mo->n_float == 0 && mo->table_built;
     cudaError_t e = launch_build_table(mo->d_static, d_params, mo->d_md, mo->d_pscale, mo->d_status,
-                                       st, fast);
+                                       st, fast, mo->d_acc, 4 * mo->nslot);
     if (e == cudaSuccess && mo->n_float == 0) mo->table_built = true;
     return e;
 }
@@ -257,6 +257,7 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
     a.nslot = mo->nslot;
     a.all_fixed = mo->n_float == 0;
+    a.acc = (&s == &mo->ev) ? mo->d_acc : mo->d_acc + 2 * mo->nslot;
     return a;
 }
 
@@ -368,7 +369,9 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         if (rc) return rc;
     }
     CK(mark());
-    double *rd = model->d_red, *rn = model->d_red + model->nslot;
+    // The kernels add their sums to the 128-bit accumulators the table kernel
+    // zeroed; the finishing kernel reads them (no separate reduction launch).
+    const unsigned long long *ad = model->d_acc, *an = model->d_acc + 2 * model->nslot;
     if (use_gram(model)) {
         if (!model->gram_valid) {
             amp4d_status rc = build_gram(model, st);
@@ -376,19 +379,15 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         }
         const double von = model->mc.volume / (double)model->mc.n;
         if (with_grad) {
-            LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
-            CK(launch_grad(ad, false));
-            CK(mark());
-            CK(mark());
-            CK(launch_reduce_cols(model->ev.part, grad_grid(model, model->ev), model->nslot, rd, st));
+            LaunchArgs la = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
+            CK(launch_grad(la, false));
         } else {
-            LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
-            CK(launch_eval(ad, 0));
-            CK(mark());
-            CK(mark());
-            CK(launch_reduce_cols(model->ev.part, model->ev.grid_eval, 1, rd, st));
+            LaunchArgs la = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
+            CK(launch_eval(la, 0));
         }
-        CK(launch_finish_gram(rd, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
+        CK(mark());
+        CK(mark());
+        CK(launch_finish_gram(ad, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
                               model->n_param, (double)model->ev.n, model->ev.lnpq, von, d_params,
                               model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st,
                               (double)model->mc.n, partials ? 1 : 0));
@@ -397,37 +396,33 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         return AMP4D_OK;
     }
     if (with_grad) {
-        LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
-        CK(launch_grad(ad, false));
+        LaunchArgs ld = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
+        CK(launch_grad(ld, false));
         CK(mark());
-        LaunchArgs an = args_for(model, model->mc, model->mc.part, nullptr, st, grad_grid(model, model->mc));
-        CK(launch_grad(an, true));
+        LaunchArgs ln = args_for(model, model->mc, model->mc.part, nullptr, st, grad_grid(model, model->mc));
+        CK(launch_grad(ln, true));
         CK(mark());
-        CK(launch_reduce_cols(model->ev.part, grad_grid(model, model->ev), model->nslot, rd, st));
-        CK(launch_reduce_cols(model->mc.part, grad_grid(model, model->mc), model->nslot, rn, st));
         if (partials)
-            CK(launch_partials(rd, rn, model->d_slot_param, model->d_pscale, model->nslot,
+            CK(launch_partials(ad, an, model->d_slot_param, model->d_pscale, model->nslot,
                                model->n_param, (double)model->ev.n, model->ev.lnpq,
                                (double)model->mc.n, model->mc.volume, model->d_status, d_out, st));
         else
-            CK(launch_finish(rd, rn, model->d_slot_param, model->d_pscale, model->nslot,
+            CK(launch_finish(ad, an, model->d_slot_param, model->d_pscale, model->nslot,
                              model->n_param, (double)model->ev.n, model->ev.lnpq,
                              model->mc.volume / (double)model->mc.n, model->d_status, d_out, st));
     } else {
-        LaunchArgs ad = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
-        CK(launch_eval(ad, 0));
+        LaunchArgs ld = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
+        CK(launch_eval(ld, 0));
         CK(mark());
-        LaunchArgs an = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_eval);
-        CK(launch_eval(an, 1));
+        LaunchArgs ln = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_eval);
+        CK(launch_eval(ln, 1));
         CK(mark());
-        CK(launch_reduce_cols(model->ev.part, model->ev.grid_eval, 1, rd, st));
-        CK(launch_reduce_cols(model->mc.part, model->mc.grid_eval, 1, rn, st));
         if (partials)
-            CK(launch_partials(rd, rn, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
+            CK(launch_partials(ad, an, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
                                model->ev.lnpq, (double)model->mc.n, model->mc.volume,
                                model->d_status, d_out, st));
         else
-            CK(launch_finish(rd, rn, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
+            CK(launch_finish(ad, an, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
                              model->ev.lnpq, model->mc.volume / (double)model->mc.n,
                              model->d_status, d_out, st));
     }
@@ -555,7 +550,7 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
         e = cudaMemcpy(model->d_static, &ms, sizeof ms, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&model->d_slot_param, model->nslot * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&model->d_red, 2 * model->nslot * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_acc, 4 * model->nslot * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&model->h_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_status, sizeof(unsigned));
@@ -593,7 +588,7 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
         for (cudaEvent_t e : v) cudaEventDestroy(e);
     for (cudaEvent_t e : model->ev_pool) cudaEventDestroy(e);
     if (model->d_slot_param) cudaFree(model->d_slot_param);
-    if (model->d_red) cudaFree(model->d_red);
+    if (model->d_acc) cudaFree(model->d_acc);
     if (model->d_out) cudaFree(model->d_out);
     if (model->h_out) cudaFreeHost(model->h_out);
     if (model->d_status) cudaFree(model->d_status);

@@ -97,6 +97,36 @@ struct ModelDev {
 };
 
 // ----------------------------------------------------------------------------
+// Exact, order-independent sums across CTAs: a 128-bit two's-complement
+// fixed-point integer per quantity, a[0] = high word (units of 1), a[1] = low
+// word (units of 2^-64).  Adding a double x (|x| < 2^62) converts it exactly
+// (its fraction has at most 52 significant bits below the binary point that
+// matter; smaller contributions than 2^-64 are dropped) and adds it with two
+// 64-bit atomics, carrying out of the low word.  Integer addition is
+// associative, so the total is the same bits whatever order the CTAs finish in.
+// ----------------------------------------------------------------------------
+// A value that is not finite or not below 2^62 in magnitude cannot be added; it
+// sets status bit 1 (the same domain flag as S <= 0), so it is never dropped
+// silently.
+__device__ __forceinline__ void acc128_add(unsigned long long *a, double x, unsigned *status)
+{
+    if (!(fabs(x) < 0x1p62)) {
+        atomicOr(status, 1u);
+        return;
+    }
+    const double fl = floor(x);
+    const unsigned long long hi = (unsigned long long)(long long)fl;
+    const unsigned long long lo = (unsigned long long)((x - fl) * 0x1p64);
+    const unsigned long long old = atomicAdd(a + 1, lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    atomicAdd(a, hi + carry);
+}
+__device__ __forceinline__ double acc128_value(const unsigned long long *a)
+{
+    return (double)(long long)a[0] + (double)a[1] * 0x1p-64;
+}
+
+// ----------------------------------------------------------------------------
 // Complex helpers
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)

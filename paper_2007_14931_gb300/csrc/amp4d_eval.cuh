@@ -8,7 +8,7 @@
 //   a_xi = sum_k c_k B_k,xi and S = |a_+|^2 + |a_-|^2 (Eq. 5, 12).
 // Data kernels sum ln S, normalisation kernels sum w S; each thread keeps a
 // compensated FP32 sum (ln S split as ln(mantissa) + exponent ln 2), blocks
-// reduce in FP64 and write one partial per block.
+// reduce in FP64 and add their sums to exact 128-bit accumulators (acc128_add).
 // Instantiated per resonance-count bucket in amp4d_eval_nk*.cu.
 #pragma once
 #include <cmath>
@@ -334,8 +334,10 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Block sum in FP64 (fixed order), added to the 128-bit accumulator acc.
 template <int BLOCK>
-__device__ __forceinline__ void block_write(double v, double *smem, double *out)
+__device__ __forceinline__ void block_accumulate(double v, double *smem, unsigned long long *acc,
+                                                 unsigned *status)
 {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -344,7 +346,7 @@ __device__ __forceinline__ void block_write(double v, double *smem, double *out)
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < BLOCK / 32; ++i) t += smem[i];
-        *out = t;
+        acc128_add(acc, t, status);
     }
 }
 
@@ -373,14 +375,14 @@ __device__ __forceinline__ constexpr bool record_used(int k)
 template <int NK, int NZ, int MODE, int BLOCK, bool FX>
 __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, int64_t npad,
                                                 int64_t n, int wrec, const ModelDev *__restrict__ gmd,
-                                                double *__restrict__ part, float *__restrict__ S_out,
+                                                unsigned long long *__restrict__ acc, float *__restrict__ S_out,
                                                 unsigned *__restrict__ status,
                                                 const float2 *__restrict__ lc)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     const ModelDev &md = c_md;   // gmd is its source (copied by with_const_table)
     __shared__ double red[BLOCK / 32];
-    Kahan acc;
+    Kahan ksum;
     int esum = 0;
     bool bad = false;
     // One event per thread and iteration, coalesced scalar loads of every record.
@@ -396,19 +398,19 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
             int ex;
             float mant = frexpf(ev.S, &ex);
             if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
-            acc.add(logf(mant));
+            ksum.add(logf(mant));
             esum += ex;
         } else if (MODE == MODE_SUM_WS) {
-            acc.add(__ldg(rec + wrec * npad + e) * ev.S);
+            ksum.add(__ldg(rec + wrec * npad + e) * ev.S);
         } else {
             S_out[e] = ev.S;
         }
     }
     if (MODE == MODE_WRITE) return;
     if (bad) atomicOr(status, 1u);
-    double tot = acc.value();
+    double tot = ksum.value();
     if (MODE == MODE_SUM_LNS) tot += (double)esum * 0.69314718055994530942;
-    block_write<BLOCK>(tot, red, part + blockIdx.x);
+    block_accumulate<BLOCK>(tot, red, acc, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -442,11 +444,12 @@ __device__ __forceinline__ void lineshape_derivs(const ResDev &rs, float2 A, flo
 }
 
 // End of an adjoint CTA: FP64 block sum of ln S (or w S), compensated FP32 block
-// sums of every gradient slot in thread order, one partial row per CTA.
+// sums of every gradient slot in thread order, each added to its 128-bit
+// accumulator (acc + 2 s for slot s).
 template <bool NORM, int BLOCK>
 __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, bool bad,
                                                 unsigned *__restrict__ status, double *red,
-                                                const float2 *gsl, double *__restrict__ part,
+                                                const float2 *gsl, unsigned long long *__restrict__ acc,
                                                 int nslot)
 {
     const int tid = threadIdx.x;
@@ -459,7 +462,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
     if (tid == 0) {
         double t = 0.0;
         for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww];
-        part[(int64_t)blockIdx.x * nslot] = t;
+        acc128_add(acc, t, status);
     }
     // Block sums of every gradient slot, in thread order, as compensated FP32
     // (Neumaier) sums written once in FP64: the FP32 slot values are summed to
@@ -474,7 +477,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
             cm += (fabsf(sm) >= fabsf(x)) ? (sm - t) + x : (x - t) + sm;
             sm = t;
         }
-        part[(int64_t)blockIdx.x * nslot + s2] = (double)sm + (double)cm;
+        acc128_add(acc + 2 * s2, (double)sm + (double)cm, status);
     }
 }
 
@@ -485,7 +488,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
-                                                         double *__restrict__ part,
+                                                         unsigned long long *__restrict__ acc,
                                                          unsigned *__restrict__ status,
                                                          const float2 *__restrict__ lc, int nslot)
 {
@@ -591,7 +594,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             }
         }
     }
-    grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, part, nslot);
+    grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, acc, nslot);
 }
 
 // Per-thread gradient accumulators live in shared memory, which keeps the
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 template <int NK, int NZ, bool NORM, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *__restrict__ rec, int64_t npad,
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
-                                                   double *__restrict__ part,
+                                                   unsigned long long *__restrict__ acc,
                                                    unsigned *__restrict__ status,
                                                    const float2 *__restrict__ lc, int nslot)
 {
@@ -717,7 +720,7 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
             }
         }
     }
-    grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, part, nslot);
+    grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, acc, nslot);
 }
 
 constexpr int EVAL_BLOCK = 256;
@@ -730,15 +733,15 @@ cudaError_t launch_eval_fx(const LaunchArgs &a, int mode)
         switch (mode) {
         case MODE_SUM_LNS:
             k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
+                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
             break;
         case MODE_SUM_WS:
             k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
+                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
             break;
         default:
             k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.out, a.status, a.lcache);
+                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
             break;
         }
         return cudaGetLastError();
@@ -763,7 +766,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
             if (e != cudaSuccess) return e;
         }
         return with_const_table(a.md, a.stream, [&]() {
-            kern<<<a.grid, GRAD_BLOCK, smem, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.part, a.status,
+            kern<<<a.grid, GRAD_BLOCK, smem, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.acc, a.status,
                                                          a.lcache, a.nslot);
             return cudaGetLastError();
         });
@@ -775,7 +778,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
         }
         return with_const_table(a.md, a.stream, [&]() {
             k_grad<NK, NZ, NORM, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.part, a.status, a.lcache, a.nslot);
+                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.status, a.lcache, a.nslot);
             return cudaGetLastError();
         });
     }

@@ -49,20 +49,21 @@ __global__ void k_reduce_cols(const double *__restrict__ part, int nblk, int nco
 // out: [0] nll, [1] sum ln S, [2] sum ln pq, [3] I, [4] N, [5] status bits
 // (1: domain, 2: invalid parameters), [6..] grad.
 // ---------------------------------------------------------------------------
-__global__ void k_finish(const double *__restrict__ rd, const double *__restrict__ rn,
+__global__ void k_finish(const unsigned long long *__restrict__ ad, const unsigned long long *__restrict__ an,
                          const int *__restrict__ slot_param, const double *__restrict__ pscale,
                          int nslot, int nparam,
                          double n_events, double lnpq, double vol_over_n,
                          const unsigned *__restrict__ status, double *__restrict__ out)
 {
-    const double I = vol_over_n * rn[0];
+    const double rd0 = acc128_value(ad), rn0 = acc128_value(an);
+    const double I = vol_over_n * rn0;
     unsigned st = *status;
-    const double nll = -2.0 * (rd[0] + lnpq - n_events * log(I));
+    const double nll = -2.0 * (rd0 + lnpq - n_events * log(I));
     if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
     const bool bad = st != 0u;
     if (threadIdx.x == 0) {
         out[0] = bad ? INFINITY : nll;
-        out[1] = rd[0];
+        out[1] = rd0;
         out[2] = lnpq;
         out[3] = I;
         out[4] = n_events;
@@ -74,7 +75,9 @@ __global__ void k_finish(const double *__restrict__ rd, const double *__restrict
     for (int s = 1 + threadIdx.x; s < nslot; s += blockDim.x) {
         const int p = slot_param[s];
         if (p >= 0)
-            out[6 + p] = bad ? 0.0 : -2.0 * pscale[p] * (rd[s] - n_events * vol_over_n * rn[s] / I);
+            out[6 + p] = bad ? 0.0
+                             : -2.0 * pscale[p] *
+                                   (acc128_value(ad + 2 * s) - n_events * vol_over_n * acc128_value(an + 2 * s) / I);
     }
 }
 
@@ -85,17 +88,17 @@ __global__ void k_finish(const double *__restrict__ rd, const double *__restrict
 // union of the shards), [4] M, [5] status bits, [6 .. 6+P) d(sum ln S)/dtheta,
 // [6+P .. 6+2P) dT/dtheta.  No logarithm of I is taken here.
 // ---------------------------------------------------------------------------
-__global__ void k_partials(const double *__restrict__ rd, const double *__restrict__ rn,
+__global__ void k_partials(const unsigned long long *__restrict__ ad, const unsigned long long *__restrict__ an,
                            const int *__restrict__ slot_param, const double *__restrict__ pscale,
                            int nslot, int nparam, double n_events, double lnpq, double n_points,
                            double volume, const unsigned *__restrict__ status,
                            double *__restrict__ out)
 {
     if (threadIdx.x == 0) {
-        out[0] = rd[0];
+        out[0] = acc128_value(ad);
         out[1] = lnpq;
         out[2] = n_events;
-        out[3] = volume * rn[0];
+        out[3] = volume * acc128_value(an);
         out[4] = n_points;
         out[5] = (double)*status;
     }
@@ -105,8 +108,8 @@ __global__ void k_partials(const double *__restrict__ rd, const double *__restri
     for (int s = 1 + threadIdx.x; s < nslot; s += blockDim.x) {
         const int p = slot_param[s];
         if (p >= 0) {
-            out[6 + p] = pscale[p] * rd[s];
-            out[6 + nparam + p] = volume * pscale[p] * rn[s];
+            out[6 + p] = pscale[p] * acc128_value(ad + 2 * s);
+            out[6 + nparam + p] = volume * pscale[p] * acc128_value(an + 2 * s);
         }
     }
 }
@@ -119,7 +122,7 @@ __global__ void k_partials(const double *__restrict__ rd, const double *__restri
 // dI/dIm c'_k = 2 vol_over_n ((Gv)_2k - (Gu)_2k+1).  One block; fixed order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_finish_gram(
-    const double *__restrict__ rd, const int *__restrict__ slot_param,
+    const unsigned long long *__restrict__ ad, const int *__restrict__ slot_param,
     const double *__restrict__ pscale, int nslot, int ncol, int nparam, double n_events,
     double lnpq, double vol_over_n, const double *__restrict__ params, const double *__restrict__ G,
     const unsigned *__restrict__ status, double *__restrict__ out, int with_grad, double n_points,
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(256) k_finish_gram(
         // Shard partials (layout of k_partials) with T = V (u^T G u + v^T G v).
         const double volume = vol_over_n * n_points;
         if (t == 0) {
-            out[0] = rd[0];
+            out[0] = acc128_value(ad);
             out[1] = lnpq;
             out[2] = n_events;
             out[3] = volume * q;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(256) k_finish_gram(
         for (int s = 1 + t; s < nslot; s += blockDim.x) {
             const int p = slot_param[s];
             if (p < 0) continue;
-            out[6 + p] = pscale[p] * rd[s];
+            out[6 + p] = pscale[p] * acc128_value(ad + 2 * s);
             if (p < dim) {
                 const int k = p >> 1;
                 const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1])
@@ -194,10 +197,11 @@ __global__ void __launch_bounds__(256) k_finish_gram(
     if (t == 0) {
         const double I = vol_over_n * q;
         unsigned st = *status;
-        const double nll = -2.0 * (rd[0] + lnpq - n_events * log(I));
+        const double rd0 = acc128_value(ad);
+        const double nll = -2.0 * (rd0 + lnpq - n_events * log(I));
         if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
         out[0] = st ? INFINITY : nll;
-        out[1] = rd[0];
+        out[1] = rd0;
         out[2] = lnpq;
         out[3] = I;
         out[4] = n_events;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(256) k_finish_gram(
         if (p < 0 || p >= dim || Iv == 0.0) continue;
         const int k = p >> 1;
         const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1]) : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
-        out[6 + p] = -2.0 * pscale[p] * (rd[s] - n_events * vol_over_n * dq / Iv);
+        out[6 + p] = -2.0 * pscale[p] * (acc128_value(ad + 2 * s) - n_events * vol_over_n * dq / Iv);
     }
 }
 
@@ -281,9 +285,11 @@ __device__ __forceinline__ void pack_pairs(float2 hi, float2 lo, float sg, float
 
 __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *__restrict__ params,
                               ModelDev *__restrict__ md, double *__restrict__ pscale,
-                              unsigned *__restrict__ status)
+                              unsigned *__restrict__ status, unsigned long long *__restrict__ acc,
+                              int nacc)
 {
     const int t = threadIdx.x;
+    for (int i = t; i < nacc; i += blockDim.x) acc[i] = 0ull;   // this evaluation's sums
     __shared__ int bad, sbad;   // any invalid input; invalid pole constants of a fixed resonance
     if (t == 0) bad = sbad = 0;
     __syncthreads();
@@ -432,9 +438,11 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
 // same FP64 arithmetic as k_build_table (identical bits).
 __global__ void k_update_couplings(const ModelStatic *__restrict__ st, const double *__restrict__ params,
                                    ModelDev *__restrict__ md, const double *__restrict__ pscale,
-                                   unsigned *__restrict__ status)
+                                   unsigned *__restrict__ status, unsigned long long *__restrict__ acc,
+                                   int nacc)
 {
     const int t = threadIdx.x;
+    for (int i = t; i < nacc; i += blockDim.x) acc[i] = 0ull;   // this evaluation's sums
     __shared__ int bad;
     if (t == 0) bad = 0;
     __syncthreads();
@@ -540,17 +548,17 @@ cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *o
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_param,
+cudaError_t launch_finish(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                           const double *pscale, int nslot, int nparam, double n_events,
                           double lnpq, double vol_over_n, const unsigned *status, double *out,
                           cudaStream_t s)
 {
-    k_finish<<<1, 128, 0, s>>>(rd, rn, slot_param, pscale, nslot, nparam, n_events, lnpq,
+    k_finish<<<1, 128, 0, s>>>(ad, an, slot_param, pscale, nslot, nparam, n_events, lnpq,
                                vol_over_n, status, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
+cudaError_t launch_finish_gram(const unsigned long long *ad, const int *slot_param, const double *pscale,
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
                                const unsigned *status, double *out, int with_grad, cudaStream_t s,
@@ -562,30 +570,30 @@ cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const do
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_finish_gram<<<1, 256, smem, s>>>(rd, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
+    k_finish_gram<<<1, 256, smem, s>>>(ad, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
                                        vol_over_n, params, G, status, out, with_grad, n_points,
                                        partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_partials(const double *rd, const double *rn, const int *slot_param,
+cudaError_t launch_partials(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                             const double *pscale, int nslot, int nparam, double n_events,
                             double lnpq, double n_points, double volume, const unsigned *status,
                             double *out, cudaStream_t s)
 {
-    k_partials<<<1, 128, 0, s>>>(rd, rn, slot_param, pscale, nslot, nparam, n_events, lnpq,
+    k_partials<<<1, 128, 0, s>>>(ad, an, slot_param, pscale, nslot, nparam, n_events, lnpq,
                                  n_points, volume, status, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_table(const ModelStatic *st, const double *params, ModelDev *md,
                                double *pscale, unsigned *status, cudaStream_t s,
-                               bool couplings_only)
+                               bool couplings_only, unsigned long long *acc, int nacc)
 {
     if (couplings_only)
-        k_update_couplings<<<1, 64, 0, s>>>(st, params, md, pscale, status);
+        k_update_couplings<<<1, 64, 0, s>>>(st, params, md, pscale, status, acc, nacc);
     else
-        k_build_table<<<1, 64, 0, s>>>(st, params, md, pscale, status);
+        k_build_table<<<1, 64, 0, s>>>(st, params, md, pscale, status, acc, nacc);
     return cudaGetLastError();
 }
 

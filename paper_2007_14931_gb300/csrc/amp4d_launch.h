@@ -15,7 +15,8 @@ struct LaunchArgs {
     int64_t npad, n;         // padded and true event counts
     int wrec;                // record index of the weights (normalisation points)
     const ModelDev *md;      // device model table
-    double *part;            // per-block partials
+    double *part;            // per-block partials (ingest)
+    unsigned long long *acc = nullptr;  // 128-bit accumulators of the sums (evaluation kernels)
     float *out;              // per-event output (MODE_WRITE)
     unsigned *status;        // error flags
     int grid;
@@ -48,22 +49,24 @@ cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *o
                                cudaStream_t s);
 cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double inv_I, float *S,
                              cudaStream_t s);
-cudaError_t launch_finish(const double *rd, const double *rn, const int *slot_param,
+cudaError_t launch_finish(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                           const double *pscale, int nslot, int nparam, double n_events,
                           double lnpq, double vol_over_n, const unsigned *status, double *out,
                           cudaStream_t s);
 
 // couplings_only: refresh the folded couplings of a table whose masses and
 // widths are all fixed and which has had one full build.
+// acc (nacc words, may be null): the evaluation's 128-bit accumulators, zeroed.
 cudaError_t launch_build_table(const ModelStatic *st, const double *params, ModelDev *md,
                                double *pscale, unsigned *status, cudaStream_t s,
-                               bool couplings_only = false);
-cudaError_t launch_finish_gram(const double *rd, const int *slot_param, const double *pscale,
+                               bool couplings_only = false, unsigned long long *acc = nullptr,
+                               int nacc = 0);
+cudaError_t launch_finish_gram(const unsigned long long *ad, const int *slot_param, const double *pscale,
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
                                const unsigned *status, double *out, int with_grad, cudaStream_t s,
                                double n_points = 0.0, int partials = 0);
-cudaError_t launch_partials(const double *rd, const double *rn, const int *slot_param,
+cudaError_t launch_partials(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                             const double *pscale, int nslot, int nparam, double n_events,
                             double lnpq, double n_points, double volume, const unsigned *status,
                             double *out, cudaStream_t s);
