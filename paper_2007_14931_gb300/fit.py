@@ -99,25 +99,30 @@ class MinResult:
     history: list = field(default_factory=list)
 
 
-def migrad(fg, x0, tol=0.1, errordef=1.0, maxiter=500, init_step=None):
-    """Minimise f with gradient: fg(x) -> (f, g).  Returns a MinResult."""
+def migrad(fg, x0, tol=0.1, errordef=1.0, maxiter=500, init_step=None, V0=None):
+    """Minimise f with gradient: fg(x) -> (f, g).  Returns a MinResult.  V0: an
+    initial inverse-Hessian estimate (positive definite), e.g. from HESSE."""
     x = np.array(x0, dtype=np.float64)
     n = len(x)
     f, g = fg(x)
     nfcn = 1
     if not math.isfinite(f):
         raise ValueError("starting point has a non-finite function value")
-    # Initial V from the diagonal of the Hessian (forward differences of the gradient).
-    h = np.array(init_step if init_step is not None else 1e-4 * np.maximum(np.abs(x), 1e-2))
-    diag = np.empty(n)
-    for i in range(n):
-        xp = x.copy()
-        xp[i] += h[i]
-        fp, gpi = fg(xp)
-        nfcn += 1
-        d = (gpi[i] - g[i]) / h[i]
-        diag[i] = d if d > 0 else abs(g[i]) / max(abs(h[i]), 1e-12) + 1.0
-    V = np.diag(1.0 / diag)
+    if V0 is not None:
+        V = np.array(V0, dtype=np.float64)
+        diag = 1.0 / np.maximum(np.diag(V), 1e-300)
+    else:
+        # Initial V from the diagonal of the Hessian (forward differences of the gradient).
+        h = np.array(init_step if init_step is not None else 1e-4 * np.maximum(np.abs(x), 1e-2))
+        diag = np.empty(n)
+        for i in range(n):
+            xp = x.copy()
+            xp[i] += h[i]
+            fp, gpi = fg(xp)
+            nfcn += 1
+            d = (gpi[i] - g[i]) / h[i]
+            diag[i] = d if d > 0 else abs(g[i]) / max(abs(h[i]), 1e-12) + 1.0
+        V = np.diag(1.0 / diag)
     edm_stop = 0.002 * tol * errordef
     hist = []
     converged = False
@@ -210,25 +215,81 @@ class FitResult:
     edm: float
     nfcn: int
     converged: bool
+    hessian: np.ndarray | None = None   # H of -2 ln L at the minimum (HESSE), if computed
+
+    def well_constrained(self, rel=1e-6):
+        """Eigen-decomposition of the Hessian restricted to the directions the data
+        constrain: (eigenvalues, eigenvectors as columns) with lambda > rel lambda_max.
+        Weak modes (a spin-4 state near the kinematic edge, interference ambiguities)
+        have curvature near zero or, within the gradient's rounding noise, below it."""
+        w, V = np.linalg.eigh(self.hessian)
+        keep = w > rel * w.max()
+        return w[keep], V[:, keep]
 
 
-def fit(eval_nll_grad, par: Parametrization, start_params, tol=0.1, with_hesse=True, maxiter=500):
+def _two_pass_hesse(gfun, x):
+    """H of -2 ln L at x from central differences of the gradient, in two passes
+    (as MINUIT scales its steps to the curvature): a small fixed step gives the
+    diagonal of H (large signal), then the full H is differenced over 0.2 of each
+    parameter's conditional standard error sqrt(2 / H_ii).  A step of a fixed
+    small fraction of |theta| leaves the off-diagonal differences too close to
+    the gradient's FP32 rounding noise once the data set is large."""
+    h0 = 1e-4 * np.maximum(np.abs(x), 1e-2)
+    hd = np.empty(len(x))
+    for i in range(len(x)):
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h0[i]
+        xm[i] -= h0[i]
+        hd[i] = (gfun(xp)[i] - gfun(xm)[i]) / (2 * h0[i])
+    step = np.where(hd > 0, 0.2 * np.sqrt(2.0 / np.where(hd > 0, hd, 1.0)), h0)
+    cov, H = hesse(gfun, x, step=step)
+    return cov, H, 4 * len(x)
+
+
+def _regularised_inverse(H, rel=1e-6):
+    """H^-1 with every eigenvalue floored at rel lambda_max: weak modes (curvature
+    near zero, or below it within the gradient's noise) take bounded steps."""
+    w, V = np.linalg.eigh(H)
+    w = np.maximum(w, rel * w.max())
+    return (V / w) @ V.T
+
+
+def fit(eval_nll_grad, par: Parametrization, start_params, tol=0.1, with_hesse=True, maxiter=500,
+        max_rounds=4):
     """Fit with a model's NLL + gradient callable (params -> (nll, grad)).
 
-    Works with the GPU model (``Model.eval_nll_grad``) or any other callable of
-    the same signature.
+    MIGRAD, then HESSE; as in MINUIT, when the estimated distance to the minimum
+    computed with the HESSE matrix (EDM = g^T H^-1 g / 2) is above the tolerance,
+    MIGRAD runs again from the HESSE matrix (the variable-metric estimate can be
+    far from the curvature in strongly correlated directions).  Works with the
+    GPU model (``Model.eval_nll_grad``) or any other callable of the same
+    signature.
     """
     def fg(theta):
         p = par.to_params(theta)
         f, gp = eval_nll_grad(p)
         return f, par.grad_to_theta(theta, gp)
 
+    gfun = lambda t: fg(t)[1]
+    edm_stop = 0.002 * tol
     th0 = par.from_params(start_params)
     r = migrad(fg, th0, tol=tol, maxiter=maxiter)
     cov = r.V * 2.0
     nf = r.nfcn
+    H = None
+    edm, converged = r.edm, r.converged
     if with_hesse:
-        cov, _ = hesse(lambda t: fg(t)[1], r.x)
-        nf += 2 * len(r.x)
+        for _ in range(max_rounds):
+            cov, H, k = _two_pass_hesse(gfun, r.x)
+            nf += k
+            Hinv = _regularised_inverse(H)
+            g = gfun(r.x)
+            nf += 1
+            edm = 0.5 * g @ Hinv @ g
+            converged = edm < edm_stop
+            if converged:
+                break
+            r = migrad(fg, r.x, tol=tol, maxiter=maxiter, V0=Hinv)
+            nf += r.nfcn
     err = np.sqrt(np.maximum(np.diag(cov), 0.0))
-    return FitResult(par.to_params(r.x), r.x, err, cov, r.fval, r.edm, nf, r.converged)
+    return FitResult(par.to_params(r.x), r.x, err, cov, r.fval, edm, nf, converged, H)
