@@ -164,8 +164,8 @@ amp4d_num_params = _proto("amp4d_num_params", C.c_int, [_vp])
 amp4d_set_events = _proto("amp4d_set_events", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int64, _vp])
 amp4d_set_norm_points = _proto("amp4d_set_norm_points", C.c_int,
                                [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_double, _vp])
-amp4d_eval_nll = _proto("amp4d_eval_nll", C.c_int, [_vp, _d, _d, _vp])
-amp4d_eval_nll_grad = _proto("amp4d_eval_nll_grad", C.c_int, [_vp, _d, _d, _d, _vp])
+amp4d_eval_nll = _proto("amp4d_eval_nll", C.c_int, [_vp, _vp, _vp, _vp])
+amp4d_eval_nll_grad = _proto("amp4d_eval_nll_grad", C.c_int, [_vp, _vp, _vp, _vp, _vp])
 amp4d_eval_terms = _proto("amp4d_eval_terms", C.c_int, [_vp, _d, _d, _vp])
 amp4d_eval_density = _proto("amp4d_eval_density", C.c_int, [_vp, _d, C.c_int, _vp, _vp])
 amp4d_enqueue_eval = _proto("amp4d_enqueue_eval", C.c_int, [_vp, C.c_int, _vp, _vp, _vp])
@@ -214,10 +214,17 @@ class Amp4dError(RuntimeError):
         self.code = code
 
 
+_torch_cuda = None
+
+
 def _stream_ptr(stream):
+    """cudaStream_t of a torch stream, an int, or (None) torch's current stream."""
+    global _torch_cuda
     if stream is None:
-        import torch
-        return torch.cuda.current_stream().cuda_stream
+        if _torch_cuda is None:
+            import torch
+            _torch_cuda = torch.cuda
+        return _torch_cuda.current_stream().cuda_stream
     return stream if isinstance(stream, int) else stream.cuda_stream
 
 
@@ -292,21 +299,20 @@ class Model:
 
     def eval_nll(self, params, stream=None, check=True):
         p = self._params(params)
-        out = C.c_double()
-        rc = amp4d_eval_nll(self.h, p.ctypes.data_as(_d), C.byref(out), _stream_ptr(stream))
+        out = np.empty(1)
+        rc = amp4d_eval_nll(self.h, p.ctypes.data, out.ctypes.data, _stream_ptr(stream))
         if check and rc not in (0, AMP4D_ERR_DOMAIN):
             self._check(rc)
-        return out.value
+        return float(out[0])
 
     def eval_nll_grad(self, params, stream=None):
         p = self._params(params)
-        out = C.c_double()
-        g = np.zeros(self.n_params)
-        rc = amp4d_eval_nll_grad(self.h, p.ctypes.data_as(_d), C.byref(out), g.ctypes.data_as(_d),
+        out = np.empty(1 + self.n_params)   # NLL, then the gradient
+        rc = amp4d_eval_nll_grad(self.h, p.ctypes.data, out.ctypes.data, out[1:].ctypes.data,
                                  _stream_ptr(stream))
         if rc not in (0, AMP4D_ERR_DOMAIN):
             self._check(rc)
-        return out.value, g
+        return float(out[0]), out[1:]
 
     def eval_terms(self, params, stream=None):
         p = self._params(params)

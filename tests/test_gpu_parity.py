@@ -265,3 +265,34 @@ def test_pdf_parity(A, name):
     err = np.abs(P - P_o)
     assert np.all(err[good] <= 2e-5 * P_o[good]), np.max(err[good] / P_o[good])
     assert np.all(err[~good] <= 2e-5 * mag[~good] * pq_o[~good] / I_o)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 127, 129, 4097, 100_003])
+def test_cached_all_fixed_ragged_sizes(A, n):
+    """The all-cached adjoint kernel takes two events per thread (e and e + grid
+    stride); at these sizes some threads have one real event and one beyond n.
+    Its NLL and gradient must match the oracle and the plain path, and repeated
+    calls (the Gram path, the couplings-only table update) must give the same bits."""
+    cfg = W.CONFIGS["large"]
+    res = cfg.resonances
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c)
+    ev = W.peaked_points(n, 19, res)
+    nm = W.uniform_points(max(n + 5, 70_001), 20)
+    om = O.Model(res)
+    nll_o, g_o, _, rc = om.nll(p, ev, nm, grad=True)
+    assert rc == 0
+    gc = A.Model(res, path=A.AMP4D_PATH_CACHED)
+    gc.set_events(*_dev(ev))
+    gc.set_norm_points(*_dev(nm))
+    gp = A.Model(res)
+    gp.set_events(*_dev(ev))
+    gp.set_norm_points(*_dev(nm))
+    nll_c, g_c = gc.eval_nll_grad(p)
+    nll_c2, g_c2 = gc.eval_nll_grad(p)
+    nll_p, g_p = gp.eval_nll_grad(p)
+    assert nll_c2 == nll_c and np.array_equal(g_c2, g_c)
+    tol_nll = 1e-4 + 1e-9 * abs(nll_o)
+    assert abs(nll_c - nll_o) < tol_nll and abs(nll_p - nll_o) < tol_nll
+    assert np.max(np.abs(g_c - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g_c - g_p)) <= 1e-5 * np.max(np.abs(g_o))
