@@ -250,6 +250,20 @@ amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *st
 amp4d_status amp4d_get_gram(amp4d_model *model, double *G, void *stream);
 
 /*
+ * Fit fractions (Eq. 13): FF_j = I_j / I, where I_j is the normalisation integral
+ * of the PDF with every helicity coupling outside resonance j set to zero and I
+ * the full one, both over the current normalisation points (so with the phase-
+ * space density p q).  The paper writes |S|^2 in the integrands although S
+ * (Eq. 12) is already a squared modulus; S is read.  The fractions need not sum
+ * to one (interference).  Computed from the normalisation Gram matrix, built at
+ * params when a mass or width floats or none is valid yet (which synchronises).
+ * params: host, amp4d_num_params doubles; ff: host, one double per resonance in
+ * the order given to amp4d_model_create.  Errors: ARG, STATE (no points),
+ * DOMAIN (I <= 0), TIMEOUT, CUDA.
+ */
+amp4d_status amp4d_fit_fractions(amp4d_model *model, const double *params, double *ff, void *stream);
+
+/*
  * Self-test of the tensor-core Gram accumulation on this GPU: X holds n points x
  * 2 rows x 64 columns of fixed-point values (int32, |X| <= 2^30, host or device
  * memory, caller-owned).  G_int (host, 64 x 64 int64) receives the kernel's

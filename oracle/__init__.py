@@ -250,6 +250,21 @@ class Model:
                           len(nm[0]), float(volume), 1 if grad else 0, _pd(out))
         return out
 
+    def fit_fractions(self, params, pts, w=None, volume=None):
+        """Fit fractions (Eq. 13) by their definition: FF_j = I_j / I, I_j the
+        normalisation integral over pts with every helicity coupling outside
+        resonance j set to zero (masses and widths unchanged)."""
+        pr = _f64(params)
+        I = self.norm(pr, pts, w=w, volume=volume)
+        out = np.zeros(len(self.res_list))
+        for R in range(len(self.res_list)):
+            pj = pr.copy()
+            for k, r in enumerate(self.col_res):
+                if r != R:
+                    pj[2 * k] = pj[2 * k + 1] = 0.0
+            out[R] = self.norm(pj, pts, w=w, volume=volume) / I
+        return out
+
     def gram(self, params, pts, w=None):
         m, cK, cpsi, phi = (_f64(a) for a in pts)
         D = 2 * self.n_cols

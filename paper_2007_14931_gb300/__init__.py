@@ -172,6 +172,7 @@ amp4d_enqueue_eval = _proto("amp4d_enqueue_eval", C.c_int, [_vp, C.c_int, _vp, _
 amp4d_eval_pdf = _proto("amp4d_eval_pdf", C.c_int, [_vp, _d, _vp, _vp])
 amp4d_build_gram = _proto("amp4d_build_gram", C.c_int, [_vp, _d, _vp])
 amp4d_get_gram = _proto("amp4d_get_gram", C.c_int, [_vp, _d, _vp])
+amp4d_fit_fractions = _proto("amp4d_fit_fractions", C.c_int, [_vp, _d, _d, _vp])
 amp4d_gram_selftest = _proto("amp4d_gram_selftest", C.c_int, [_vp, C.c_int64, _vp, _vp])
 amp4d_generate = _proto("amp4d_generate", C.c_int, [_vp, _d, C.c_uint64, C.c_int64, _vp, _vp, _vp, _vp, _vp])
 amp4d_proposal_train = _proto("amp4d_proposal_train", C.c_int,
@@ -203,7 +204,7 @@ EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "am
             "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample",
             "amp4d_mlp_loss_grad_noalloc", "amp4d_noalloc_last_error", "amp4d_eval_partials",
             "amp4d_enqueue_partials", "amp4d_combine_partials", "amp4d_shard_last_error",
-            "amp4d_eval_pdf"]
+            "amp4d_eval_pdf", "amp4d_fit_fractions"]
 
 MLP_NUM_PARAMS = 4545
 
@@ -344,6 +345,14 @@ class Model:
     def build_gram(self, params, stream=None):
         p = self._params(params)
         self._check(amp4d_build_gram(self.h, p.ctypes.data_as(_d), _stream_ptr(stream)))
+
+    def fit_fractions(self, params, stream=None):
+        """Fit fraction of every resonance (Eq. 13), in creation order (host float64)."""
+        p = self._params(params)
+        ff = np.zeros(len(self.res_list))
+        self._check(amp4d_fit_fractions(self.h, p.ctypes.data_as(_d), ff.ctypes.data_as(_d),
+                                        _stream_ptr(stream)))
+        return ff
 
     def get_gram(self, stream=None):
         d = 2 * self.n_cols

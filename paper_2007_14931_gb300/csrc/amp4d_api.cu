@@ -751,6 +751,51 @@ amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *st
     return build_gram(model, st);
 }
 
+amp4d_status amp4d_fit_fractions(amp4d_model *model, const double *params, double *ff, void *stream)
+{
+    if (!model || !params || !ff) return AMP4D_ERR_ARG;
+    if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "set_norm_points must come first");
+    // The Gram matrix at these masses and widths (fixed-mass models reuse it).
+    if (model->n_float > 0 || !model->gram_valid) {
+        const amp4d_status rc = amp4d_build_gram(model, params, stream);
+        if (rc) return rc;
+    } else {
+        const amp4d_status rc = check_params(model, params);
+        if (rc) return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = model->n_col, dim = 2 * K;
+    std::vector<double> G((size_t)dim * dim), kap(model->n_param);
+    CK(cudaMemcpyAsync(G.data(), model->d_G, G.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(kap.data(), model->d_pscale, kap.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // q(c) = u^T G u + v^T G v with u = (Re c', -Im c'), v = (Im c', Re c') per column,
+    // c'_k = kappa_k c_k the folded couplings (the Gram rows are the folded basis).
+    auto q_of = [&](int only_res) {
+        std::vector<double> u(dim, 0.0), v(dim, 0.0);
+        for (int k = 0; k < K; ++k) {
+            if (only_res >= 0 && model->col_res[k] != only_res) continue;
+            const double re = kap[2 * k] * params[2 * k], im = kap[2 * k] * params[2 * k + 1];
+            u[2 * k] = re; u[2 * k + 1] = -im;
+            v[2 * k] = im; v[2 * k + 1] = re;
+        }
+        double q = 0.0;
+        for (int i = 0; i < dim; ++i) {
+            double gu = 0.0, gv = 0.0;
+            for (int j = 0; j < dim; ++j) {
+                gu += G[(size_t)i * dim + j] * u[j];
+                gv += G[(size_t)i * dim + j] * v[j];
+            }
+            q += u[i] * gu + v[i] * gv;
+        }
+        return q;
+    };
+    const double qt = q_of(-1);
+    if (!(qt > 0.0)) return fail(model, AMP4D_ERR_DOMAIN, "I <= 0");
+    for (int r = 0; r < (int)model->res.size(); ++r) ff[r] = q_of(r) / qt;
+    return AMP4D_OK;
+}
+
 amp4d_status amp4d_get_gram(amp4d_model *model, double *G, void *stream)
 {
     if (!model || !G) return AMP4D_ERR_ARG;

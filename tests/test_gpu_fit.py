@@ -122,3 +122,37 @@ def test_large_fit_minimum_agrees_with_oracle(A):
     assert len(lam) >= len(rg.theta) - 5
     assert abs(nll_g - nll_o) <= 1e-9 * abs(nll_o)   # as for the full-size NLL parity
     assert np.max(np.abs(dev)) < 0.05
+
+
+def test_toy_pull_distributions(A):
+    """Toy study (the paper's pull distributions, Figs. 5-8): 40 data sets of 5000
+    events drawn by the GPU generator from the two-K* model, each fitted from a
+    perturbed start; for every free parameter the pulls (fitted - generated) /
+    error have mean within 0.6 of 0 (3.8 standard errors of the mean) and
+    standard deviation within [0.6, 1.5].  The 4e5 normalisation points are
+    shared by all toys (events / points = 0.0125)."""
+    cfg = W.CONFIGS["tiny"]
+    res = cfg.resonances
+    cols = W.columns(res)
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    fixed = [k for k, (R, l) in enumerate(cols) if res[R].name == "K*(892)" and l == 0][0]
+    c = c / c[fixed]
+    p_true = W.couplings_to_params(c)
+    par = F.Parametrization(len(c), 0, fixed_col=fixed, polar=True)
+    th_true = par.from_params(p_true)
+    gen = A.Model(res)
+    gm = A.Model(res, path=A.AMP4D_PATH_CACHED)
+    gm.set_norm_points(*(torch.from_numpy(a).cuda() for a in W.uniform_points(400_000, 41)))
+    pulls = []
+    for toy in range(40):
+        gm.set_events(*gen.generate(p_true, 5000, 1000 + toy))
+        c0 = W.perturbed_start(c, seed=toy)
+        c0[fixed] = 1.0
+        r = F.fit(gm.eval_nll_grad, par, W.couplings_to_params(c0), tol=0.1)
+        assert r.converged
+        pulls.append(_wrap(r.theta - th_true) / r.errors)
+    pulls = np.array(pulls)
+    mean, sd = pulls.mean(axis=0), pulls.std(axis=0, ddof=1)
+    print("toy pulls: mean", np.round(mean, 2), "sd", np.round(sd, 2))
+    assert np.all(np.abs(mean) < 0.6)
+    assert np.all((sd > 0.6) & (sd < 1.5))

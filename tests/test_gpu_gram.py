@@ -200,3 +200,22 @@ def test_basis_cache_reproduces_recompute_bit_for_bit(A):
     S0 = models[0].eval_density(p2, 0).cpu().numpy()
     S1 = models[1].eval_density(p2, 0).cpu().numpy()
     assert np.array_equal(S0, S1)
+
+
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+def test_fit_fractions_match_oracle(A, name):
+    """Eq. 13 from the tensor-core Gram matrix against the oracle's definition
+    (normalisation integrals with the other couplings zeroed) on the same points;
+    with floated masses the Gram is built at the given masses and widths."""
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c, W.float_mg_values(res, cfg.float_mg))
+    nm = W.uniform_points(65_537, 23)
+    gm = A.Model(res, float_names=cfg.float_mg, path=A.AMP4D_PATH_CACHED)
+    gm.set_events(*_dev(W.uniform_points(1000, 24)))
+    gm.set_norm_points(*_dev(nm))
+    ff = gm.fit_fractions(p)
+    ff_o = O.Model(res, float_names=cfg.float_mg).fit_fractions(p, nm)
+    print(name, "fit fractions", np.round(ff, 4), "sum", ff.sum())
+    assert np.allclose(ff, ff_o, rtol=1e-7, atol=1e-10)

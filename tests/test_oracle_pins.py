@@ -336,6 +336,45 @@ def test_pdf_integrates_to_one_tiny_model():
     assert tot / I1 == pytest.approx(1.0, abs=1e-10)
 
 
+# ---------------------------------------------------------------- fit fractions (Eq. 13)
+def test_fit_fraction_of_a_single_resonance_is_one():
+    res = [r for r in W.CONFIGS["tiny"].resonances if r.name == "K*(892)"]
+    mo = O.Model(res)
+    c = W.draw_couplings(res, 5)
+    pts = W.uniform_points(20000, 3)
+    assert mo.fit_fractions(W.couplings_to_params(c), pts)[0] == pytest.approx(1.0, abs=1e-14)
+
+
+def test_fit_fractions_of_different_spins_sum_to_one():
+    """K*(892) (J = 1) and K2*(1430) (J = 2): integrated over the full angular range
+    their interference vanishes (the phi integral removes lambda != lambda', and
+    int d^1_{l0} d^2_{l0} dcos = 0), so with an exact angular rule the two
+    fractions add up to one."""
+    res = W.CONFIGS["tiny"].resonances
+    mo = O.Model(res)
+    c = W.draw_couplings(res, W.CONFIGS["tiny"].coupling_seed)
+    p = W.couplings_to_params(c)
+    mn, mw = _m_rule(res)
+    cK, cpsi, phi, wt = _angular_rule()
+    M = np.repeat(mn, len(cK))
+    pts = (M, np.tile(cK, len(mn)), np.tile(cpsi, len(mn)), np.tile(phi, len(mn)))
+    wq = np.repeat(mw, len(cK)) * np.tile(wt, len(mn)) * \
+        np.array([O.breakup(W.M_B, m, W.M_PSI) * O.breakup(m, W.M_K, W.M_PI) for m in M])
+    ff = mo.fit_fractions(p, pts, w=wq, volume=1.0)
+    assert ff.sum() == pytest.approx(1.0, abs=1e-12)
+    assert np.all(ff > 0)
+
+
+def test_fit_fractions_invariant_under_global_phase_and_scale():
+    res = W.CONFIGS["kstar10_z"].resonances
+    mo = O.Model(res)
+    c = W.draw_couplings(res, 3)
+    pts = W.uniform_points(30000, 4)
+    f0 = mo.fit_fractions(W.couplings_to_params(c), pts)
+    f1 = mo.fit_fractions(W.couplings_to_params(c * 2.5 * np.exp(0.7j)), pts)
+    assert np.allclose(f0, f1, rtol=1e-12, atol=1e-15)
+
+
 def test_mc_normalisation_within_statistical_error():
     res = W.CONFIGS["tiny"].resonances
     mo = O.Model(res)
