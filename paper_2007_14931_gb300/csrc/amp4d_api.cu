@@ -79,6 +79,8 @@ struct amp4d_model {
     int gram_grid = 0;
     bool gram_valid = false;
     bool table_built = false;    // one full table build enqueued (all masses fixed)
+    bool kstar_fixed = true;     // no K* has a floating mass or width
+    bool z_float = false;        // some Z has a floating mass and width
     // learned proposal
     float *d_th = nullptr, *d_am = nullptr, *d_av = nullptr;   // FP32 master weights, Adam moments
     __nv_bfloat16 *d_wb = nullptr;                              // BF16 weights
@@ -234,7 +236,7 @@ cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t 
 // Grid of the adjoint kernel over a set: one full wave of the variant that runs.
 int grad_grid(const amp4d_model *mo, const EventSet &s)
 {
-    const bool cached = mo->path == AMP4D_PATH_CACHED && s.lcache_valid && mo->n_float == 0;
+    const bool cached = mo->path == AMP4D_PATH_CACHED && s.lcache_valid && mo->kstar_fixed;
     return cached ? s.grid_grad_cached : s.grid_grad;
 }
 
@@ -257,6 +259,8 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
     a.nslot = mo->nslot;
     a.all_fixed = mo->n_float == 0;
+    a.kstar_fixed = mo->kstar_fixed;
+    a.z_float = mo->z_float;
     a.acc = (&s == &mo->ev) ? mo->d_acc : mo->d_acc + 2 * mo->nslot;
     return a;
 }
@@ -519,7 +523,11 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
     for (int i = 0; i < n_res; ++i) {
         const amp4d_resonance &r = res[i];
         model->res_col[i] = model->n_col;
-        if (r.float_mg) model->res_fpos[i] = model->n_float++;
+        if (r.float_mg) {
+            model->res_fpos[i] = model->n_float++;
+            if (r.chain == AMP4D_CHAIN_KSTAR) model->kstar_fixed = false;
+            else model->z_float = true;
+        }
         if (r.chain == AMP4D_CHAIN_KSTAR) {
             if (r.J == 0) { model->col_res.push_back(i); model->col_lam.push_back(0); }
             else for (int l = -1; l <= 1; ++l) { model->col_res.push_back(i); model->col_lam.push_back(l); }

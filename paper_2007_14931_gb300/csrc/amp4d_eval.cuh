@@ -197,10 +197,12 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     ev.S = cabs2(ev.a[0]) + cabs2(ev.a[1]);
 }
 
-// All-cached evaluation of NE events at once (FX only): the per-resonance
-// constants are read once for all NE events.  r[j] holds the records of event
-// e[j]; lc is the basis cache [resonance][lcn].
-template <int NK, int NZ, int NE>
+// Evaluation of NE events at once when every K* lineshape comes from the basis
+// cache: the per-resonance constants are read once for all NE events.  r[j]
+// holds the records of event e[j]; lc is the basis cache [resonance][lcn].  ZF:
+// a Z resonance whose mass and width float is computed (Eq. 2-3) from the
+// Z-chain records, the others come from the cache.
+template <int NK, int NZ, int NE, bool ZF = false>
 __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
                                                EvState<NK, NZ> (&ev)[NE],
                                                const float2 *__restrict__ lc, int64_t lcn,
@@ -283,12 +285,24 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
             wigner_1(ctz, stz, d1t[j]);
         }
+        if constexpr (ZF) {
+#pragma unroll
+            for (int j = 0; j < NE; ++j) {
+                ev[j].mZ = r[j][REC_MZ];
+                ev[j].pZ = r[j][REC_PZ];
+                ev[j].qZ = r[j][REC_QZ];
+                ev[j].invmZ = __frcp_rn(ev[j].mZ);
+            }
+        }
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
             const ResDev &rs = md.zr[z];
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
-                const float2 LA = LZ[j][z];
+                float2 LA = LZ[j][z];
+                if constexpr (ZF) {
+                    if (rs.fpos >= 0) LA = lineshape(rs, ev[j].mZ, ev[j].invmZ, ev[j].pZ, ev[j].qZ).A;
+                }
                 float dz0, dz1;
                 wigner_l0(rs, make_float2(cZ[j], cZ[j]), sZ[j], dz0, dz1);
                 ev[j].AZ[z] = LA;
@@ -365,11 +379,11 @@ enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
 
 // Records read by eval_event<.., FX>: all of them, or without the masses and
 // momenta when every lineshape comes from the cache.
-template <bool FX>
+template <bool FX, bool ZF = false>
 __device__ __forceinline__ constexpr bool record_used(int k)
 {
-    return !FX || !(k == REC_M || k == REC_PHI || k == REC_P || k == REC_Q || k == REC_MZ ||
-                    k == REC_PZ || k == REC_QZ);
+    return !FX || !(k == REC_M || k == REC_PHI || k == REC_P || k == REC_Q ||
+                    (!ZF && (k == REC_MZ || k == REC_PZ || k == REC_QZ)));
 }
 
 template <int NK, int NZ, int MODE, int BLOCK, bool FX>
@@ -485,7 +499,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // e + stride, ... (each load of a warp stays coalesced).  The constants of a
 // resonance and each gradient slot pair are read once for the NE events.  An
 // event index beyond n repeats a valid event with zero weight.
-template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS>
+template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, bool ZF>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
                                                          unsigned long long *__restrict__ acc,
@@ -516,10 +530,10 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             e[j] = valid[j] ? ej : e0;
 #pragma unroll
             for (int k = 0; k < NREC; ++k)
-                v[j][k] = record_used<true>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
+                v[j][k] = record_used<true, ZF>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
         }
         EvState<NK, NZ> ev[NE];
-        eval_events_fx<NK, NZ, NE>(md, v, ev, lc, npad, e);
+        eval_events_fx<NK, NZ, NE, ZF>(md, v, ev, lc, npad, e);
         float2 as[NE][2];
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
@@ -574,7 +588,9 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
         if constexpr (NZ > 0) {
 #pragma unroll
             for (int z = 0; z < NZ; ++z) {
+                const ResDev &rs = md.zr[z];
                 float2 g0 = g[(3 * NK + 2 * z) * BLOCK], g1 = g[(3 * NK + 2 * z + 1) * BLOCK];
+                float2 gmg = make_float2(0.f, 0.f);   // scale dS/dM, dS/dG0 of a floated Z
 #pragma unroll
                 for (int j = 0; j < NE; ++j) {
                     float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
@@ -588,9 +604,29 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                     g0.y = fmaf(-A.x, w0.y, fmaf(-A.y, w0.x, g0.y));
                     g1.x = fmaf(A.x, w1.x, fmaf(-A.y, w1.y, g1.x));
                     g1.y = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1.y));
+                    if constexpr (ZF) {
+                        if (rs.fpos >= 0) {
+                            // y = sum_l' c_l' w_l', then scale dS/dM = Re(dA/dM y)
+                            float2 y = make_float2(0.f, 0.f);
+                            if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
+                            if (rs.zcol1 >= 0) cfma(y, md.zc[z][1], w1);
+                            const LineOut L = lineshape(rs, ev[j].mZ, ev[j].invmZ, ev[j].pZ, ev[j].qZ);
+                            float2 dM, dG;
+                            lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
+                            gmg.x += cmul(dM, y).x;
+                            gmg.y += cmul(dG, y).x;
+                        }
+                    }
                 }
                 g[(3 * NK + 2 * z) * BLOCK] = g0;
                 g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
+                if constexpr (ZF) {
+                    if (rs.fpos >= 0) {
+                        float2 &gm = g[(3 * NK + 2 * NZ + rs.fpos) * BLOCK];
+                        gm.x += gmg.x;
+                        gm.y += gmg.y;
+                    }
+                }
             }
         }
     }
@@ -760,7 +796,9 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
 {
     const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
     if constexpr (FX) {
-        auto kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, GRAD_EVENTS_PER_THREAD_CACHED, GRAD_CTAS_PER_SM_CACHED>;
+        auto kern = a.z_float
+                        ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, GRAD_EVENTS_PER_THREAD_CACHED, GRAD_CTAS_PER_SM_CACHED, true>
+                        : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, GRAD_EVENTS_PER_THREAD_CACHED, GRAD_CTAS_PER_SM_CACHED, false>;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
@@ -787,7 +825,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
 template <int NK, int NZ>
 cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
 {
-    const bool fx = a.lcache && a.all_fixed;
+    const bool fx = a.lcache && a.kstar_fixed;
     if (norm) return fx ? launch_grad_k<NK, NZ, true, true>(a) : launch_grad_k<NK, NZ, true, false>(a);
     return fx ? launch_grad_k<NK, NZ, false, true>(a) : launch_grad_k<NK, NZ, false, false>(a);
 }

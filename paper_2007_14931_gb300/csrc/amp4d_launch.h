@@ -25,6 +25,8 @@ struct LaunchArgs {
     const float2 *lcache = nullptr;  // basis cache of the set, or null (recompute)
     int nslot = 0;                   // gradient slots (grad_num_slots)
     bool all_fixed = false;          // no mass or width floats (with lcache: all lineshapes cached)
+    bool kstar_fixed = false;        // no K* mass or width floats (with lcache: K* lineshapes cached)
+    bool z_float = false;            // some Z mass and width float
 };
 
 // Resident CTAs per SM of the adjoint kernels (their __launch_bounds__).  The

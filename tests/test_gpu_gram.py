@@ -175,9 +175,12 @@ def test_cached_path_with_floating_mass_uses_points(A):
 
 
 def test_basis_cache_reproduces_recompute_bit_for_bit(A):
-    """The per-event basis cache holds the same lineshape values the plain path computes,
-    so the cached path's densities, and its NLL + gradient when a floated Z mass and
-    width force per-point normalisation, equal the plain path's exactly."""
+    """The per-event basis cache holds the same lineshape values the plain path
+    computes, so the cached path's densities equal the plain path's exactly.  With a
+    floated Z mass and width (per-point normalisation) the cached path runs the
+    two-events-per-thread kernel with the Z lineshape computed per event: its NLL
+    and gradient, summed in another order, agree to rounding (NLL 1e-9 relative,
+    gradient 1e-6 of |g|_inf), at the start point and after the Z mass moves."""
     cfg = W.CONFIGS["kstar10_z"]
     res = cfg.resonances
     fl = ["Z(4430)"]
@@ -191,12 +194,15 @@ def test_basis_cache_reproduces_recompute_bit_for_bit(A):
         gm.set_events(*_dev(ev))
         gm.set_norm_points(*_dev(nm))
         models.append(gm)
+    def close(a, b):
+        assert abs(a[0] - b[0]) <= 1e-9 * abs(a[0])
+        assert np.max(np.abs(a[1] - b[1])) <= 1e-6 * np.max(np.abs(a[1]))
     r_plain = models[0].eval_nll_grad(p)
     r_cached = models[1].eval_nll_grad(p)          # builds the caches
-    assert r_plain[0] == r_cached[0] and np.array_equal(r_plain[1], r_cached[1])
+    close(r_plain, r_cached)
     p2 = p.copy()
     p2[-2] += 0.01                                  # Z mass moves: computed on the fly
-    assert models[0].eval_nll_grad(p2)[0] == models[1].eval_nll_grad(p2)[0]
+    close(models[0].eval_nll_grad(p2), models[1].eval_nll_grad(p2))
     S0 = models[0].eval_density(p2, 0).cpu().numpy()
     S1 = models[1].eval_density(p2, 0).cpu().numpy()
     assert np.array_equal(S0, S1)
