@@ -123,7 +123,7 @@ def test_gram_matches_oracle(A, name, n_mc):
     assert np.array_equal(gm.get_gram(), G)  # deterministic
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
 def test_cached_path_nll_grad(A, name):
     cfg = W.CONFIGS[name]
     res = cfg.resonances
@@ -208,7 +208,7 @@ def test_basis_cache_reproduces_recompute_bit_for_bit(A):
     assert np.array_equal(S0, S1)
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
 def test_fit_fractions_match_oracle(A, name):
     """Eq. 13 from the tensor-core Gram matrix against the oracle's definition
     (normalisation integrals with the other couplings zeroed) on the same points;
@@ -225,3 +225,33 @@ def test_fit_fractions_match_oracle(A, name):
     ff_o = O.Model(res, float_names=cfg.float_mg).fit_fractions(p, nm)
     print(name, "fit fractions", np.round(ff, 4), "sum", ff.sum())
     assert np.allclose(ff, ff_o, rtol=1e-7, atol=1e-10)
+
+
+@pytest.mark.parametrize("name", ["large_float_z", "kstar10_2z"])
+def test_cached_path_floated_z_matches_oracle(A, name):
+    """K* fixed (lineshapes from the basis cache) and the Z masses and widths
+    floating: the two-events-per-thread kernel computes the Z lineshapes and
+    their mass/width adjoint per event, for the data and the per-point
+    normalisation.  NLL and full gradient (couplings, Z masses and widths)
+    against the oracle, at the start point and after the Z parameters move."""
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    fl = cfg.float_mg
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c, W.float_mg_values(res, fl))
+    ev = W.peaked_points(30_001, 5, res)
+    nm = W.uniform_points(60_003, 6)
+    gm = A.Model(res, float_names=fl, path=A.AMP4D_PATH_CACHED)
+    gm.set_events(*_dev(ev))
+    gm.set_norm_points(*_dev(nm))
+    om = O.Model(res, float_names=fl)
+    nz = 2 * len(fl)
+    for shift in (0.0, 0.02):
+        pp = p.copy()
+        pp[-nz::2] += shift            # every floated Z mass
+        nll_o, g_o, _, rc = om.nll(pp, ev, nm, grad=True)
+        assert rc == 0
+        nll, g = gm.eval_nll_grad(pp)
+        assert abs(nll - nll_o) < 1e-4 + 1e-9 * abs(nll_o)
+        assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+        assert np.all(np.abs(g[-nz:] - g_o[-nz:]) <= 1e-5 * np.abs(g_o[-nz:]) + 1e-6 * np.max(np.abs(g_o)))

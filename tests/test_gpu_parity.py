@@ -67,7 +67,7 @@ def _check_density(om, p, c, pts, S_gpu):
     return good.mean(), np.max(err[good] / S_o[good])
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
 @pytest.mark.parametrize("data", ["peaked", "uniform"])
 def test_density_parity(A, name, data):
     n = 20_003  # several tiles and a ragged tail (n % 4 = 3)
@@ -79,7 +79,7 @@ def test_density_parity(A, name, data):
     _check_density(om, p, c, nm, Sn)
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
 def test_nll_terms_parity(A, name):
     cfg, res, c, p, om, gm, ev, nm = _setup(A, name, 50_001, 200_003)
     nll_o, _, aux, rc = om.nll(p, ev, nm)
@@ -94,7 +94,7 @@ def test_nll_terms_parity(A, name):
     assert abs(nll - nll_o) < 1e-3
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10_z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z"])
 def test_nll_grad_parity_model_data(A, name):
     n = 20_000 if name == "tiny" else 8_000
     cfg, res, c, p, om, gm, ev, nm = _setup(A, name, n, 40_000, data="model")
@@ -249,7 +249,7 @@ def test_density_bias(A):
     assert abs(bias) < 5e-9 + 4 * sem
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10_z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z"])
 def test_pdf_parity(A, name):
     """P(e) = S p q / I per data event (Eq. 5 with the phase-space density): the
     oracle's S and p q over its own I, per event, with the per-event density
