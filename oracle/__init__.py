@@ -46,6 +46,8 @@ def lib():
             L.or_model_new.argtypes = [_d, C.c_double, C.c_double, C.c_int, _i, _i, _i, _i, _i,
                                        _d, _d, _d, _i]
             L.or_model_free.argtypes = [C.c_void_p]
+            L.or_model_set_lass.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                            C.c_double]
             L.or_num_cols.argtypes = [C.c_void_p]
             L.or_num_params.argtypes = [C.c_void_p]
             L.or_columns.argtypes = [C.c_void_p, _i, _i]
@@ -157,6 +159,12 @@ class Model:
                                     _pd(a["M"]), _pd(a["G0"]), _pd(a["r"]), _pi(a["flt"]))
         if not self.h:
             raise ValueError("oracle: bad model")
+        for i, r in enumerate(res_list):
+            if r.shape == W.SHAPE_LASS:
+                if lib().or_model_set_lass(self.h, i, r.lass_a, r.lass_b, r.lass_R) != 0:
+                    lib().or_model_free(self.h)
+                    self.h = None
+                    raise ValueError(f"oracle: bad LASS record {r.name}")
         self.n_cols = lib().or_num_cols(self.h)
         self.n_params = lib().or_num_params(self.h)
         res = np.zeros(self.n_cols, np.int32)

@@ -12,6 +12,7 @@
  *   - lineshape with barrier factors and running width                 Eq. 2, Eq. 3
  *   - K* helicity amplitude d^J_{l0}(theta_K*) e^{i l phi} d^1_{l xi}   Eq. 4
  *   - coherent sum, squared per muon helicity xi                      Eq. 5, Eq. 12
+ *   - LASS K pi S-wave: effective-range term + K0*(1430) Breit-Wigner   Eq. 7, Eq. 8, Eq. 9
  *   - Z -> J/psi pi amplitude with Z-frame angles and alignment alpha  Eq. 10
  *   - parity relation of the Z helicity couplings                      Eq. 11
  *   - unbinned -2 ln L with a numerical (MC) normalisation             Introduction,
@@ -35,6 +36,11 @@
  *     about z2 from the (z2, K) half-plane; alpha is the signed angle about mu+
  *     from the (mu+, z1) plane to the (mu+, z2) plane.
  *
+ *   - LASS (Eq. 7): the amplitude is the whole mass dependence of its J = 0
+ *     column (no barrier factors); the resonant term carries a factor R, 1 for
+ *     the elastic (unitary) form and 2 as printed; the running width is Eq. 3
+ *     at L = 0.
+ *
  * Parameters of a model: [Re c_k, Im c_k] per basis column k, then [M_R, G_R]
  * for every resonance flagged as floating, in resonance order.
  */
@@ -54,6 +60,7 @@ typedef double complex cplx;
 #define OR_BLOCK 2048 /* events per deterministic reduction block */
 
 enum { CH_KSTAR = 0, CH_Z = 1 };
+enum { SHAPE_BW = 0, SHAPE_LASS = 1 };
 
 typedef struct {
     double mB, mpsi, mK, mpi, m_lo, m_hi;
@@ -61,6 +68,8 @@ typedef struct {
     int chain[OR_MAXR], J[OR_MAXR], P[OR_MAXR], LB[OR_MAXR], LR[OR_MAXR], flt[OR_MAXR];
     int float_pos[OR_MAXR]; /* index among floated resonances, or -1 */
     double M[OR_MAXR], G0[OR_MAXR], r[OR_MAXR];
+    int shape[OR_MAXR];                                   /* SHAPE_BW or SHAPE_LASS */
+    double lass_a[OR_MAXR], lass_b[OR_MAXR], lass_R[OR_MAXR]; /* Eq. 7-8 constants */
     int col_res[OR_MAXC], col_lam[OR_MAXC];
     int has_z;
 } or_model;
@@ -182,8 +191,44 @@ static void chain_masses(const or_model *mo, int R, double *md1, double *md2, do
  * where p (q) is the resonance momentum in the B frame (the daughter momentum in
  * the resonance frame) at the running mass m, and p0, q0 the same at m = M.
  */
+/*
+ * LASS K pi S-wave of Eq. 7 with the effective-range phase of Eq. 8, as a dual
+ * number in the K0*(1430) pole parameters (M, G0):
+ *   A = (m/q) sin(thB) e^{i thB}
+ *       + R e^{2 i thB} (M^2 / q0) G0 / (M^2 - m^2 - i M Gamma(m)),
+ *   cot(thB) = 1 / (a q) + b q / 2,   Gamma(m) = G0 (q / q0) (M / m)  (Eq. 3, L = 0),
+ * q (q0) the K momentum in the K pi frame at m (at m = M).  At q = 0 the first
+ * term takes its limit m a (sin thB / q -> a) and e^{2 i thB} -> 1.
+ */
+static cdual lass_lineshape(const or_model *mo, int R, double mrun, dual M, dual G0)
+{
+    const double a = mo->lass_a[R], b = mo->lass_b[R];
+    const double q = breakup(dk(mrun), dk(mo->mK), dk(mo->mpi)).v;
+    cplx nonres, e2;
+    if (q > 0.0) {
+        const double cot_b = 1.0 / (a * q) + 0.5 * b * q;
+        const double th = atan2(1.0, cot_b); /* sin(thB) > 0: thB in (0, pi) */
+        nonres = (mrun / q) * sin(th) * cexp(I * th);
+        e2 = cexp(2.0 * I * th);
+    } else {
+        nonres = mrun * a;
+        e2 = 1.0;
+    }
+    dual q0 = breakup(M, dk(mo->mK), dk(mo->mpi));
+    dual width = dmul(dmul(G0, ddiv(dk(q), q0)), dscale(M, 1.0 / mrun));
+    dual num = dscale(ddiv(dmul(dmul(M, M), G0), q0), mo->lass_R[R]);
+    dual re = dsub(dmul(M, M), dk(mrun * mrun));
+    dual im = dscale(dmul(M, width), -1.0);
+    cdual n = {e2 * num.v, e2 * num.d};
+    cdual den = {re.v + I * im.v, re.d + I * im.d};
+    cdual res = cdiv(n, den);
+    res.v += nonres;
+    return res;
+}
+
 static cdual lineshape(const or_model *mo, int R, double mrun, dual M, dual G0)
 {
+    if (mo->shape[R] == SHAPE_LASS) return lass_lineshape(mo, R, mrun, M, G0);
     double md1, md2, mspec;
     chain_masses(mo, R, &md1, &md2, &mspec);
     const int LB = mo->LB[R], LR = mo->LR[R];
@@ -289,6 +334,18 @@ or_model *or_model_new(const double *masses4, double m_lo, double m_hi, int n_re
 }
 
 void or_model_free(or_model *mo) { free(mo); }
+
+/* Make K* resonance R (J = 0) the LASS S-wave of Eq. 7-8 with effective-range
+ * constants a, b (GeV^-1) and resonant-term factor Rfac.  Returns 0, or -1 if R
+ * is not a J = 0 K* or a constant is out of range. */
+int or_model_set_lass(or_model *mo, int R, double a, double b, double Rfac)
+{
+    if (R < 0 || R >= mo->n_res || mo->chain[R] != CH_KSTAR || mo->J[R] != 0) return -1;
+    if (!(a > 0.0) || !(b >= 0.0) || !(Rfac >= 0.0) || !isfinite(b) || !isfinite(Rfac)) return -1;
+    mo->shape[R] = SHAPE_LASS;
+    mo->lass_a[R] = a; mo->lass_b[R] = b; mo->lass_R[R] = Rfac;
+    return 0;
+}
 int or_num_cols(const or_model *mo) { return mo->n_col; }
 int or_num_params(const or_model *mo) { return 2 * mo->n_col + 2 * mo->n_float; }
 void or_columns(const or_model *mo, int *res, int *lam)

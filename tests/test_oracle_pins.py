@@ -159,6 +159,140 @@ def test_lineshape_derivatives_match_finite_differences():
         assert abs(dG - fdG) <= 1e-7 * max(abs(dG), 1e-12) + 1e-12
 
 
+# ---------------------------------------------------------------- LASS S-wave (Eq. 7, Eq. 8)
+def _lass_model(R=W.LASS_R, a=W.LASS_A, b=W.LASS_B):
+    import dataclasses
+    return O.Model([dataclasses.replace(W.LASS, lass_R=R, lass_a=a, lass_b=b)])
+
+
+_LASS_M = np.linspace(W.M_K + W.M_PI + 1e-4, 2.18, 61)
+
+
+def test_lass_background_is_the_effective_range_amplitude():
+    """Resonant term off (R = 0): the first term of Eq. 7 with the phase of Eq. 8
+    is m times the textbook effective-range partial wave
+    f = 1 / (q cot d - i q), q cot d = 1/a + r_e q^2 / 2, with r_e = b."""
+    for a, b in ((W.LASS_A, W.LASS_B), (3.1, 0.0), (0.7, 5.0)):
+        mo = _lass_model(R=0.0, a=a, b=b)
+        for m in _LASS_M:
+            q = O.breakup(m, W.M_K, W.M_PI)
+            ref = m / (1.0 / a + 0.5 * b * q * q - 1j * q)
+            A, dM, dG = mo.lineshape(0, m)
+            assert abs(A - ref) <= 1e-13 * abs(ref)
+            assert dM == 0 and dG == 0
+
+
+def test_lass_elastic_unitarity():
+    """With R = 1 and the running width of Eq. 3 at L = 0, T = A q / m is an
+    elastic partial wave: sin(d) e^{i d} with d = thB + dR, so T lies on the
+    unitarity circle |T - i/2| = 1/2, and its phase is the background phase of
+    Eq. 8 plus the Breit-Wigner phase cot dR = (M^2 - m^2) / (M Gamma(m)).  The
+    printed factor 2 (R = 2) leaves the circle away from the background."""
+    mo1, mo2 = _lass_model(R=1.0), _lass_model(R=2.0)
+    M, G0 = W.LASS.M, W.LASS.G0
+    q0 = O.breakup(M, W.M_K, W.M_PI)
+    off = 0
+    for m in _LASS_M:
+        q = O.breakup(m, W.M_K, W.M_PI)
+        T = mo1.lineshape(0, m)[0] * q / m
+        assert abs(abs(T - 0.5j) - 0.5) < 1e-13
+        thB = math.atan2(1.0, 1.0 / (W.LASS_A * q) + 0.5 * W.LASS_B * q)
+        dR = math.atan2(M * G0 * (q / q0) * (M / m), M * M - m * m)
+        d = thB + dR
+        assert abs(T - math.sin(d) * complex(math.cos(d), math.sin(d))) < 1e-13
+        T2 = mo2.lineshape(0, m)[0] * q / m
+        off += abs(abs(T2 - 0.5j) - 0.5) > 1e-3
+    assert off > len(_LASS_M) // 2
+
+
+def test_lass_at_the_pole():
+    """At m = M the resonant term of Eq. 7 is R e^{2i thB} i M / q0 (Gamma(M) = G0)."""
+    M = W.LASS.M
+    q0 = O.breakup(M, W.M_K, W.M_PI)
+    e2 = (1 / W.LASS_A + 0.5 * W.LASS_B * q0 ** 2 + 1j * q0) / \
+         (1 / W.LASS_A + 0.5 * W.LASS_B * q0 ** 2 - 1j * q0)
+    bg = _lass_model(R=0.0).lineshape(0, M)[0]
+    for R in (1.0, 2.0, 0.37):
+        A = _lass_model(R=R).lineshape(0, M)[0]
+        ref = R * e2 * 1j * M / q0
+        assert abs((A - bg) - ref) <= 1e-13 * abs(ref)
+
+
+def test_lass_threshold_limit():
+    """At q = 0 the background tends to m a (the scattering length) and
+    e^{2i thB} to 1: the amplitude is continuous at the K pi threshold."""
+    mo = _lass_model()
+    mth = W.M_K + W.M_PI
+    M, G0 = W.LASS.M, W.LASS.G0
+    q0 = O.breakup(M, W.M_K, W.M_PI)
+    a0 = mo.lineshape(0, mth)[0]
+    ref = mth * W.LASS_A + W.LASS_R * (M * M * G0 / q0) / (M * M - mth * mth)
+    assert abs(a0 - ref) <= 1e-13 * abs(ref)
+    # above threshold A - A(threshold) = O(q), q ~ sqrt(m - m_th)
+    for dm in (1e-8, 1e-10, 1e-12):
+        q = O.breakup(mth + dm, W.M_K, W.M_PI)
+        assert abs(mo.lineshape(0, mth + dm)[0] - a0) < 10.0 * q
+
+
+def test_lass_derivatives_match_finite_differences():
+    mo = _lass_model()
+    M, G0 = W.LASS.M, W.LASS.G0
+    for mrun in (0.7, 1.2, M + 0.1 * G0, 2.0):
+        _, dM, dG = mo.lineshape(0, mrun)
+        h = 1e-6
+        fdM = (mo.lineshape(0, mrun, M=M + h)[0] - mo.lineshape(0, mrun, M=M - h)[0]) / (2 * h)
+        fdG = (mo.lineshape(0, mrun, G0=G0 + h)[0] - mo.lineshape(0, mrun, G0=G0 - h)[0]) / (2 * h)
+        assert abs(dM - fdM) <= 1e-7 * abs(dM)
+        assert abs(dG - fdG) <= 1e-7 * abs(dG)
+
+
+def test_lass_density_is_the_scalar_wave():
+    """Eq. 9 with the LASS term alone: one J = 0 column, d^0_00 = 1 and
+    sum_xi |d^1_{0 xi}(theta_psi)|^2 = sin^2 theta_psi, so
+    S = |H|^2 |A_LASS(m)|^2 sin^2 theta_psi, flat in cos theta_K* and phi."""
+    mo = _lass_model()
+    assert mo.n_cols == 1
+    H = 0.6 - 0.3j
+    pts = W.uniform_points(500, 17)
+    S, _ = mo.density([H.real, H.imag], pts)
+    for i in range(0, 500, 7):
+        m, cpsi = float(pts[0][i]), float(pts[2][i])
+        A = mo.lineshape(0, m)[0]
+        ref = abs(H) ** 2 * abs(A) ** 2 * (1.0 - cpsi * cpsi)
+        assert S[i] == pytest.approx(ref, rel=1e-12, abs=1e-300)
+
+
+def test_lass_model_gradient_matches_central_differences():
+    """Eq. 9 model (LASS + the other K* states + Z(4430)) with every other mass
+    and width floating: the oracle's analytic NLL gradient against central
+    differences."""
+    cfg = W.CONFIGS["lass_z"]
+    res = cfg.resonances
+    mo = O.Model(res, float_names=cfg.float_mg)
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed),
+                              W.float_mg_values(res, cfg.float_mg))
+    ev = W.peaked_points(400, 3, res)
+    nm = W.uniform_points(800, 4)
+    _, g, _, rc = mo.nll(p, ev, nm, grad=True)
+    assert rc == 0
+    rng = np.random.default_rng(5)
+    for i in sorted(rng.choice(len(p), 12, replace=False)) + [0, 1, len(p) - 1]:
+        h = 1e-6 * max(1.0, abs(p[i]))
+        up, dn = p.copy(), p.copy()
+        up[i] += h
+        dn[i] -= h
+        fd = (mo.nll(up, ev, nm)[0] - mo.nll(dn, ev, nm)[0]) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-5 * max(1.0, abs(g[i]))
+
+
+def test_lass_rejected_where_it_does_not_apply():
+    import dataclasses
+    with pytest.raises(ValueError):
+        O.Model([dataclasses.replace(W.RESONANCES["K*(892)"], shape=W.SHAPE_LASS)])
+    with pytest.raises(ValueError):
+        _lass_model(a=0.0)
+
+
 # ---------------------------------------------------------------- kinematics
 def test_kstar_angles_round_trip():
     mo = _all_model()

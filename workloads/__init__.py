@@ -39,6 +39,15 @@ CHAIN_Z = 1
 # Blatt-Weisskopf radius (GeV^-1) used for both barrier factors.
 R_BW = 1.6
 
+# Lineshape kinds: the Breit-Wigner of Eq. 2-3, or the LASS K pi S-wave of Eq. 7-8.
+SHAPE_BW = 0
+SHAPE_LASS = 1
+# Effective-range constants of Eq. 8 (GeV^-1), and the factor on the resonant
+# term of Eq. 7: 1 for the elastic (unitary) form; the paper prints 2.
+LASS_A = 1.95
+LASS_B = 1.76
+LASS_R = 1.0
+
 
 @dataclass(frozen=True)
 class Resonance:
@@ -49,6 +58,10 @@ class Resonance:
     M: float        # pole mass, GeV
     G0: float       # nominal width, GeV
     r: float = R_BW
+    shape: int = SHAPE_BW   # SHAPE_LASS: the K0*(1430) pole inside the LASS S-wave
+    lass_a: float = LASS_A
+    lass_b: float = LASS_B
+    lass_R: float = LASS_R
 
     @property
     def LB(self) -> int:
@@ -93,7 +106,12 @@ KSTAR_TABLE = [
 ]
 Z4430 = Resonance("Z(4430)", CHAIN_Z, 1, +1, 4.43, 0.18)
 Z4200 = Resonance("Z(4200)", CHAIN_Z, 1, +1, 4.196, 0.37)
-RESONANCES = {r.name: r for r in KSTAR_TABLE + [Z4430, Z4200]}
+# LASS K pi S-wave (Eq. 7-9): the effective-range amplitude with the K0*(1430)
+# pole inside it.  In Eq. 9 it replaces the two scalar Breit-Wigners K0*(800)
+# and K0*(1430); the other K* states keep theirs.
+LASS = Resonance("LASS", CHAIN_KSTAR, 0, +1, 1.425, 0.270, shape=SHAPE_LASS)
+RESONANCES = {r.name: r for r in KSTAR_TABLE + [Z4430, Z4200, LASS]}
+KSTAR_PRIME = [r.name for r in KSTAR_TABLE if r.name not in ("K0*(800)", "K0*(1430)")]
 
 # Z helicity couplings are drawn like the K* ones, then scaled by this factor
 # so that the Z fit fraction is a few percent.
@@ -159,6 +177,11 @@ CONFIGS = {
     # Z-sensitivity model: both Z states, their masses and widths floating.
     "kstar10_2z": Config("kstar10_2z", 6, ALL_KSTAR + ["Z(4200)", "Z(4430)"], 200_000, 2_000_000,
                          float_mg=["Z(4200)", "Z(4430)"]),
+    # Eq. 9: the LASS S-wave and the eight other K* states.
+    "lass": Config("lass", 7, ["LASS"] + KSTAR_PRIME, 200_000, 2_000_000),
+    # Eq. 9 with Z(4430); every mass and width but the LASS pole's floating.
+    "lass_z": Config("lass_z", 8, ["LASS"] + KSTAR_PRIME + ["Z(4430)"], 200_000, 2_000_000,
+                     float_mg=KSTAR_PRIME + ["Z(4430)"]),
 }
 
 
