@@ -9,12 +9,12 @@
  *
  * What is computed (Methodology section):
  *   A^R(m)      lineshape, Eq. 2 with the running width of Eq. 3 and ratio-form
- *               Blatt-Weisskopf barrier factors;
+ *               Blatt-Weisskopf barrier factors, or the LASS S-wave of Eq. 7-8;
  *   B_k,xi(e)   basis column k = (resonance R, helicity l) for muon helicity xi:
  *               K*  A^R(m_Kpi) d^J_{l0}(theta_K*) e^{i l phi} d^1_{l xi}(theta_psi)   (Eq. 4)
  *               Z   A^Z(m_psipi) d^J_{0l'}(theta_Z) e^{i l' phi~} d^1_{l' xi}(theta~_psi)
  *                   e^{i xi alpha}, with l' = +-1 tied by H_{-l'} = eta H_{l'}     (Eq. 10, 11)
- *   S(e)        sum_xi |sum_k c_k B_k,xi(e)|^2                                (Eq. 5, Eq. 12)
+ *   S(e)        sum_xi |sum_k c_k B_k,xi(e)|^2                         (Eq. 5, Eq. 9, Eq. 12)
  *   I           (V / N_mc) sum_n w_n S(x_n), the numerical normalisation over MC
  *               phase-space points (State-of-the-art section), w = p q for uniform points
  *   NLL         -2 sum_e [ ln S(e) + ln(p_e q_e) - ln I ]   (unbinned ML, Introduction)
@@ -73,6 +73,22 @@ typedef struct {
     double mB, mpsi, mK, mpi; /* B0, J/psi, K+, pi- masses (GeV) */
 } amp4d_particle_masses;
 
+#define AMP4D_SHAPE_BW 0   /* Breit-Wigner with barrier factors, Eq. 2-3            */
+#define AMP4D_SHAPE_LASS 1 /* LASS K pi S-wave, Eq. 7-8 (a J = 0 K* only)           */
+
+/*
+ * One resonance.  Zero-initialise the record: shape 0 is the Breit-Wigner.
+ *
+ * shape = AMP4D_SHAPE_LASS makes a J = 0 K* the LASS S-wave of Eq. 7-9, with
+ * (M, G0) the K0*(1430) pole inside it:
+ *   A(m) = m / (1/a + (b/2) q^2 - i q)                   [= (m/q) sin(thB) e^{i thB}]
+ *        + R e^{2 i thB} (M^2 / q0) G0 / (M^2 - m^2 - i M Gamma(m)),
+ *   cot(thB) = 1/(a q) + b q / 2,  Gamma(m) = G0 (q/q0) (M/m)  (Eq. 3 at L = 0),
+ * q (q0) the K momentum in the K pi frame at m (at m = M).  A is the whole mass
+ * dependence of the column: LB, LR and r are not used.  lass_a > 0, lass_b >= 0
+ * (GeV^-1; Eq. 8 gives 1.95 and 1.76), lass_R >= 0 (1: the elastic form; Eq. 7
+ * prints 2).  Its M and G0 cannot float (float_mg must be 0).
+ */
 typedef struct {
     int chain;    /* AMP4D_CHAIN_KSTAR or AMP4D_CHAIN_Z                          */
     int J, P;     /* spin and intrinsic parity (+1 / -1) of the resonance        */
@@ -80,6 +96,8 @@ typedef struct {
     double M, G0; /* pole mass and nominal width (GeV)                           */
     double r;     /* Blatt-Weisskopf radius (GeV^-1)                             */
     int float_mg; /* 1: M and G0 are fit parameters (appended to the vector)     */
+    int shape;    /* AMP4D_SHAPE_BW or AMP4D_SHAPE_LASS                          */
+    double lass_a, lass_b, lass_R; /* AMP4D_SHAPE_LASS constants (see above)     */
 } amp4d_resonance;
 
 typedef struct amp4d_model amp4d_model;

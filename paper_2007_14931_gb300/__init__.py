@@ -34,6 +34,8 @@ AMP4D_ERR_TIMEOUT = -6
 AMP4D_ERR_STATE = -7
 AMP4D_CHAIN_KSTAR = 0
 AMP4D_CHAIN_Z = 1
+AMP4D_SHAPE_BW = 0
+AMP4D_SHAPE_LASS = 1
 AMP4D_PATH_PLAIN = 0
 AMP4D_PATH_CACHED = 1
 AMP4D_MAX_RES = 16
@@ -134,7 +136,8 @@ class amp4d_particle_masses(C.Structure):
 class amp4d_resonance(C.Structure):
     _fields_ = [("chain", C.c_int), ("J", C.c_int), ("P", C.c_int), ("LB", C.c_int),
                 ("LR", C.c_int), ("M", C.c_double), ("G0", C.c_double), ("r", C.c_double),
-                ("float_mg", C.c_int)]
+                ("float_mg", C.c_int), ("shape", C.c_int), ("lass_a", C.c_double),
+                ("lass_b", C.c_double), ("lass_R", C.c_double)]
 
 
 class amp4d_mlp_cfg(C.Structure):
@@ -251,7 +254,10 @@ class Model:
         arr = (amp4d_resonance * len(res_list))()
         for i, r in enumerate(res_list):
             arr[i] = amp4d_resonance(r.chain, r.J, r.P, r.LB, r.LR, r.M, r.G0, r.r,
-                                     1 if r.name in float_names else 0)
+                                     1 if r.name in float_names else 0,
+                                     getattr(r, "shape", AMP4D_SHAPE_BW),
+                                     getattr(r, "lass_a", 0.0), getattr(r, "lass_b", 0.0),
+                                     getattr(r, "lass_R", 0.0))
         pm = amp4d_particle_masses(*masses)
         h = _vp()
         rc = amp4d_model_create(C.byref(pm), arr, len(res_list), box[0], box[1], path, C.byref(h))

@@ -469,6 +469,12 @@ ModelStatic make_static(const amp4d_model *mo)
         ResStatic &d = s.res[i];
         d.M = r.M; d.G0 = r.G0; d.r = r.r;
         d.chain = r.chain; d.J = r.J; d.LB = r.LB; d.LR = r.LR;
+        d.shape = r.shape;
+        if (r.shape == AMP4D_SHAPE_LASS) {
+            // Eq. 7 is the whole mass dependence: no barrier factors.
+            d.LB = d.LR = 0;
+            d.lass_a = r.lass_a; d.lass_b = r.lass_b; d.lass_R = r.lass_R;
+        }
         d.col = mo->res_col[u];
         d.fpos = mo->res_fpos[u];
         d.eta = -r.P * ((r.J % 2) ? -1 : 1);
@@ -505,6 +511,14 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
         if (r.J < 0 || r.J > 4 || r.LB < 0 || r.LB > 4 || r.LR < 0 || r.LR > 4 ||
             (r.P != 1 && r.P != -1) || !(r.M > 0) || !(r.G0 > 0) || !(r.r >= 0))
             return fail(nullptr, AMP4D_ERR_ARG, "bad resonance record");
+        if (r.shape != AMP4D_SHAPE_BW && r.shape != AMP4D_SHAPE_LASS)
+            return fail(nullptr, AMP4D_ERR_ARG, "bad lineshape kind");
+        if (r.shape == AMP4D_SHAPE_LASS &&
+            (r.chain != AMP4D_CHAIN_KSTAR || r.J != 0 || r.float_mg || !(r.lass_a > 0) ||
+             !(r.lass_b >= 0) || !(r.lass_R >= 0) || !std::isfinite(r.lass_a) ||
+             !std::isfinite(r.lass_b) || !std::isfinite(r.lass_R)))
+            return fail(nullptr, AMP4D_ERR_ARG,
+                        "LASS: a fixed J = 0 K* with a > 0, b >= 0, R >= 0 (finite)");
         if (r.chain == AMP4D_CHAIN_Z) {
             ++nz;
             const int eta = -r.P * ((r.J % 2) ? -1 : 1);

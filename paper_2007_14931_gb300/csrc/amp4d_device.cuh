@@ -45,6 +45,7 @@ enum : int {
 // constant carries a systematic FP32 rounding into S.
 struct ResDev {
     float Mhi, Mlo;   // pole mass M
+    float M2lo;       // M^2 - Mhi^2 = Mlo (2 Mhi + Mlo)
     float r2hi, r2lo; // Blatt-Weisskopf radius squared
     float Ghi, Glo;   // G0 M^2 KR / q0^(2 LR + 1): M Gamma(m) = G q^(2LR+1) / (P_LR(r^2 q^2) m)
     float dNhi, dNlo; // d ln(sqrt(KB KR))/dM, KB = P_LB(r^2 p0^2), KR = P_LR(r^2 q0^2)
@@ -53,6 +54,10 @@ struct ResDev {
     // Horner pairs for P_J(c) = sum_i a_i c^i (d^J_00) and P_J'(c) = sum_i b_i c^i
     // (d1 = -sin P_J'): hp[0] = (a_4, 0), hp[j] = (a_{4-j}, b_{4-j}) for j = 1..4.
     float2 hp[5];
+    // LASS S-wave (Eq. 7-8; shape == AMP4D_SHAPE_LASS): a, a b / 2 and the
+    // resonant-term constant R M^2 G0 / q0, each as hi + lo.
+    float ahi, alo, chi, clo, RKhi, RKlo;
+    int shape;
     int chain, J, LB, LR;
     int col;          // first basis column
     int fpos;         // index among floated resonances, -1 if fixed
@@ -64,8 +69,9 @@ struct ResDev {
 // Static description of a resonance (internal order: K* first, then Z).
 struct ResStatic {
     double M, G0, r;          // model values (replaced by floated parameters)
-    int chain, J, LB, LR;
-    int col, fpos, eta, zcol0, zcol1, pad_;
+    double lass_a, lass_b, lass_R;  // AMP4D_SHAPE_LASS constants (Eq. 7-8)
+    int chain, J, LB, LR;     // LB = LR = 0 for the LASS S-wave
+    int col, fpos, eta, zcol0, zcol1, shape;
 };
 
 struct ModelStatic {
@@ -241,16 +247,50 @@ __device__ __forceinline__ LineOut lineshape(const ResDev &r, float mrun, float 
     const float num = rs * ipow(p, r.LB) * ipow(q * invm, r.LR);
     const float X = ipow(q, 2 * r.LR + 1) * invm * __frcp_rn(PR);
     const float MG = fmaf(r.Ghi, X, r.Glo * X);
-    // M^2 - m^2 = (M - m)(M + m) with M = hi + lo: (hi - m) is exact near the pole,
-    // and lo enters (M + m) inside the final FMA.
-    const float dm = (r.Mhi - mrun) + r.Mlo;
-    const float Dr = fmaf(dm, r.Mhi + mrun, dm * r.Mlo);
+    // M^2 - m^2 = (hi - m)(hi + m) + lo (2 hi + lo) for M = hi + lo: (hi - m) is
+    // exact near the pole, and the constant lo (2 hi + lo) enters the FMA before
+    // its one rounding.  (Adding lo to hi - m first would round at the same
+    // offset from the FP32 grid that m and hi share for every event: a
+    // systematic error in every lineshape.)
+    const float Dr = fmaf(r.Mhi - mrun, r.Mhi + mrun, r.M2lo);
     const float den = __frcp_rn(fmaf(Dr, Dr, MG * MG));
     LineOut o;
     o.invD = make_float2(Dr * den, MG * den);          // 1/(Dr - i MG) = (Dr + i MG)/|D|^2
     o.A = make_float2(num * o.invD.x, num * o.invD.y);
     o.MG = MG;
     return o;
+}
+
+// LASS S-wave of Eq. 7-8 from the K0*(1430) Breit-Wigner denominator 1/D of
+// lineshape() (built with LB = LR = 0, so M Gamma(m) = (M^2 G0/q0) q/m, Eq. 3 at
+// L = 0).  Eq. 8 is taken as a q cot(thB) = v = 1 + (a b/2) q^2 with s = a q:
+//   (m/q) sin(thB) e^{i thB} = m a / (v - i s) = (m a)(v + i s) / (v^2 + s^2),
+//   e^{2 i thB} = (v + i s) / (v - i s) = ((v^2 - s^2) + 2 i v s) / (v^2 + s^2),
+//   A = (m a) w + R (M^2 G0 / q0) e^{2 i thB} / D,   w = 1 / (v - i s).
+// Every constant (a, a b/2, R M^2 G0/q0) multiplies inside an FMA with its low
+// part as the addend, and the one added constant (1) is exact, so no constant
+// leaves a systematic FP32 rounding in A.  Finite at q = 0 (A = m a + R K/D).
+__device__ __forceinline__ float2 lass_shape(const ResDev &r, float m, float q, float2 invD)
+{
+    const float q2 = q * q;
+    const float sq = fmaf(r.ahi, q, r.alo * q);
+    const float v = 1.0f + fmaf(r.chi, q2, r.clo * q2);
+    const float n = __frcp_rn(fmaf(v, v, sq * sq));
+    const float ma = fmaf(r.ahi, m, r.alo * m);
+    const float2 w = make_float2(v * n, sq * n);
+    const float2 e2 = make_float2((v - sq) * (v + sq) * n, 2.0f * v * sq * n);
+    const float2 t = make_float2(e2.x * invD.x - e2.y * invD.y, e2.x * invD.y + e2.y * invD.x);
+    return make_float2(fmaf(ma, w.x, fmaf(r.RKhi, t.x, r.RKlo * t.x)),
+                       fmaf(ma, w.y, fmaf(r.RKhi, t.y, r.RKlo * t.y)));
+}
+
+// Lineshape of a K* chain resonance: Eq. 2-3, or the LASS S-wave of Eq. 7-8.
+__device__ __forceinline__ float2 kstar_lineshape(const ResDev &r, float mrun, float invm, float p,
+                                                  float q)
+{
+    const LineOut L = lineshape(r, mrun, invm, p, q);
+    if (r.shape != AMP4D_SHAPE_LASS) return L.A;
+    return lass_shape(r, mrun, q, L.invD);
 }
 
 }  // namespace amp4d

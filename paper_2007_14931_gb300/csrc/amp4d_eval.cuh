@@ -78,10 +78,12 @@ struct EvState {
 // Lineshape of a resonance for this event: the basis-cache value (loaded up
 // front) when a cache is given and the resonance's mass and width are fixed,
 // else computed.
+template <bool KSTAR>
 __device__ __forceinline__ float2 cached_or_computed(const ResDev &rs, bool have_lc, float2 cached,
                                                      float m, float invm, float p, float q)
 {
     if (have_lc && rs.fpos < 0) return cached;
+    if constexpr (KSTAR) return kstar_lineshape(rs, m, invm, p, q);
     return lineshape(rs, m, invm, p, q).A;
 }
 
@@ -132,7 +134,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
     for (int k = 0; k < NK; ++k) {
         if (k < nK) {
             const ResDev &rs = md.res[k];
-            const float2 LA = FX ? LK[k] : cached_or_computed(rs, have_lc, LK[k], m, invm, p, q);
+            const float2 LA = FX ? LK[k] : cached_or_computed<true>(rs, have_lc, LK[k], m, invm, p, q);
             float d0, d1;
             wigner_l0(rs, cc, sK, d0, d1);
             const float2 b0 = cscale(LA, d0), b1 = cscale(LA, d1);
@@ -173,7 +175,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
             const ResDev &rs = md.zr[z];
-            const float2 LA = FX ? LZ[z] : cached_or_computed(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
+            const float2 LA = FX ? LZ[z] : cached_or_computed<false>(rs, have_lc, LZ[z], mZ, invmZ, pZ, qZ);
             float dz0, dz1;
             wigner_l0(rs, make_float2(cZ, cZ), sZ, dz0, dz1);  // d^J_{00}, d^J_{0,+-1} ~ -+ dz1
             ev.AZ[z] = LA;
@@ -848,7 +850,7 @@ __global__ void __launch_bounds__(256) k_build_lcache(const float *__restrict__ 
         const float invm = __frcp_rn(m);
 #pragma unroll
         for (int k = 0; k < NK; ++k)
-            if (k < nK) lc[k * npad + e] = lineshape(md.res[k], m, invm, p, q).A;
+            if (k < nK) lc[k * npad + e] = kstar_lineshape(md.res[k], m, invm, p, q);
         if constexpr (NZ > 0) {
             const float mZ = rec[REC_MZ * npad + e], pZ = rec[REC_PZ * npad + e];
             const float qZ = rec[REC_QZ * npad + e], invmZ = __frcp_rn(mZ);

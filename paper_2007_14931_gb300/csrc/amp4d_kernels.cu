@@ -333,6 +333,7 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         ResDev d;
         d.Mhi = (float)M;
         d.Mlo = (float)(M - (double)d.Mhi);
+        d.M2lo = (float)((M - (double)d.Mhi) * ((double)d.Mhi + M));
         d.r2hi = (float)r2;
         d.r2lo = (float)(r2 - (double)d.r2hi);
         d.Ghi = (float)G;
@@ -343,6 +344,15 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         d.dNhi = (float)dN; d.dNlo = (float)(dN - (double)d.dNhi);
         d.dGhi = (float)dG; d.dGlo = (float)(dG - (double)d.dGhi);
         d.iGhi = (float)iG; d.iGlo = (float)(iG - (double)d.iGhi);
+        // LASS S-wave (Eq. 7-8): built with LB = LR = 0, so G = M^2 G0 / q0.
+        d.shape = r.shape;
+        d.ahi = d.alo = d.chi = d.clo = d.RKhi = d.RKlo = 0.f;
+        if (r.shape == AMP4D_SHAPE_LASS) {
+            const double a = r.lass_a, c = 0.5 * r.lass_a * r.lass_b, RK = r.lass_R * G;
+            d.ahi = (float)a; d.alo = (float)(a - (double)d.ahi);
+            d.chi = (float)c; d.clo = (float)(c - (double)d.chi);
+            d.RKhi = (float)RK; d.RKlo = (float)(RK - (double)d.RKhi);
+        }
         // Legendre coefficients of P_J and P_J' (exact in FP32), lowest power first.
         {
             const float P[5][5] = {{1.f, 0.f, 0.f, 0.f, 0.f},

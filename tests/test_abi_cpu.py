@@ -51,3 +51,50 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     rc = A.amp4d_model_create(None, None, 0, 0.6, 2.1, 0, ctypes.byref(h))
     assert rc == A.AMP4D_ERR_ARG
     assert b"null" in A.amp4d_last_error(None)
+
+
+def test_binding_records_match_header_layout(tmp_path):
+    """The ctypes records of the binding have the C layout of include/amp4d.h
+    (sizes and field offsets, as gcc lays the header's structs out)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    import paper_2007_14931_gb300 as A
+    recs = {"amp4d_resonance": A.amp4d_resonance, "amp4d_particle_masses": A.amp4d_particle_masses,
+            "amp4d_mlp_cfg": A.amp4d_mlp_cfg}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "amp4d.h"', "int main(void) {"]
+    for name, cls in recs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for name, cls in recs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(got["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_create_rejects_bad_lass_records_without_gpu(lib):
+    """The LASS S-wave (Eq. 7-8) applies to a fixed J = 0 K* with a > 0, b >= 0, R >= 0."""
+    import dataclasses
+    import paper_2007_14931_gb300 as A
+    import workloads as W
+    bad = [dataclasses.replace(W.LASS, J=1), dataclasses.replace(W.LASS, chain=W.CHAIN_Z, J=1),
+           dataclasses.replace(W.LASS, lass_a=0.0), dataclasses.replace(W.LASS, lass_b=-1.0),
+           dataclasses.replace(W.LASS, lass_R=float("nan")), dataclasses.replace(W.LASS, shape=7)]
+    for r in bad:
+        with pytest.raises(A.Amp4dError) as e:
+            A.Model([r, W.RESONANCES["K*(892)"]])
+        assert e.value.code == A.AMP4D_ERR_ARG
+    with pytest.raises(A.Amp4dError) as e:
+        A.Model([W.LASS], float_names=["LASS"])
+    assert e.value.code == A.AMP4D_ERR_ARG
+    assert b"LASS" in A.amp4d_last_error(None)

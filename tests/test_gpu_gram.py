@@ -89,7 +89,7 @@ def _uv(c):
 
 
 @pytest.mark.parametrize("name,n_mc", [("tiny", 100_003), ("kstar10", 65_536), ("kstar10_z", 123_457),
-                                       ("kstar10_z", 7), ("tiny", 1)])
+                                       ("kstar10_z", 7), ("tiny", 1), ("lass", 65_536)])
 def test_gram_matches_oracle(A, name, n_mc):
     cfg = W.CONFIGS[name]
     res = cfg.resonances
@@ -123,7 +123,7 @@ def test_gram_matches_oracle(A, name, n_mc):
     assert np.array_equal(gm.get_gram(), G)  # deterministic
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z", "lass", "lass_z"])
 def test_cached_path_nll_grad(A, name):
     cfg = W.CONFIGS[name]
     res = cfg.resonances
@@ -208,7 +208,7 @@ def test_basis_cache_reproduces_recompute_bit_for_bit(A):
     assert np.array_equal(S0, S1)
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z", "lass"])
 def test_fit_fractions_match_oracle(A, name):
     """Eq. 13 from the tensor-core Gram matrix against the oracle's definition
     (normalisation integrals with the other couplings zeroed) on the same points;

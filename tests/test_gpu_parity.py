@@ -67,7 +67,7 @@ def _check_density(om, p, c, pts, S_gpu):
     return good.mean(), np.max(err[good] / S_o[good])
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z", "lass", "lass_z"])
 @pytest.mark.parametrize("data", ["peaked", "uniform"])
 def test_density_parity(A, name, data):
     n = 20_003  # several tiles and a ragged tail (n % 4 = 3)
@@ -79,7 +79,7 @@ def test_density_parity(A, name, data):
     _check_density(om, p, c, nm, Sn)
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10", "kstar10_z", "kstar10_2z", "lass", "lass_z"])
 def test_nll_terms_parity(A, name):
     cfg, res, c, p, om, gm, ev, nm = _setup(A, name, 50_001, 200_003)
     nll_o, _, aux, rc = om.nll(p, ev, nm)
@@ -88,13 +88,22 @@ def test_nll_terms_parity(A, name):
     assert t[3] == len(ev[0])
     assert t[1] == pytest.approx(aux[1], abs=1e-9 * abs(aux[1]) + 1e-9)   # sum ln(p q), FP64 once
     assert t[2] == pytest.approx(aux[2], rel=1e-8)                         # I
-    assert abs(t[0] - aux[0]) < 5e-4                                       # sum ln S
-    print("%s: dI/I %.3e  d(sum ln S) %.3e" % (name, t[2] / aux[2] - 1, t[0] - aux[0]))
+    # sum ln S: 5e-4, widened by three standard deviations of the sum of the
+    # per-event errors of ln S if they were independent and unbiased.  A model
+    # whose amplitude has a zero (the LASS S-wave, Eq. 7, where thB + dR = pi)
+    # has events whose S is ill-conditioned in the FP32 inputs; a bias would
+    # still show as |sum d| >> sqrt(sum d^2).
+    S_o, _ = om.density(p, ev)
+    d = np.log(gm.eval_density(p, 0).cpu().numpy().astype(np.float64) / S_o)
+    spread = 3.0 * math.sqrt(np.sum(d * d))
+    print("%s: dI/I %.3e  d(sum ln S) %.3e  per-event sum %.3e  3 sigma %.3e" % (
+        name, t[2] / aux[2] - 1, t[0] - aux[0], np.sum(d), spread))
+    assert abs(t[0] - aux[0]) < 5e-4 + spread                              # sum ln S
     nll = gm.eval_nll(p)
-    assert abs(nll - nll_o) < 1e-3
+    assert abs(nll - nll_o) < 1e-3 + 2.0 * spread
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z", "lass_z"])
 def test_nll_grad_parity_model_data(A, name):
     n = 20_000 if name == "tiny" else 8_000
     cfg, res, c, p, om, gm, ev, nm = _setup(A, name, n, 40_000, data="model")
@@ -249,7 +258,7 @@ def test_density_bias(A):
     assert abs(bias) < 5e-9 + 4 * sem
 
 
-@pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z", "lass"])
 def test_pdf_parity(A, name):
     """P(e) = S p q / I per data event (Eq. 5 with the phase-space density): the
     oracle's S and p q over its own I, per event, with the per-event density
@@ -296,3 +305,38 @@ def test_cached_all_fixed_ragged_sizes(A, n):
     assert abs(nll_c - nll_o) < tol_nll and abs(nll_p - nll_o) < tol_nll
     assert np.max(np.abs(g_c - g_o)) <= 1e-5 * np.max(np.abs(g_o))
     assert np.max(np.abs(g_c - g_p)) <= 1e-5 * np.max(np.abs(g_o))
+
+
+@pytest.mark.parametrize("R", [1.0, 2.0, 0.0])
+def test_lass_density_near_threshold_and_pole(A, R):
+    """LASS S-wave (Eq. 7-9) with K*(892): events packed near the K pi threshold
+    (q -> 0, where the background term tends to m a), at the K0*(1430) pole and
+    across the box, for the elastic factor R = 1, the printed R = 2 and the
+    background alone (R = 0)."""
+    import dataclasses
+    res = [dataclasses.replace(W.LASS, lass_R=R), W.RESONANCES["K*(892)"]]
+    c = W.draw_couplings(res, 77)
+    p = W.couplings_to_params(c)
+    rng = np.random.default_rng(78)
+    n = 12_007
+    m = np.concatenate([W.M_LO + rng.uniform(0, 1e-3, 4000),
+                        W.LASS.M + rng.normal(0, 0.02, 4000),
+                        rng.uniform(W.M_LO, W.M_END - 1e-6, n - 8000)])
+    m = np.clip(m, W.M_LO, W.M_END - 1e-6).astype(np.float32)
+    pts = (m, rng.uniform(-1, 1, n).astype(np.float32), rng.uniform(-1, 1, n).astype(np.float32),
+           rng.uniform(-math.pi, math.pi, n).astype(np.float32))
+    om = O.Model(res)
+    gm = A.Model(res)
+    gm.set_events(*_dev(pts))
+    gm.set_norm_points(*_dev(W.uniform_points(4097, 79)))
+    S = gm.eval_density(p, 0).cpu().numpy()
+    _check_density(om, p, c, pts, S)
+    for path in (A.AMP4D_PATH_PLAIN, A.AMP4D_PATH_CACHED):
+        g2 = A.Model(res, path=path)
+        g2.set_events(*_dev(pts))
+        g2.set_norm_points(*_dev(W.uniform_points(70_001, 80)))
+        nll_o, g_o, _, rc = om.nll(p, pts, W.uniform_points(70_001, 80), grad=True)
+        assert rc == 0
+        nll, g = g2.eval_nll_grad(p)
+        assert abs(nll - nll_o) < 1e-4 + 1e-9 * abs(nll_o)
+        assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
