@@ -66,6 +66,13 @@ def lib():
             L.or_nll.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d, _d,
                                  C.c_int64, C.c_double, _d, _d, _d]
             L.or_gram.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, _d, C.c_int64, _d]
+            L.or_nll_eq14.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d,
+                                      _d, C.c_int64, C.c_double, _d, _d, _d]
+            L.or_model_set_template.argtypes = [C.c_void_p, C.c_int, _d, C.c_int, C.c_int, _d,
+                                                _d, C.c_int, C.c_int, _d, C.c_double]
+            L.or_tpl_value.restype = C.c_double
+            L.or_tpl_value.argtypes = [_d, C.c_int, C.c_int, _d, C.c_double, C.c_double]
+            L.or_templates.argtypes = [C.c_void_p, _d, _d, _d, _d, C.c_int64, _d]
             L.or_partials.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d,
                                       _d, C.c_int64, C.c_double, C.c_int, _d]
             L.or_generate.restype = C.c_int64
@@ -273,6 +280,42 @@ class Model:
             out[R] = self.norm(pj, pts, w=w, volume=volume) / I
         return out
 
+    def set_template(self, which, mass, angle, purity=1.0):
+        """Eq. 14 templates: which 0 = efficiency, 1 = background (with purity).
+        mass, angle: workloads.Hist2D (contents [ny, nx], x and y ranges)."""
+        hm, ha = _f64(np.ravel(mass.h)), _f64(np.ravel(angle.h))
+        rm, ra = _f64(mass.range), _f64(angle.range)
+        self._keep_tpl = getattr(self, "_keep_tpl", []) + [hm, ha, rm, ra]
+        rc = lib().or_model_set_template(self.h, int(which), _pd(hm), mass.nx, mass.ny, _pd(rm),
+                                         _pd(ha), angle.nx, angle.ny, _pd(ra), float(purity))
+        if rc != 0:
+            raise ValueError("oracle: bad template")
+
+    def templates(self, pts):
+        """(eps, hb, m^2_psipi) per point."""
+        m, cK, cpsi, phi = (_f64(a) for a in pts)
+        out = np.zeros((len(m), 3))
+        lib().or_templates(self.h, _pd(m), _pd(cK), _pd(cpsi), _pd(phi), len(m), _pd(out))
+        return out[:, 0], out[:, 1], out[:, 2]
+
+    def nll_eq14(self, params, events, norm_pts, w=None, volume=None, grad=False):
+        """Eq. 14: (-2 ln L, gradient or None, aux, status); aux = [sum ln(f/pq),
+        sum ln pq, I_eps, B, sum of signal probabilities]."""
+        import workloads as W
+        volume = W.BOX_VOLUME if volume is None else volume
+        ev = [_f64(a) for a in events]
+        nm = [_f64(a) for a in norm_pts]
+        wf = _f64(w) if w is not None else None
+        out = C.c_double()
+        g = np.zeros(self.n_params) if grad else None
+        aux = np.zeros(5)
+        pr = _f64(params)
+        rc = lib().or_nll_eq14(self.h, _pd(pr), *(_pd(a) for a in ev), len(ev[0]),
+                               *(_pd(a) for a in nm), _pd(wf) if wf is not None else None,
+                               len(nm[0]), float(volume), C.byref(out), _pd(g) if grad else None,
+                               _pd(aux))
+        return out.value, g, aux, rc
+
     def gram(self, params, pts, w=None):
         m, cK, cpsi, phi = (_f64(a) for a in pts)
         D = 2 * self.n_cols
@@ -325,6 +368,13 @@ def adam_step(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """In-place Adam update of theta, m, v (float64 arrays)."""
     lib().or_adam_step(_pd(theta), _pd(m), _pd(v), _pd(_f64(grad)), len(theta), lr, beta1, beta2,
                        eps, int(t))
+
+
+def tpl_value(hist, x, y):
+    """Content of a workloads.Hist2D template at (x, y) by the oracle's bin rule."""
+    h = _f64(np.ravel(hist.h))
+    r = _f64(hist.range)
+    return lib().or_tpl_value(_pd(h), hist.nx, hist.ny, _pd(r), float(x), float(y))
 
 
 def grid_sample(gc, nb, alpha, seed, n, masses=None, box=None):

@@ -14,6 +14,7 @@
  *   - coherent sum, squared per muon helicity xi                      Eq. 5, Eq. 12
  *   - LASS K pi S-wave: effective-range term + K0*(1430) Breit-Wigner   Eq. 7, Eq. 8, Eq. 9
  *   - Z -> J/psi pi amplitude with Z-frame angles and alignment alpha  Eq. 10
+ *   - efficiency x signal + background with a fixed purity             Eq. 14
  *   - parity relation of the Z helicity couplings                      Eq. 11
  *   - unbinned -2 ln L with a numerical (MC) normalisation             Introduction,
  *                                                                     State of the art
@@ -40,6 +41,16 @@
  *     column (no barrier factors); the resonant term carries a factor R, 1 for
  *     the elastic (unitary) form and 2 as printed; the running width is Eq. 3
  *     at L = 0.
+ *
+ *   - Eq. 14 templates: the efficiency and the background are each a product
+ *     of a binned template in the two mass variables (m^2_Kpi, m^2_psipi) and
+ *     one in the two angles (cos theta_psi, phi), read at the bin holding the
+ *     point (bin i covers [lo + i d, lo + (i+1) d), the upper edge in the last
+ *     bin, 0 outside the range).  The background template is a density in the
+ *     Dalitz variables and the angles, so its density in (m, cK, cpsi, phi)
+ *     carries the Jacobian p q like the signal's; it is normalised over the
+ *     normalisation points with their weights.  S is normalised with the
+ *     efficiency-weighted points.  The purity P is fixed.
  *
  * Parameters of a model: [Re c_k, Im c_k] per basis column k, then [M_R, G_R]
  * for every resonance flagged as floating, in resonance order.
@@ -69,6 +80,11 @@ typedef struct {
     int float_pos[OR_MAXR]; /* index among floated resonances, or -1 */
     double M[OR_MAXR], G0[OR_MAXR], r[OR_MAXR];
     int shape[OR_MAXR];                                   /* SHAPE_BW or SHAPE_LASS */
+    /* Eq. 14 templates: [0] efficiency x (m^2_Kpi, m^2_psipi), [1] efficiency x
+     * (cos theta_psi, phi), [2] background x masses, [3] background x angles. */
+    struct { double *h; int nx, ny; double xlo, xhi, ylo, yhi; } tpl[4];
+    int has_eff, has_bkg;
+    double purity;
     double lass_a[OR_MAXR], lass_b[OR_MAXR], lass_R[OR_MAXR]; /* Eq. 7-8 constants */
     int col_res[OR_MAXC], col_lam[OR_MAXC];
     int has_z;
@@ -333,7 +349,12 @@ or_model *or_model_new(const double *masses4, double m_lo, double m_hi, int n_re
     return mo;
 }
 
-void or_model_free(or_model *mo) { free(mo); }
+void or_model_free(or_model *mo)
+{
+    if (!mo) return;
+    for (int i = 0; i < 4; ++i) free(mo->tpl[i].h);
+    free(mo);
+}
 
 /* Make K* resonance R (J = 0) the LASS S-wave of Eq. 7-8 with effective-range
  * constants a, b (GeV^-1) and resonant-term factor Rfac.  Returns 0, or -1 if R
@@ -654,13 +675,64 @@ static double nval(nsum a) { return a.s + a.c; }
  * is requested.  mode 0: data (ln S and d ln S); mode 1: normalisation (w S and
  * w dS).  Returns -1 if a data event has S <= 0 (or p q <= 0).
  */
+/*
+ * S of one point (Eq. 5 / 12) and, when dS is non-NULL, dS/dtheta for every
+ * parameter: dS/dRe c_k = 2 Re z_k, dS/dIm c_k = -2 Im z_k with
+ * z_k = sum_xi conj(a_xi) B_k xi, and dS/dM_R = 2 Re sum_xi conj(a_xi)
+ * sum_{k in R} c_k dB_k xi/dM_R (the same for G0).  *pq receives p q and
+ * *kin (when non-NULL) the point's kinematics.
+ */
+static double event_S(const or_model *mo, const double *params, const double *M, const double *G,
+                      double m, double cK, double cpsi, double phi, double *dS, double *pq,
+                      or_kin *kin)
+{
+    const int K = mo->n_col;
+    or_event ev;
+    event_basis(mo, M, G, m, cK, cpsi, phi, dS != NULL, &ev);
+    if (pq) *pq = ev.pq;
+    if (kin) kinematics(mo, m, cK, cpsi, phi, kin);
+    cplx a[2] = {0, 0};
+    for (int x = 0; x < 2; ++x)
+        for (int c = 0; c < K; ++c) a[x] += (params[2 * c] + I * params[2 * c + 1]) * ev.B[c][x];
+    double S = 0.0;
+    for (int x = 0; x < 2; ++x) S += creal(a[x]) * creal(a[x]) + cimag(a[x]) * cimag(a[x]);
+    if (!dS) return S;
+    for (int c = 0; c < K; ++c) {
+        cplx z = conj(a[0]) * ev.B[c][0] + conj(a[1]) * ev.B[c][1];
+        dS[2 * c] = 2.0 * creal(z);
+        dS[2 * c + 1] = -2.0 * cimag(z);
+    }
+    for (int R = 0; R < mo->n_res; ++R) {
+        if (!mo->flt[R]) continue;
+        cplx yM = 0, yG = 0;
+        for (int c = 0; c < K; ++c) {
+            if (mo->col_res[c] != R) continue;
+            cplx cc = params[2 * c] + I * params[2 * c + 1];
+            for (int x = 0; x < 2; ++x) {
+                yM += conj(a[x]) * cc * ev.dBM[c][x];
+                yG += conj(a[x]) * cc * ev.dBG[c][x];
+            }
+        }
+        int f = 2 * K + 2 * mo->float_pos[R];
+        dS[f] = 2.0 * creal(yM);
+        dS[f + 1] = 2.0 * creal(yG);
+    }
+    return S;
+}
+
+/*
+ * Sums over a point set of: [0] ln S (or w S when weights mode), and the
+ * derivatives of the same quantity wrt every parameter (np of them) when grad
+ * is requested.  mode 0: data (ln S and d ln S); mode 1: normalisation (w S and
+ * w dS).  Returns -1 if a data event has S <= 0 (or p q <= 0).
+ */
 static int accumulate(const or_model *mo, const double *params, int mode, const double *m,
                       const double *cK, const double *cpsi, const double *phi, const double *w,
                       int64_t n, int want_grad, double *sum0, double *sum_lnpq, double *grad)
 {
     double M[OR_MAXR], G[OR_MAXR];
     pole_params(mo, params, M, G);
-    const int K = mo->n_col, NP = or_num_params(mo);
+    const int NP = or_num_params(mo);
     const int64_t nblk = (n + OR_BLOCK - 1) / OR_BLOCK;
     const int stride = 2 + NP;
     double *bs = (double *)calloc((size_t)(nblk > 0 ? nblk : 1) * stride, sizeof(double));
@@ -670,49 +742,25 @@ static int accumulate(const or_model *mo, const double *params, int mode, const 
         nsum acc0 = {0, 0}, accpq = {0, 0};
         nsum accg[2 * OR_MAXC + 2 * OR_MAXR];
         memset(accg, 0, sizeof(accg));
+        double dS[2 * OR_MAXC + 2 * OR_MAXR];
         int64_t e1 = (b + 1) * OR_BLOCK < n ? (b + 1) * OR_BLOCK : n;
         for (int64_t e = b * OR_BLOCK; e < e1; ++e) {
-            or_event ev;
-            event_basis(mo, M, G, m[e], cK[e], cpsi[e], phi[e], want_grad, &ev);
-            cplx a[2] = {0, 0};
-            for (int x = 0; x < 2; ++x)
-                for (int c = 0; c < K; ++c) a[x] += (params[2 * c] + I * params[2 * c + 1]) * ev.B[c][x];
-            double S = 0.0;
-            for (int x = 0; x < 2; ++x) S += creal(a[x]) * creal(a[x]) + cimag(a[x]) * cimag(a[x]);
+            double pq;
+            const double S = event_S(mo, params, M, G, m[e], cK[e], cpsi[e], phi[e],
+                                     want_grad ? dS : NULL, &pq, NULL);
             double scale;
             if (mode == 0) {
-                if (!(S > 0.0) || !(ev.pq > 0.0)) { bad = 1; continue; }
+                if (!(S > 0.0) || !(pq > 0.0)) { bad = 1; continue; }
                 nadd(&acc0, log(S));
-                nadd(&accpq, log(ev.pq));
+                nadd(&accpq, log(pq));
                 scale = 1.0 / S;
             } else {
-                double we = w ? w[e] : ev.pq;
+                double we = w ? w[e] : pq;
                 nadd(&acc0, we * S);
                 scale = we;
             }
             if (!want_grad) continue;
-            /* dS/dRe c_k = 2 Re z_k, dS/dIm c_k = -2 Im z_k, z_k = sum_xi conj(a_xi) B_k xi. */
-            for (int c = 0; c < K; ++c) {
-                cplx z = conj(a[0]) * ev.B[c][0] + conj(a[1]) * ev.B[c][1];
-                nadd(&accg[2 * c], scale * 2.0 * creal(z));
-                nadd(&accg[2 * c + 1], scale * -2.0 * cimag(z));
-            }
-            /* dS/dM_R = 2 Re sum_xi conj(a_xi) sum_{k in R} c_k dB_k xi/dM_R (same for G). */
-            for (int R = 0; R < mo->n_res; ++R) {
-                if (!mo->flt[R]) continue;
-                cplx yM = 0, yG = 0;
-                for (int c = 0; c < K; ++c) {
-                    if (mo->col_res[c] != R) continue;
-                    cplx cc = params[2 * c] + I * params[2 * c + 1];
-                    for (int x = 0; x < 2; ++x) {
-                        yM += conj(a[x]) * cc * ev.dBM[c][x];
-                        yG += conj(a[x]) * cc * ev.dBG[c][x];
-                    }
-                }
-                int f = 2 * K + 2 * mo->float_pos[R];
-                nadd(&accg[f], scale * 2.0 * creal(yM));
-                nadd(&accg[f + 1], scale * 2.0 * creal(yG));
-            }
+            for (int i = 0; i < NP; ++i) nadd(&accg[i], scale * dS[i]);
         }
         double *o = bs + b * stride;
         o[0] = nval(acc0);
@@ -783,6 +831,191 @@ int or_nll(const or_model *mo, const double *params, const double *m, const doub
         free(gd);
         free(gI);
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Efficiency and background (Eq. 14)                                  */
+/* ------------------------------------------------------------------ */
+
+/* Content of a binned template at (x, y): bin ix = floor((x - xlo) * nx / (xhi - xlo)),
+ * iy likewise, content h[iy * nx + ix]; the upper edge belongs to the last bin,
+ * and the template is 0 outside [xlo, xhi] x [ylo, yhi]. */
+static double tpl_value(const double *h, int nx, int ny, double xlo, double xhi, double ylo,
+                        double yhi, double x, double y)
+{
+    if (!(x >= xlo && x <= xhi && y >= ylo && y <= yhi)) return 0.0;
+    int ix = (int)floor((x - xlo) * nx / (xhi - xlo));
+    int iy = (int)floor((y - ylo) * ny / (yhi - ylo));
+    if (ix >= nx) ix = nx - 1;
+    if (iy >= ny) iy = ny - 1;
+    return h[(int64_t)iy * nx + ix];
+}
+
+double or_tpl_value(const double *h, int nx, int ny, const double *range, double x, double y)
+{
+    return tpl_value(h, nx, ny, range[0], range[1], range[2], range[3], x, y);
+}
+
+/* Set the efficiency (which = 0) or background (which = 1, with purity P in
+ * [0, 1]) templates: hm over (m^2_Kpi, m^2_psipi) with range rm = {xlo, xhi, ylo,
+ * yhi}, ha over (cos theta_psi, phi) with range ra.  Returns 0, or -1 on a bad
+ * argument. */
+int or_model_set_template(or_model *mo, int which, const double *hm, int nxm, int nym,
+                          const double *rm, const double *ha, int nxa, int nya, const double *ra,
+                          double purity)
+{
+    if (which != 0 && which != 1) return -1;
+    if (nxm < 1 || nym < 1 || nxa < 1 || nya < 1 || !hm || !ha) return -1;
+    if (!(rm[1] > rm[0]) || !(rm[3] > rm[2]) || !(ra[1] > ra[0]) || !(ra[3] > ra[2])) return -1;
+    if (which == 1 && !(purity >= 0.0 && purity <= 1.0)) return -1;
+    const double *src[2] = {hm, ha};
+    const int nx[2] = {nxm, nxa}, ny[2] = {nym, nya};
+    const double *rg[2] = {rm, ra};
+    for (int j = 0; j < 2; ++j) {
+        int t = 2 * which + j;
+        free(mo->tpl[t].h);
+        mo->tpl[t].h = (double *)malloc((size_t)nx[j] * ny[j] * sizeof(double));
+        memcpy(mo->tpl[t].h, src[j], (size_t)nx[j] * ny[j] * sizeof(double));
+        mo->tpl[t].nx = nx[j]; mo->tpl[t].ny = ny[j];
+        mo->tpl[t].xlo = rg[j][0]; mo->tpl[t].xhi = rg[j][1];
+        mo->tpl[t].ylo = rg[j][2]; mo->tpl[t].yhi = rg[j][3];
+    }
+    if (which == 0) mo->has_eff = 1;
+    else { mo->has_bkg = 1; mo->purity = purity; }
+    return 0;
+}
+
+static double tpl_at(const or_model *mo, int t, double x, double y)
+{
+    return tpl_value(mo->tpl[t].h, mo->tpl[t].nx, mo->tpl[t].ny, mo->tpl[t].xlo, mo->tpl[t].xhi,
+                     mo->tpl[t].ylo, mo->tpl[t].yhi, x, y);
+}
+
+/* eps and the background template value hb at one point (1 and 0 when unset),
+ * with m^2_psipi from the point's four-vectors. */
+static void point_templates(const or_model *mo, double m, double cK, double cpsi, double phi,
+                            double *eps, double *hb)
+{
+    or_kin k;
+    kinematics(mo, m, cK, cpsi, phi, &k);
+    const double x = m * m, y = k.m_psipi * k.m_psipi;
+    *eps = mo->has_eff ? tpl_at(mo, 0, x, y) * tpl_at(mo, 1, cpsi, phi) : 1.0;
+    *hb = mo->has_bkg ? tpl_at(mo, 2, x, y) * tpl_at(mo, 3, cpsi, phi) : 0.0;
+}
+
+/* Per point: out[3 e] = eps, out[3 e + 1] = hb, out[3 e + 2] = m^2_psipi. */
+void or_templates(const or_model *mo, const double *m, const double *cK, const double *cpsi,
+                  const double *phi, int64_t n, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n; ++e) {
+        or_kin k;
+        kinematics(mo, m[e], cK[e], cpsi[e], phi[e], &k);
+        point_templates(mo, m[e], cK[e], cpsi[e], phi[e], &out[3 * e], &out[3 * e + 1]);
+        out[3 * e + 2] = k.m_psipi * k.m_psipi;
+    }
+}
+
+/*
+ * -2 ln L of Eq. 14.  Per event the PDF in (m, cK, cpsi, phi) is
+ *   f = p q [ P eps S / I_eps + (1 - P) hb / B ],
+ *   I_eps = (V / N_mc) sum_n w_n eps_n S_n,   B = (V / N_mc) sum_n w_n hb_n,
+ * over the normalisation points (w = p q when nw is NULL); without a background
+ * P = 1.  NLL = -2 sum_e ln f_e and
+ *   d ln f_e / dtheta = (P eps_e p_e q_e / (I_eps f_e)) (dS_e - S_e dI_eps / I_eps).
+ * aux (5 doubles): sum ln(f / (p q)), sum ln(p q), I_eps, B, sum_e r_e with
+ * r_e = P eps_e S_e p_e q_e / (I_eps f_e) the signal probability of event e.
+ * Returns -1 (NLL = +inf) if some f_e <= 0, p q <= 0 or I_eps <= 0.
+ */
+int or_nll_eq14(const or_model *mo, const double *params, const double *m, const double *cK,
+                const double *cpsi, const double *phi, int64_t n, const double *nm,
+                const double *ncK, const double *ncpsi, const double *nphi, const double *nw,
+                int64_t n_mc, double volume, double *nll, double *grad, double *aux)
+{
+    const int NP = or_num_params(mo);
+    const double P = mo->has_bkg ? mo->purity : 1.0;
+    /* normalisation points: efficiency-weighted weights and the background sum */
+    double *weps = (double *)malloc((size_t)(n_mc > 0 ? n_mc : 1) * sizeof(double));
+    double *whb = (double *)malloc((size_t)(n_mc > 0 ? n_mc : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n_mc; ++i) {
+        double eps, hb, w = nw ? nw[i] : 0.0;
+        point_templates(mo, nm[i], ncK[i], ncpsi[i], nphi[i], &eps, &hb);
+        if (!nw) {
+            or_kin k;
+            kinematics(mo, nm[i], ncK[i], ncpsi[i], nphi[i], &k);
+            w = k.p * k.q;
+        }
+        weps[i] = w * eps;
+        whb[i] = w * hb;
+    }
+    double sI, Bs = 0.0;
+    double *gI = (double *)calloc(NP > 0 ? NP : 1, sizeof(double));
+    accumulate(mo, params, 1, nm, ncK, ncpsi, nphi, weps, n_mc, grad != NULL, &sI, NULL, gI);
+    const double Ie = volume / (double)n_mc * sI;
+    {
+        nsum b = {0, 0};
+        for (int64_t i = 0; i < n_mc; ++i) nadd(&b, whb[i]);
+        Bs = volume / (double)n_mc * nval(b);
+    }
+    free(weps);
+    free(whb);
+    for (int i = 0; i < NP; ++i) gI[i] *= volume / (double)n_mc;
+    /* data events, in blocks of fixed size summed in block order */
+    double Mp[OR_MAXR], Gp[OR_MAXR];
+    pole_params(mo, params, Mp, Gp);
+    const int64_t nblk = (n + OR_BLOCK - 1) / OR_BLOCK;
+    const int stride = 3 + NP;
+    double *bs = (double *)calloc((size_t)(nblk > 0 ? nblk : 1) * stride, sizeof(double));
+    int bad = !(Ie > 0.0) || (P < 1.0 && !(Bs > 0.0));
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t b = 0; b < nblk; ++b) {
+        nsum sl = {0, 0}, spq = {0, 0}, sr = {0, 0};
+        nsum sg[2 * OR_MAXC + 2 * OR_MAXR];
+        memset(sg, 0, sizeof(sg));
+        double dS[2 * OR_MAXC + 2 * OR_MAXR];
+        int64_t e1 = (b + 1) * OR_BLOCK < n ? (b + 1) * OR_BLOCK : n;
+        for (int64_t e = b * OR_BLOCK; e < e1; ++e) {
+            double pq, eps, hb;
+            const double S = event_S(mo, params, Mp, Gp, m[e], cK[e], cpsi[e], phi[e],
+                                     grad ? dS : NULL, &pq, NULL);
+            point_templates(mo, m[e], cK[e], cpsi[e], phi[e], &eps, &hb);
+            const double sig = P * eps * S / Ie;
+            const double g = sig + (P < 1.0 ? (1.0 - P) * hb / Bs : 0.0);   /* f / (p q) */
+            if (!(g > 0.0) || !(pq > 0.0)) { bad = 1; continue; }
+            nadd(&sl, log(g));
+            nadd(&spq, log(pq));
+            nadd(&sr, sig / g);
+            if (!grad) continue;
+            const double c = P * eps / (Ie * g);
+            for (int i = 0; i < NP; ++i) nadd(&sg[i], c * (dS[i] - S * gI[i] / Ie));
+        }
+        double *o = bs + b * stride;
+        o[0] = nval(sl);
+        o[1] = nval(spq);
+        o[2] = nval(sr);
+        for (int i = 0; i < NP; ++i) o[3 + i] = nval(sg[i]);
+    }
+    nsum tl = {0, 0}, tpq = {0, 0}, tr = {0, 0};
+    nsum tg[2 * OR_MAXC + 2 * OR_MAXR];
+    memset(tg, 0, sizeof(tg));
+    for (int64_t b = 0; b < nblk; ++b) {
+        nadd(&tl, bs[b * stride]);
+        nadd(&tpq, bs[b * stride + 1]);
+        nadd(&tr, bs[b * stride + 2]);
+        for (int i = 0; i < NP; ++i) nadd(&tg[i], bs[b * stride + 3 + i]);
+    }
+    free(bs);
+    free(gI);
+    if (aux) { aux[0] = nval(tl); aux[1] = nval(tpq); aux[2] = Ie; aux[3] = Bs; aux[4] = nval(tr); }
+    if (bad) {
+        *nll = INFINITY;
+        if (grad) for (int i = 0; i < NP; ++i) grad[i] = 0.0;
+        return -1;
+    }
+    *nll = -2.0 * (nval(tl) + nval(tpq));
+    if (grad) for (int i = 0; i < NP; ++i) grad[i] = -2.0 * nval(tg[i]);
     return 0;
 }
 

@@ -293,6 +293,130 @@ def test_lass_rejected_where_it_does_not_apply():
         _lass_model(a=0.0)
 
 
+# ---------------------------------------------------------------- efficiency and background (Eq. 14)
+def _hist(h, rng):
+    return W.Hist2D(np.asarray(h, dtype=np.float32), rng)
+
+
+def test_template_bin_rule():
+    """Bin i covers [lo + i d, lo + (i+1) d); the upper edge is in the last bin;
+    0 outside the range."""
+    h = _hist([[1, 2, 3, 4], [11, 12, 13, 14]], (0.0, 1.0, 0.0, 2.0))
+    cases = [((0.0, 0.0), 1), ((0.2499, 0.0), 1), ((0.25, 0.0), 2), ((0.9, 1.0), 14),
+             ((1.0, 2.0), 14), ((0.5, 0.999), 3), ((0.74, 1.5), 13), ((-1e-9, 0.5), 0),
+             ((0.5, 2.0 + 1e-9), 0), ((1.0 + 1e-9, 1.0), 0)]
+    for (x, y), ref in cases:
+        assert O.tpl_value(h, x, y) == ref, (x, y)
+
+
+def test_templates_read_the_dalitz_variables():
+    """The mass template is read at (m^2_Kpi, m^2_psipi); m^2_psipi from the
+    oracle's four-vectors equals the closed form in the K pi frame,
+    m_psi^2 + m_pi^2 + 2 (E_psi E_pi - p* q cos theta_K*), p* = p m_B / m."""
+    mo = O.Model([W.RESONANCES["K*(892)"]])
+    ym = _hist(np.arange(1, 401, dtype=float).reshape(400, 1), (0.0, 1e3, 8.0, 24.0))
+    ones_a = _hist(np.ones((1, 1)), W.ANGLE_RANGE)
+    mo.set_template(0, ym, ones_a)
+    pts = W.uniform_points(300, 21, box=(W.M_LO, W.M_END - 1e-6))
+    eps, hb, m2z = mo.templates(pts)
+    for i in range(300):
+        m, cK = float(pts[0][i]), float(pts[1][i])
+        p = O.breakup(W.M_B, m, W.M_PSI)
+        q = O.breakup(m, W.M_K, W.M_PI)
+        ps = p * W.M_B / m
+        ref = W.M_PSI ** 2 + W.M_PI ** 2 + 2 * (math.hypot(W.M_PSI, ps) * math.hypot(W.M_PI, q) - ps * q * cK)
+        assert m2z[i] == pytest.approx(ref, rel=1e-12)
+        assert eps[i] == O.tpl_value(ym, m * m, m2z[i]) and hb[i] == 0.0
+
+
+def _eq14_case(name="tiny", n_ev=3000, n_mc=6000):
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    ev = W.peaked_points(n_ev, 31, res)
+    nm = W.uniform_points(n_mc, 32)
+    return res, p, ev, nm
+
+
+def test_eq14_reduces_to_the_signal_fit():
+    """P = 1 with a constant efficiency c: f = p q c S / (c I) = p q S / I, the
+    signal-only likelihood, for any c."""
+    res, p, ev, nm = _eq14_case()
+    plain = O.Model(res)
+    nll0, g0, aux0, rc0 = plain.nll(p, ev, nm, grad=True)
+    for c in (1.0, float(np.float32(0.37))):   # templates hold FP32 contents
+        mo = O.Model(res)
+        mo.set_template(0, _hist(np.full((3, 2), c), W.MASS2_RANGE), _hist(np.ones((2, 5)), W.ANGLE_RANGE))
+        nll, g, aux, rc = mo.nll_eq14(p, ev, nm, grad=True)
+        assert rc == 0 and rc0 == 0
+        assert nll == pytest.approx(nll0, rel=1e-12)
+        assert np.allclose(g, g0, rtol=1e-9, atol=1e-9 * np.max(np.abs(g0)))
+        assert aux[2] == pytest.approx(c * aux0[2], rel=1e-12)
+        assert aux[4] == pytest.approx(len(ev[0]), rel=1e-12)
+
+
+def test_eq14_pure_background():
+    """P = 0: f = p q hb / B does not depend on the couplings; with a flat
+    background B = int p q dPhi = 8 pi int p(m) q(m) dm (quadrature) within the
+    Monte Carlo error of the points."""
+    res, p, ev, nm = _eq14_case(n_mc=200_000)
+    mo = O.Model(res)
+    one_m, one_a = _hist(np.ones((4, 4)), W.MASS2_RANGE), _hist(np.ones((2, 2)), W.ANGLE_RANGE)
+    mo.set_template(1, one_m, one_a, purity=0.0)
+    nll, g, aux, rc = mo.nll_eq14(p, ev, nm, grad=True)
+    nll2, _, _, _ = mo.nll_eq14(p * 1.7 + 0.1, ev, nm)
+    assert rc == 0 and nll2 == pytest.approx(nll, rel=1e-13)
+    assert np.all(g == 0.0)
+    quad = 8 * math.pi * integrate.quad(
+        lambda m: O.breakup(W.M_B, m, W.M_PSI) * O.breakup(m, W.M_K, W.M_PI), W.M_LO, W.M_HI,
+        limit=200, epsabs=0, epsrel=1e-12)[0]
+    pq = O.Model(res).density(p, nm)[1]
+    sem = W.BOX_VOLUME * np.std(pq) / math.sqrt(len(pq))
+    assert abs(aux[3] - quad) < 4 * sem
+    assert nll == pytest.approx(-2 * (aux[1] - len(ev[0]) * math.log(aux[3])), rel=1e-12)
+
+
+def test_eq14_pdf_integrates_to_one():
+    """With efficiency and background templates and P = 0.85 the PDF
+    p q [P eps S / I_eps + (1 - P) hb / B] integrates to 1: its mean over an
+    independent uniform sample times the box volume, within the Monte Carlo error."""
+    res, p, ev, nm = _eq14_case(n_mc=100_000)
+    em, ea, bm, ba, P = W.eq14_templates(3)
+    mo = O.Model(res)
+    mo.set_template(0, em, ea)
+    mo.set_template(1, bm, ba, purity=P)
+    _, _, aux, rc = mo.nll_eq14(p, ev, nm)
+    assert rc == 0
+    fresh = W.uniform_points(100_000, 33)
+    S, pq = mo.density(p, fresh)
+    eps, hb, _ = mo.templates(fresh)
+    f = pq * (P * eps * S / aux[2] + (1 - P) * hb / aux[3])
+    est = W.BOX_VOLUME * f.mean()
+    sem = W.BOX_VOLUME * f.std() / math.sqrt(len(f))
+    assert abs(est - 1.0) < 4 * sem + 0.0
+
+
+def test_eq14_gradient_matches_central_differences():
+    res, p, ev, nm = _eq14_case("kstar10_z", 400, 800)
+    cfg = W.CONFIGS["kstar10_z"]
+    mo = O.Model(res, float_names=["K*(892)", "Z(4430)"])
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed),
+                              W.float_mg_values(res, ["K*(892)", "Z(4430)"]))
+    em, ea, bm, ba, P = W.eq14_templates(4)
+    mo.set_template(0, em, ea)
+    mo.set_template(1, bm, ba, purity=P)
+    _, g, _, rc = mo.nll_eq14(p, ev, nm, grad=True)
+    assert rc == 0
+    rng = np.random.default_rng(6)
+    for i in sorted(rng.choice(len(p), 14, replace=False)) + [len(p) - 1, len(p) - 3]:
+        h = 1e-6 * max(1.0, abs(p[i]))
+        up, dn = p.copy(), p.copy()
+        up[i] += h
+        dn[i] -= h
+        fd = (mo.nll_eq14(up, ev, nm)[0] - mo.nll_eq14(dn, ev, nm)[0]) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-5 * max(1.0, abs(g[i]))
+
+
 # ---------------------------------------------------------------- kinematics
 def test_kstar_angles_round_trip():
     mo = _all_model()

@@ -146,6 +146,11 @@ class Config:
     n_events: int
     n_norm: int
     float_mg: list = field(default_factory=list)   # names whose M, Gamma float
+    eq14: bool = False   # efficiency and background templates (Eq. 14)
+
+    @property
+    def template_seed(self):
+        return 1400 + self.index
 
     @property
     def resonances(self):
@@ -182,7 +187,59 @@ CONFIGS = {
     # Eq. 9 with Z(4430); every mass and width but the LASS pole's floating.
     "lass_z": Config("lass_z", 8, ["LASS"] + KSTAR_PRIME + ["Z(4430)"], 200_000, 2_000_000,
                      float_mg=KSTAR_PRIME + ["Z(4430)"]),
+    # The paper's real-life test (Eq. 14): 10 K* + Z(4200) + Z(4430) with a
+    # relative efficiency and 15 % background.
+    "real_life": Config("real_life", 9, ALL_KSTAR + ["Z(4200)", "Z(4430)"], 1_000_000, 1 << 22,
+                        eq14=True),
 }
+
+
+# ---------------------------------------------------------------- Eq. 14 templates
+@dataclass
+class Hist2D:
+    """Binned template: contents h[iy, ix] (FP32) over [x_lo, x_hi] x [y_lo, y_hi]."""
+    h: np.ndarray
+    range: tuple
+
+    @property
+    def nx(self):
+        return int(self.h.shape[1])
+
+    @property
+    def ny(self):
+        return int(self.h.shape[0])
+
+
+# Template axes: the two mass variables (m^2_Kpi, m^2_psipi over the Dalitz
+# plot's bounding box) and the two angles (cos theta_psi, phi).
+MASS2_RANGE = (M_LO ** 2, M_HI ** 2, (M_PSI + M_PI) ** 2, (M_B - M_K) ** 2)
+ANGLE_RANGE = (-1.0, 1.0, -math.pi, math.pi)
+PURITY = 0.85   # signal purity of the paper's real-life test (15 % background)
+
+
+def bernstein_hist(nx, ny, rng_xy, degree, seed, floor=0.2):
+    """A 2D Bernstein polynomial of the given degree with seeded coefficients in
+    [floor, 1], binned at the bin centres and scaled to a maximum of 1: the
+    generic template shape of the paper's efficiency and background tests."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    coef = rng.uniform(floor, 1.0, size=(degree + 1, degree + 1))
+    u = (np.arange(nx) + 0.5) / nx
+    v = (np.arange(ny) + 0.5) / ny
+    bu = np.array([math.comb(degree, i) * u ** i * (1 - u) ** (degree - i) for i in range(degree + 1)])
+    bv = np.array([math.comb(degree, j) * v ** j * (1 - v) ** (degree - j) for j in range(degree + 1)])
+    h = bv.T @ coef.T @ bu          # [ny, nx]
+    h = h / h.max()
+    return Hist2D(h.astype(np.float32), tuple(float(x) for x in rng_xy))
+
+
+def eq14_templates(seed):
+    """(efficiency x masses, efficiency x angles, background x masses,
+    background x angles, purity), seeded."""
+    return (bernstein_hist(40, 40, MASS2_RANGE, 3, seed),
+            bernstein_hist(20, 24, ANGLE_RANGE, 2, seed + 1),
+            bernstein_hist(30, 30, MASS2_RANGE, 2, seed + 2, floor=0.05),
+            bernstein_hist(16, 16, ANGLE_RANGE, 2, seed + 3, floor=0.3),
+            PURITY)
 
 
 def draw_couplings(res_list, seed, z_scale=Z_COUPLING_SCALE):
