@@ -154,6 +154,51 @@ amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const flo
                                    int64_t n, double volume, void *stream);
 
 /*
+ * Binned 2D template (efficiency and background of Eq. 14).  h: nx * ny FP32
+ * contents, h[iy * nx + ix] (host or device memory; copied by the setters, the
+ * caller keeps ownership).  The content at (x, y) is that of the bin
+ * ix = floor((x - x_lo) * nx / (x_hi - x_lo)), iy likewise, evaluated in FP64 in
+ * that order; the upper edge belongs to the last bin and the template is 0
+ * outside [x_lo, x_hi] x [y_lo, y_hi].
+ */
+typedef struct {
+    const float *h;
+    int nx, ny;                     /* >= 1                     */
+    double x_lo, x_hi, y_lo, y_hi;  /* x_hi > x_lo, y_hi > y_lo */
+} amp4d_hist2d;
+
+/*
+ * Relative signal efficiency of Eq. 14, eps = mass(m_Kpi^2, m_psipi^2) *
+ * angle(cos theta_psi, phi): a template in the two mass variables (GeV^2; m_psipi
+ * computed in FP64 from m_Kpi and cos theta_K*) times one in the two angles.
+ * From then on the signal is normalised with efficiency-weighted points,
+ * I_eps = (V / n) sum w eps S (also the Gram matrix), and the likelihood of an
+ * event is p q eps S / I_eps (without a background).  Applies to the sets
+ * loaded and to those loaded later.  mass = angle = NULL removes it.
+ * Synchronous.  Errors: ARG, CUDA, OOM.
+ */
+amp4d_status amp4d_set_efficiency(amp4d_model *model, const amp4d_hist2d *mass,
+                                  const amp4d_hist2d *angle, void *stream);
+
+/*
+ * Background of Eq. 14 with the fixed signal purity P in [0, 1]: the PDF of an
+ * event becomes
+ *   f = p q [ P eps S / I_eps + (1 - P) hb / B ],   hb = mass(m_Kpi^2, m_psipi^2) *
+ *   angle(cos theta_psi, phi),   B = (V / n) sum_n w_n hb_n,
+ * hb a density in the Dalitz variables and the angles (so its density in the
+ * event coordinates carries p q), B over the normalisation points with their
+ * weights as loaded.  With a background (P < 1) each evaluation computes I_eps
+ * before the data pass (the Gram quadratic form, or the point sum first).  The
+ * NLL is -2 sum ln f; in the evaluation outputs "sum ln S" becomes
+ * sum ln(f / (p q)) and I is I_eps.  Shard partials and fit fractions are not
+ * available with a background (STATE); fit fractions need a model without an
+ * efficiency too (they are defined on S).  mass = angle = NULL removes it.
+ * Synchronous.  Errors: ARG, CUDA, OOM.
+ */
+amp4d_status amp4d_set_background(amp4d_model *model, const amp4d_hist2d *mass,
+                                  const amp4d_hist2d *angle, double purity, void *stream);
+
+/*
  * -2 ln L at params (host, amp4d_num_params doubles); *nll is host memory.
  * On AMP4D_ERR_DOMAIN *nll = +INFINITY (the minimiser treats it as a bad step).
  */

@@ -140,6 +140,11 @@ class amp4d_resonance(C.Structure):
                 ("lass_b", C.c_double), ("lass_R", C.c_double)]
 
 
+class amp4d_hist2d(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("nx", C.c_int), ("ny", C.c_int), ("x_lo", C.c_double),
+                ("x_hi", C.c_double), ("y_lo", C.c_double), ("y_hi", C.c_double)]
+
+
 class amp4d_mlp_cfg(C.Structure):
     _fields_ = [("nb", C.c_int * 4), ("alpha", C.c_double), ("steps", C.c_int64),
                 ("batch", C.c_int), ("lr", C.c_double)]
@@ -176,6 +181,10 @@ amp4d_eval_pdf = _proto("amp4d_eval_pdf", C.c_int, [_vp, _d, _vp, _vp])
 amp4d_build_gram = _proto("amp4d_build_gram", C.c_int, [_vp, _d, _vp])
 amp4d_get_gram = _proto("amp4d_get_gram", C.c_int, [_vp, _d, _vp])
 amp4d_fit_fractions = _proto("amp4d_fit_fractions", C.c_int, [_vp, _d, _d, _vp])
+amp4d_set_efficiency = _proto("amp4d_set_efficiency", C.c_int,
+                              [_vp, C.POINTER(amp4d_hist2d), C.POINTER(amp4d_hist2d), _vp])
+amp4d_set_background = _proto("amp4d_set_background", C.c_int,
+                              [_vp, C.POINTER(amp4d_hist2d), C.POINTER(amp4d_hist2d), C.c_double, _vp])
 amp4d_gram_selftest = _proto("amp4d_gram_selftest", C.c_int, [_vp, C.c_int64, _vp, _vp])
 amp4d_generate = _proto("amp4d_generate", C.c_int, [_vp, _d, C.c_uint64, C.c_int64, _vp, _vp, _vp, _vp, _vp])
 amp4d_proposal_train = _proto("amp4d_proposal_train", C.c_int,
@@ -199,7 +208,8 @@ amp4d_shard_last_error = _proto("amp4d_shard_last_error", C.c_char_p, [])
 amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
 amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
 
-EXPORTED = ["amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "amp4d_num_columns",
+EXPORTED = ["amp4d_set_efficiency", "amp4d_set_background",
+            "amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "amp4d_num_columns",
             "amp4d_num_params", "amp4d_set_events", "amp4d_set_norm_points", "amp4d_eval_nll",
             "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
             "amp4d_profile_enable", "amp4d_profile_read", "amp4d_build_gram", "amp4d_get_gram",
@@ -351,6 +361,31 @@ class Model:
     def build_gram(self, params, stream=None):
         p = self._params(params)
         self._check(amp4d_build_gram(self.h, p.ctypes.data_as(_d), _stream_ptr(stream)))
+
+    @staticmethod
+    def _hist(t):
+        """ctypes record of a template with h[iy, ix] contents (FP32, kept alive by the caller)."""
+        h = np.ascontiguousarray(t.h, dtype=np.float32)
+        r = t.range
+        return amp4d_hist2d(h.ctypes.data, int(h.shape[1]), int(h.shape[0]), *map(float, r)), h
+
+    def set_efficiency(self, mass, angle, stream=None):
+        """Eq. 14 relative efficiency: templates over (m^2_Kpi, m^2_psipi) and
+        (cos theta_psi, phi) (objects with .h [ny, nx] and .range); None removes it."""
+        if mass is None:
+            self._check(amp4d_set_efficiency(self.h, None, None, _stream_ptr(stream)))
+            return
+        (hm, km), (ha, ka) = self._hist(mass), self._hist(angle)
+        self._check(amp4d_set_efficiency(self.h, C.byref(hm), C.byref(ha), _stream_ptr(stream)))
+
+    def set_background(self, mass, angle, purity, stream=None):
+        """Eq. 14 background templates with signal purity P; None removes it."""
+        if mass is None:
+            self._check(amp4d_set_background(self.h, None, None, 1.0, _stream_ptr(stream)))
+            return
+        (hm, km), (ha, ka) = self._hist(mass), self._hist(angle)
+        self._check(amp4d_set_background(self.h, C.byref(hm), C.byref(ha), float(purity),
+                                         _stream_ptr(stream)))
 
     def fit_fractions(self, params, stream=None):
         """Fit fraction of every resonance (Eq. 13), in creation order (host float64)."""

@@ -33,6 +33,12 @@ struct EventSet {
     size_t part_cap = 0;
     float2 *lcache = nullptr;   // basis cache [resonance][npad] (cached path)
     bool lcache_valid = false;
+    // Eq. 14 templates: data sets hold eps and hb per event (npad each); a
+    // normalisation set keeps its weights as loaded in w0 and its weight record
+    // holds w0 eps.
+    float *eps = nullptr, *hb = nullptr, *w0 = nullptr;
+    double lneps = 0.0;         // data: sum ln eps over the events
+    double whb = 0.0;           // points: sum w0 hb
 };
 
 thread_local std::string g_create_error;
@@ -64,7 +70,7 @@ struct amp4d_model {
     double prof_ms[4] = {0, 0, 0, 0};
     int64_t prof_n[4] = {0, 0, 0, 0};
     int *d_slot_param = nullptr;
-    unsigned long long *d_acc = nullptr;   // 128-bit sums: [data, points][nslot][hi, lo]
+    unsigned long long *d_acc = nullptr;   // 128-bit sums: [data, points][nslot][hi, lo], R
     double *d_out = nullptr, *h_out = nullptr;
     unsigned *d_status = nullptr;
     unsigned long long *d_bad = nullptr;
@@ -79,6 +85,11 @@ struct amp4d_model {
     int gram_grid = 0;
     bool gram_valid = false;
     bool table_built = false;    // one full table build enqueued (all masses fixed)
+    // Eq. 14: templates [efficiency x masses, x angles, background x masses, x angles]
+    float *d_tpl[4] = {nullptr, nullptr, nullptr, nullptr};
+    TplDev tpl[4] = {};
+    bool has_eff = false, has_bkg = false;
+    double purity = 1.0;
     bool kstar_fixed = true;     // no K* has a floating mass or width
     bool z_float = false;        // some Z has a floating mass and width
     // learned proposal
@@ -166,6 +177,9 @@ amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const flo
     if (s.rec) { cudaFree(s.rec); s.rec = nullptr; }
     if (s.part) { cudaFree(s.part); s.part = nullptr; }
     if (s.lcache) { cudaFree(s.lcache); s.lcache = nullptr; }
+    for (float **b : {&s.eps, &s.hb, &s.w0})
+        if (*b) { cudaFree(*b); *b = nullptr; }
+    s.lneps = s.whb = 0.0;
     s.lcache_valid = false;
     s.n = 0;
     const int64_t npad = (n + 3) & ~int64_t(3);
@@ -228,7 +242,7 @@ cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t 
 {
     const bool fast = mo->n_float == 0 && mo->table_built;
     cudaError_t e = launch_build_table(mo->d_static, d_params, mo->d_md, mo->d_pscale, mo->d_status,
-                                       st, fast, mo->d_acc, 4 * mo->nslot);
+                                       st, fast, mo->d_acc, 4 * mo->nslot + 2);
     if (e == cudaSuccess && mo->n_float == 0) mo->table_built = true;
     return e;
 }
@@ -262,6 +276,11 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.kstar_fixed = mo->kstar_fixed;
     a.z_float = mo->z_float;
     a.acc = (&s == &mo->ev) ? mo->d_acc : mo->d_acc + 2 * mo->nslot;
+    if (&s == &mo->ev && mo->has_bkg && mo->purity < 1.0 && s.eps && s.hb) {
+        a.mix_eps = s.eps;
+        a.mix_hb = s.hb;
+        a.acc_r = mo->d_acc + 4 * mo->nslot;
+    }
     return a;
 }
 
@@ -302,6 +321,9 @@ cudaEvent_t prof_event(amp4d_model *m)
     cudaEventCreate(&e);
     return e;
 }
+
+// Eq. 14 with a background: the data term mixes signal and background.
+bool mixing(const amp4d_model *m) { return m->has_bkg && m->purity < 1.0; }
 
 bool use_gram(const amp4d_model *m)
 {
@@ -358,6 +380,15 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
 {
     if (model->ev.n == 0 || model->mc.n == 0)
         return fail(model, AMP4D_ERR_STATE, "set_events and set_norm_points must come first");
+    const bool mix = mixing(model);
+    if (mix && partials)
+        return fail(model, AMP4D_ERR_STATE, "shard partials are not available with a background");
+    if (mix && !(model->mc.whb > 0.0))
+        return fail(model, AMP4D_ERR_DOMAIN, "the background template is 0 over the normalisation points");
+    // Parameter-independent part of ln f per event: ln(p q), and ln eps with an
+    // efficiency but no background (with a background eps sits inside g).
+    const double lnconst = model->ev.lnpq + (mix ? 0.0 : model->ev.lneps);
+    const unsigned long long *ar = mix ? model->d_acc + 4 * model->nslot : nullptr;
     std::vector<cudaEvent_t> marks;
     auto mark = [&]() {
         if (!model->prof_on) return cudaSuccess;
@@ -382,6 +413,11 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
             if (rc) return rc;
         }
         const double von = model->mc.volume / (double)model->mc.n;
+        if (mix)   // alpha = P / I_eps from the Gram quadratic form, before the data pass
+            CK(launch_finish_gram(ad, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
+                                  model->n_param, (double)model->ev.n, lnconst, von, d_params,
+                                  model->d_G, model->d_status, d_out, 0, st, (double)model->mc.n, 0,
+                                  nullptr, model->d_md, model->purity));
         if (with_grad) {
             LaunchArgs la = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
             CK(launch_grad(la, false));
@@ -392,44 +428,47 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         CK(mark());
         CK(mark());
         CK(launch_finish_gram(ad, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
-                              model->n_param, (double)model->ev.n, model->ev.lnpq, von, d_params,
+                              model->n_param, (double)model->ev.n, lnconst, von, d_params,
                               model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st,
-                              (double)model->mc.n, partials ? 1 : 0));
+                              (double)model->mc.n, partials ? 1 : 0, ar));
         CK(mark());
         if (model->prof_on) model->prof_pending.push_back(marks);
         return AMP4D_OK;
     }
-    if (with_grad) {
-        LaunchArgs ld = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
-        CK(launch_grad(ld, false));
+    // Data pass and point pass.  With a background the point pass runs first:
+    // the data pass needs alpha = P / I_eps (the profile's second interval is
+    // then the point pass, the third the data pass).
+    const double von = model->mc.volume / (double)model->mc.n;
+    auto data_pass = [&]() -> cudaError_t {
+        LaunchArgs ld = args_for(model, model->ev, model->ev.part, nullptr, st,
+                                 with_grad ? grad_grid(model, model->ev) : model->ev.grid_eval);
+        return with_grad ? launch_grad(ld, false) : launch_eval(ld, 0);
+    };
+    auto point_pass = [&]() -> cudaError_t {
+        LaunchArgs ln = args_for(model, model->mc, model->mc.part, nullptr, st,
+                                 with_grad ? grad_grid(model, model->mc) : model->mc.grid_eval);
+        return with_grad ? launch_grad(ln, true) : launch_eval(ln, 1);
+    };
+    if (mix) {
+        CK(point_pass());
         CK(mark());
-        LaunchArgs ln = args_for(model, model->mc, model->mc.part, nullptr, st, grad_grid(model, model->mc));
-        CK(launch_grad(ln, true));
+        CK(launch_mix_alpha(an, von, model->purity, model->d_md, model->d_status, st));
+        CK(data_pass());
         CK(mark());
-        if (partials)
-            CK(launch_partials(ad, an, model->d_slot_param, model->d_pscale, model->nslot,
-                               model->n_param, (double)model->ev.n, model->ev.lnpq,
-                               (double)model->mc.n, model->mc.volume, model->d_status, d_out, st));
-        else
-            CK(launch_finish(ad, an, model->d_slot_param, model->d_pscale, model->nslot,
-                             model->n_param, (double)model->ev.n, model->ev.lnpq,
-                             model->mc.volume / (double)model->mc.n, model->d_status, d_out, st));
     } else {
-        LaunchArgs ld = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
-        CK(launch_eval(ld, 0));
+        CK(data_pass());
         CK(mark());
-        LaunchArgs ln = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_eval);
-        CK(launch_eval(ln, 1));
+        CK(point_pass());
         CK(mark());
-        if (partials)
-            CK(launch_partials(ad, an, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
-                               model->ev.lnpq, (double)model->mc.n, model->mc.volume,
-                               model->d_status, d_out, st));
-        else
-            CK(launch_finish(ad, an, nullptr, model->d_pscale, 1, 0, (double)model->ev.n,
-                             model->ev.lnpq, model->mc.volume / (double)model->mc.n,
-                             model->d_status, d_out, st));
     }
+    const int *slots = with_grad ? model->d_slot_param : nullptr;
+    const int nsl = with_grad ? model->nslot : 1, npar = with_grad ? model->n_param : 0;
+    if (partials)
+        CK(launch_partials(ad, an, slots, model->d_pscale, nsl, npar, (double)model->ev.n, lnconst,
+                           (double)model->mc.n, model->mc.volume, model->d_status, d_out, st));
+    else
+        CK(launch_finish(ad, an, slots, model->d_pscale, nsl, npar, (double)model->ev.n, lnconst,
+                         von, model->d_status, d_out, st, ar));
     CK(mark());
     if (model->prof_on) model->prof_pending.push_back(marks);
     return AMP4D_OK;
@@ -463,6 +502,9 @@ ModelStatic make_static(const amp4d_model *mo)
     s.n_col = mo->n_col;
     s.n_float = mo->n_float;
     s.n_param = mo->n_param;
+    // Eq. 14: beta = (1 - P) / B, B = (V / n) sum w0 hb over the normalisation points
+    const double B = mo->mc.n > 0 ? mo->mc.volume / (double)mo->mc.n * mo->mc.whb : 0.0;
+    s.mix_beta = (mixing(mo) && B > 0.0) ? (1.0 - mo->purity) / B : 0.0;
     for (size_t i = 0; i < mo->internal.size(); ++i) {
         const int u = mo->internal[i];
         const amp4d_resonance &r = mo->res[u];
@@ -486,6 +528,112 @@ ModelStatic make_static(const amp4d_model *mo)
         }
     }
     return s;
+}
+
+// Eq. 14 templates over one loaded set: a data set gets eps and hb per event and
+// sum ln eps; a normalisation set gets the weight record w0 eps (w0 = the weights
+// as loaded, kept) and sum w0 hb.  Without templates the set is restored.
+amp4d_status apply_templates(amp4d_model *model, EventSet &s, bool is_norm, cudaStream_t st)
+{
+    if (s.n == 0) return AMP4D_OK;
+    const bool any = model->has_eff || model->has_bkg;
+    float *wrec = is_norm ? s.rec + (size_t)s.wrec * s.npad : nullptr;
+    const size_t bytes = (size_t)s.npad * sizeof(float);
+    if (!any) {
+        if (is_norm && s.w0) {
+            CK(cudaMemcpyAsync(wrec, s.w0, bytes, cudaMemcpyDeviceToDevice, st));
+            CK(cudaStreamSynchronize(st));
+            cudaFree(s.w0);
+            s.w0 = nullptr;
+            model->gram_valid = false;
+        }
+        for (float **b : {&s.eps, &s.hb})
+            if (*b) { cudaFree(*b); *b = nullptr; }
+        s.lneps = s.whb = 0.0;
+        return AMP4D_OK;
+    }
+    if (is_norm) {
+        if (!s.w0) {
+            CK(cudaMalloc(&s.w0, bytes));
+            CK(cudaMemcpyAsync(s.w0, wrec, bytes, cudaMemcpyDeviceToDevice, st));
+        }
+    } else {
+        if (!s.eps) CK(cudaMalloc(&s.eps, bytes));
+        if (!s.hb) CK(cudaMalloc(&s.hb, bytes));
+    }
+    TplArgs a{};
+    a.rec = s.rec;
+    a.npad = s.npad;
+    a.n = s.n;
+    a.eps = is_norm ? nullptr : s.eps;
+    a.hb = is_norm ? nullptr : s.hb;
+    a.w0 = is_norm ? s.w0 : nullptr;
+    a.wout = wrec;
+    for (int i = 0; i < 4; ++i) a.t[i] = model->tpl[i];
+    if (!model->has_eff) a.t[0].h = a.t[1].h = nullptr;
+    if (!model->has_bkg) a.t[2].h = a.t[3].h = nullptr;
+    a.mB = model->mass.mB; a.mpsi = model->mass.mpsi; a.mK = model->mass.mK; a.mpi = model->mass.mpi;
+    a.grid = (int)std::min<int64_t>((s.npad + prepare_block() - 1) / prepare_block(), model->nsm * 8);
+    amp4d_status rc = ensure_tmp(model, a.grid + 2);
+    if (rc) return rc;
+    a.part = model->d_tmp;
+    a.stream = st;
+    CK(launch_templates(a));
+    CK(launch_reduce_cols(model->d_tmp, a.grid, 1, model->d_tmp + a.grid, st));
+    double sum = 0.0;
+    CK(cudaMemcpyAsync(&sum, model->d_tmp + a.grid, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (is_norm) {
+        s.whb = sum;
+        model->gram_valid = false;
+    } else {
+        s.lneps = sum;
+    }
+    return AMP4D_OK;
+}
+
+// After a change of templates or sets: the static table (beta of Eq. 14) and a
+// full table build on the next evaluation.
+amp4d_status refresh_static(amp4d_model *model)
+{
+    ModelStatic ms = make_static(model);
+    CK(cudaMemcpy(model->d_static, &ms, sizeof ms, cudaMemcpyHostToDevice));
+    model->table_built = false;
+    return AMP4D_OK;
+}
+
+// Copy one template pair (mass, angle) into model slots t0, t0 + 1.
+amp4d_status set_template_pair(amp4d_model *model, int t0, const amp4d_hist2d *mass,
+                               const amp4d_hist2d *angle, cudaStream_t st)
+{
+    const amp4d_hist2d *src[2] = {mass, angle};
+    for (int j = 0; j < 2; ++j) {
+        const amp4d_hist2d *h = src[j];
+        if (!h->h || h->nx < 1 || h->ny < 1 || (int64_t)h->nx * h->ny > (1 << 26) ||
+            !(h->x_hi > h->x_lo) || !(h->y_hi > h->y_lo) || !std::isfinite(h->x_lo) ||
+            !std::isfinite(h->x_hi) || !std::isfinite(h->y_lo) || !std::isfinite(h->y_hi))
+            return fail(model, AMP4D_ERR_ARG, "bad template (null contents, bins or ranges)");
+    }
+    for (int j = 0; j < 2; ++j) {
+        const amp4d_hist2d *h = src[j];
+        const int t = t0 + j;
+        if (model->d_tpl[t]) { cudaFree(model->d_tpl[t]); model->d_tpl[t] = nullptr; }
+        const size_t bytes = (size_t)h->nx * h->ny * sizeof(float);
+        if (cudaMalloc(&model->d_tpl[t], bytes) != cudaSuccess)
+            return fail(model, AMP4D_ERR_OOM, "template allocation failed");
+        CK(cudaMemcpyAsync(model->d_tpl[t], h->h, bytes, cudaMemcpyDefault, st));
+        model->tpl[t] = TplDev{model->d_tpl[t], h->nx, h->ny, h->x_lo, h->x_hi, h->y_lo, h->y_hi};
+    }
+    CK(cudaStreamSynchronize(st));
+    return AMP4D_OK;
+}
+
+amp4d_status reapply_templates(amp4d_model *model, cudaStream_t st)
+{
+    amp4d_status rc = apply_templates(model, model->ev, false, st);
+    if (rc == AMP4D_OK) rc = apply_templates(model, model->mc, true, st);
+    if (rc == AMP4D_OK) rc = refresh_static(model);
+    return rc;
 }
 
 }  // namespace
@@ -572,7 +720,8 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
         e = cudaMemcpy(model->d_static, &ms, sizeof ms, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&model->d_slot_param, model->nslot * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&model->d_acc, 4 * model->nslot * sizeof(unsigned long long));
+    // [data, points][nslot][hi, lo], then the Eq. 14 signal-probability sum
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_acc, (4 * model->nslot + 2) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&model->h_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_status, sizeof(unsigned));
@@ -600,7 +749,11 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
         if (s->rec) cudaFree(s->rec);
         if (s->part) cudaFree(s->part);
         if (s->lcache) cudaFree(s->lcache);
+        for (float *b : {s->eps, s->hb, s->w0})
+            if (b) cudaFree(b);
     }
+    for (float *t : model->d_tpl)
+        if (t) cudaFree(t);
     if (model->d_md) cudaFree(model->d_md);
     if (model->d_static) cudaFree(model->d_static);
     if (model->d_params) cudaFree(model->d_params);
@@ -640,7 +793,39 @@ amp4d_status amp4d_set_events(amp4d_model *model, const float *m, const float *c
                               const float *cpsi, const float *phi, int64_t n, void *stream)
 {
     if (!model) return AMP4D_ERR_ARG;
-    return load_set(model, model->ev, m, cK, cpsi, phi, nullptr, n, false, (cudaStream_t)stream);
+    amp4d_status rc = load_set(model, model->ev, m, cK, cpsi, phi, nullptr, n, false, (cudaStream_t)stream);
+    if (rc == AMP4D_OK) rc = apply_templates(model, model->ev, false, (cudaStream_t)stream);
+    return rc;
+}
+
+amp4d_status amp4d_set_efficiency(amp4d_model *model, const amp4d_hist2d *mass,
+                                  const amp4d_hist2d *angle, void *stream)
+{
+    if (!model || (!mass) != (!angle)) return model ? fail(model, AMP4D_ERR_ARG, "give both templates or neither") : AMP4D_ERR_ARG;
+    CK(cudaSetDevice(model->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mass) {
+        amp4d_status rc = set_template_pair(model, 0, mass, angle, st);
+        if (rc) return rc;
+    }
+    model->has_eff = mass != nullptr;
+    return reapply_templates(model, st);
+}
+
+amp4d_status amp4d_set_background(amp4d_model *model, const amp4d_hist2d *mass,
+                                  const amp4d_hist2d *angle, double purity, void *stream)
+{
+    if (!model || (!mass) != (!angle)) return model ? fail(model, AMP4D_ERR_ARG, "give both templates or neither") : AMP4D_ERR_ARG;
+    if (mass && !(purity >= 0.0 && purity <= 1.0)) return fail(model, AMP4D_ERR_ARG, "purity must lie in [0, 1]");
+    CK(cudaSetDevice(model->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mass) {
+        amp4d_status rc = set_template_pair(model, 2, mass, angle, st);
+        if (rc) return rc;
+    }
+    model->has_bkg = mass != nullptr;
+    model->purity = mass ? purity : 1.0;
+    return reapply_templates(model, st);
 }
 
 amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const float *cK,
@@ -652,6 +837,8 @@ amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const flo
     model->gram_valid = false;
     amp4d_status rc = load_set(model, model->mc, m, cK, cpsi, phi, w, n, true, (cudaStream_t)stream);
     if (rc == AMP4D_OK) model->mc.volume = volume;
+    if (rc == AMP4D_OK) rc = apply_templates(model, model->mc, true, (cudaStream_t)stream);
+    if (rc == AMP4D_OK && model->has_bkg) rc = refresh_static(model);
     return rc;
 }
 
@@ -721,11 +908,16 @@ amp4d_status amp4d_eval_pdf(amp4d_model *model, const double *params, float *pdf
     cudaStream_t st = (cudaStream_t)stream;
     amp4d_status rc = run_eval(model, params, false, st);   // I over the current points
     if (rc) return rc;
-    const double I = model->h_out[3];
+    const double I = model->h_out[3];   // I_eps with an efficiency
     if (!(I > 0.0) || !std::isfinite(I)) return fail(model, AMP4D_ERR_DOMAIN, "I <= 0");
     rc = amp4d_eval_density(model, params, 0, pdf_out, stream);
     if (rc) return rc;
-    CK(launch_pdf_scale(model->ev.rec, model->ev.npad, model->ev.n, 1.0 / I, pdf_out, st));
+    const bool mix = mixing(model);
+    const double P = mix ? model->purity : 1.0;
+    const double B = model->mc.volume / (double)model->mc.n * model->mc.whb;
+    CK(launch_pdf_scale(model->ev.rec, model->ev.npad, model->ev.n, P / I,
+                        mix ? (1.0 - P) / B : 0.0, model->has_eff ? model->ev.eps : nullptr,
+                        mix ? model->ev.hb : nullptr, pdf_out, st));
     CK(cudaStreamSynchronize(st));
     return AMP4D_OK;
 }
@@ -777,6 +969,9 @@ amp4d_status amp4d_fit_fractions(amp4d_model *model, const double *params, doubl
 {
     if (!model || !params || !ff) return AMP4D_ERR_ARG;
     if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "set_norm_points must come first");
+    if (model->has_eff || model->has_bkg)
+        return fail(model, AMP4D_ERR_STATE,
+                    "fit fractions are defined on S: use a model without efficiency or background");
     // The Gram matrix at these masses and widths (fixed-mass models reuse it).
     if (model->n_float > 0 || !model->gram_valid) {
         const amp4d_status rc = amp4d_build_gram(model, params, stream);

@@ -76,6 +76,7 @@ struct ResStatic {
 
 struct ModelStatic {
     double mB, mpsi, mK, mpi;
+    double mix_beta;   // Eq. 14: (1 - P) / B with a background, else 0
     int n_res, n_col, n_float, n_param;
     ResStatic res[AMP4D_MAX_RES];
 };
@@ -100,6 +101,9 @@ struct ModelDev {
     // Where column k's coupling is copied: K* (t << 2 | slot) or Z (0x100 | z << 2 | slot).
     int col_dst[3 * AMP4D_MAX_RES];
     int static_bad;                // a fixed resonance has no valid pole constants
+    // Eq. 14 with a background: alpha = P / I_eps (written each evaluation once
+    // I_eps is known) and beta = (1 - P) / B, each hi + lo.
+    float mahi, malo, mbhi, mblo;
 };
 
 // ----------------------------------------------------------------------------

@@ -375,6 +375,35 @@ __device__ __forceinline__ void load_model(const ModelDev *g, ModelDev *s)
     __syncthreads();
 }
 
+// The per-event data term of -2 ln L.  Without a background: ln S, and the
+// adjoint scale 2/S.  With the Eq. 14 background (MIX): g = alpha eps S + beta hb
+// = f / (p q) with alpha = P / I_eps, ln g, the scale 2 alpha eps / g, and the
+// signal probability r = alpha eps S / g (its sum replaces N in dI/I).  ln is
+// taken as ln(mantissa) + exponent ln 2.  Returns false when the logged value is
+// not > 0 (a domain error).
+template <bool MIX>
+__device__ __forceinline__ bool data_term(const ModelDev &md, float S, const float *__restrict__ meps,
+                                          const float *__restrict__ mhb, int64_t e, Kahan &lsum,
+                                          int &esum, float &scale, float &r)
+{
+    float v = S, ae = 1.0f;
+    if constexpr (MIX) {
+        const float ep = __ldg(meps + e), hv = __ldg(mhb + e);
+        ae = fmaf(md.mahi, ep, md.malo * ep);
+        v = fmaf(ae, S, fmaf(md.mbhi, hv, md.mblo * hv));
+    }
+    if (!(v > 0.0f)) return false;
+    int ex;
+    float mant = frexpf(v, &ex);
+    if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
+    lsum.add(logf(mant));
+    esum += ex;
+    const float iv = __frcp_rn(v);
+    scale = 2.0f * ae * iv;
+    if constexpr (MIX) r = ae * S * iv;
+    return true;
+}
+
 // MODE_SUM_LNS: data sum of ln S; MODE_SUM_WS: normalisation sum of w S;
 // MODE_WRITE: S per event to out.
 enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
@@ -388,12 +417,14 @@ __device__ __forceinline__ constexpr bool record_used(int k)
                     (!ZF && (k == REC_MZ || k == REC_PZ || k == REC_QZ)));
 }
 
-template <int NK, int NZ, int MODE, int BLOCK, bool FX>
+template <int NK, int NZ, int MODE, int BLOCK, bool FX, bool MIX = false>
 __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, int64_t npad,
                                                 int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                 unsigned long long *__restrict__ acc, float *__restrict__ S_out,
                                                 unsigned *__restrict__ status,
-                                                const float2 *__restrict__ lc)
+                                                const float2 *__restrict__ lc,
+                                                const float *__restrict__ meps = nullptr,
+                                                const float *__restrict__ mhb = nullptr)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     const ModelDev &md = c_md;   // gmd is its source (copied by with_const_table)
@@ -410,12 +441,8 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
         EvState<NK, NZ> ev;
         eval_event<NK, NZ, FX>(md, v, ev, lc, npad, e);
         if (MODE == MODE_SUM_LNS) {
-            if (!(ev.S > 0.0f)) { bad = true; continue; }
-            int ex;
-            float mant = frexpf(ev.S, &ex);
-            if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
-            ksum.add(logf(mant));
-            esum += ex;
+            float scale, r;
+            if (!data_term<MIX>(md, ev.S, meps, mhb, e, ksum, esum, scale, r)) { bad = true; continue; }
         } else if (MODE == MODE_SUM_WS) {
             ksum.add(__ldg(rec + wrec * npad + e) * ev.S);
         } else {
@@ -501,12 +528,15 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // e + stride, ... (each load of a warp stays coalesced).  The constants of a
 // resonance and each gradient slot pair are read once for the NE events.  An
 // event index beyond n repeats a valid event with zero weight.
-template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, bool ZF>
+template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, bool ZF, bool MIX = false>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
                                                          unsigned long long *__restrict__ acc,
                                                          unsigned *__restrict__ status,
-                                                         const float2 *__restrict__ lc, int nslot)
+                                                         const float2 *__restrict__ lc, int nslot,
+                                                         const float *__restrict__ meps,
+                                                         const float *__restrict__ mhb,
+                                                         unsigned long long *__restrict__ acc_r)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     const ModelDev &md = c_md;
@@ -516,7 +546,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     const int npair = (nslot - 1) >> 1;
     for (int i = 0; i < npair; ++i) gsl[i * BLOCK + tid] = make_float2(0.f, 0.f);
     float2 *g = gsl + tid;
-    Kahan acc0;
+    Kahan acc0, rsum;
     int esum = 0;
     bool bad = false;
     const int nK = md.n_res - NZ;
@@ -542,15 +572,12 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             float scale = 0.f;
             if (valid[j]) {
                 if (!NORM) {
-                    if (!(ev[j].S > 0.0f)) {
+                    float r = 0.f;
+                    if (!data_term<MIX>(md, ev[j].S, meps, mhb, e[j], acc0, esum, scale, r)) {
                         bad = true;
-                    } else {
-                        int ex;
-                        float mant = frexpf(ev[j].S, &ex);
-                        if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
-                        acc0.add(logf(mant));
-                        esum += ex;
-                        scale = 2.0f * __frcp_rn(ev[j].S);
+                        scale = 0.f;
+                    } else if constexpr (MIX) {
+                        rsum.add(r);
                     }
                 } else {
                     const float w = __ldg(rec + wrec * npad + e[j]);
@@ -633,6 +660,10 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
         }
     }
     grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, acc, nslot);
+    if constexpr (MIX) {
+        __syncthreads();
+        block_accumulate<BLOCK>(rsum.value(), red, acc_r, status);
+    }
 }
 
 // Per-thread gradient accumulators live in shared memory, which keeps the
@@ -641,12 +672,15 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 // is one float2 at p * BLOCK + t, so each update is one 64-bit load and store
 // and a warp's accesses cover every bank twice (two wavefronts, no conflict).
 // Events are read one per iteration with coalesced scalar loads.
-template <int NK, int NZ, bool NORM, int BLOCK>
+template <int NK, int NZ, bool NORM, int BLOCK, bool MIX = false>
 __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *__restrict__ rec, int64_t npad,
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                    unsigned long long *__restrict__ acc,
                                                    unsigned *__restrict__ status,
-                                                   const float2 *__restrict__ lc, int nslot)
+                                                   const float2 *__restrict__ lc, int nslot,
+                                                   const float *__restrict__ meps,
+                                                   const float *__restrict__ mhb,
+                                                   unsigned long long *__restrict__ acc_r)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     const ModelDev &md = c_md;   // gmd is its source (copied by with_const_table)
@@ -656,7 +690,7 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
     const int npair = (nslot - 1) >> 1;
     for (int i = 0; i < npair; ++i) gsl[i * BLOCK + tid] = make_float2(0.f, 0.f);
     float2 *g = gsl + tid;           // g[p * BLOCK] = slot pair p of this thread
-    Kahan acc0;
+    Kahan acc0, rsum;
     int esum = 0;
     bool bad = false;
     const int nK = md.n_res - NZ;
@@ -668,13 +702,9 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
         eval_event<NK, NZ>(md, v, ev, lc, npad, e);
         float scale;
         if (!NORM) {
-            if (!(ev.S > 0.0f)) { bad = true; continue; }
-            int ex;
-            float mant = frexpf(ev.S, &ex);
-            if (mant < 0.70710678f) { mant *= 2.0f; ex -= 1; }
-            acc0.add(logf(mant));
-            esum += ex;
-            scale = 2.0f * __frcp_rn(ev.S);
+            float r = 0.f;
+            if (!data_term<MIX>(md, ev.S, meps, mhb, e, acc0, esum, scale, r)) { bad = true; continue; }
+            if constexpr (MIX) rsum.add(r);
         } else {
             const float w = __ldg(rec + wrec * npad + e);
             acc0.add(w * ev.S);
@@ -759,6 +789,10 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
         }
     }
     grad_block_tail<NORM, BLOCK>(acc0, esum, bad, status, red, gsl, acc, nslot);
+    if constexpr (MIX) {
+        __syncthreads();
+        block_accumulate<BLOCK>(rsum.value(), red, acc_r, status);
+    }
 }
 
 constexpr int EVAL_BLOCK = 256;
@@ -770,8 +804,13 @@ cudaError_t launch_eval_fx(const LaunchArgs &a, int mode)
     return with_const_table(a.md, a.stream, [&]() {
         switch (mode) {
         case MODE_SUM_LNS:
-            k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
+            if (a.mix_eps)
+                k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX, true><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                    a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache, a.mix_eps,
+                    a.mix_hb);
+            else
+                k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                    a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
             break;
         case MODE_SUM_WS:
             k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
@@ -797,28 +836,39 @@ template <int NK, int NZ, bool NORM, bool FX>
 cudaError_t launch_grad_k(const LaunchArgs &a)
 {
     const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
+    constexpr int EPT = GRAD_EVENTS_PER_THREAD_CACHED, CPS = GRAD_CTAS_PER_SM_CACHED;
+    const bool mix = !NORM && a.mix_eps != nullptr;
     if constexpr (FX) {
-        auto kern = a.z_float
-                        ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, GRAD_EVENTS_PER_THREAD_CACHED, GRAD_CTAS_PER_SM_CACHED, true>
-                        : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, GRAD_EVENTS_PER_THREAD_CACHED, GRAD_CTAS_PER_SM_CACHED, false>;
+        auto kern = a.z_float ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, true>
+                              : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, false>;
+        if constexpr (!NORM) {
+            if (mix)
+                kern = a.z_float ? k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, true>
+                                 : k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, true>;
+        }
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
         return with_const_table(a.md, a.stream, [&]() {
             kern<<<a.grid, GRAD_BLOCK, smem, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.acc, a.status,
-                                                         a.lcache, a.nslot);
+                                                         a.lcache, a.nslot, a.mix_eps, a.mix_hb,
+                                                         a.acc_r);
             return cudaGetLastError();
         });
     } else {
+        auto kern = k_grad<NK, NZ, NORM, GRAD_BLOCK>;
+        if constexpr (!NORM) {
+            if (mix) kern = k_grad<NK, NZ, false, GRAD_BLOCK, true>;
+        }
         if (smem > 48 * 1024) {   // above the default dynamic shared-memory limit
-            cudaError_t e = cudaFuncSetAttribute(k_grad<NK, NZ, NORM, GRAD_BLOCK>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
         return with_const_table(a.md, a.stream, [&]() {
-            k_grad<NK, NZ, NORM, GRAD_BLOCK><<<a.grid, GRAD_BLOCK, smem, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.status, a.lcache, a.nslot);
+            kern<<<a.grid, GRAD_BLOCK, smem, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.md, a.acc,
+                                                         a.status, a.lcache, a.nslot, a.mix_eps,
+                                                         a.mix_hb, a.acc_r);
             return cudaGetLastError();
         });
     }

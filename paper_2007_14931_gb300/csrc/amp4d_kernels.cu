@@ -49,16 +49,21 @@ __global__ void k_reduce_cols(const double *__restrict__ part, int nblk, int nco
 // out: [0] nll, [1] sum ln S, [2] sum ln pq, [3] I, [4] N, [5] status bits
 // (1: domain, 2: invalid parameters), [6..] grad.
 // ---------------------------------------------------------------------------
+// With the Eq. 14 background (ar non-null) the data sum is already sum ln(f / (p q))
+// and the signal probabilities' sum R = acc(ar) replaces N:
+// NLL = -2 [ sum ln g + sum ln(pq) ], dNLL = -2 [ sum d(ln g) - R dI / I ].
 __global__ void k_finish(const unsigned long long *__restrict__ ad, const unsigned long long *__restrict__ an,
                          const int *__restrict__ slot_param, const double *__restrict__ pscale,
                          int nslot, int nparam,
                          double n_events, double lnpq, double vol_over_n,
-                         const unsigned *__restrict__ status, double *__restrict__ out)
+                         const unsigned *__restrict__ status, double *__restrict__ out,
+                         const unsigned long long *__restrict__ ar)
 {
     const double rd0 = acc128_value(ad), rn0 = acc128_value(an);
     const double I = vol_over_n * rn0;
     unsigned st = *status;
-    const double nll = -2.0 * (rd0 + lnpq - n_events * log(I));
+    const double nll = ar ? -2.0 * (rd0 + lnpq) : -2.0 * (rd0 + lnpq - n_events * log(I));
+    const double nI = ar ? acc128_value(ar) : n_events;   // coefficient of dI / I
     if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
     const bool bad = st != 0u;
     if (threadIdx.x == 0) {
@@ -77,8 +82,25 @@ __global__ void k_finish(const unsigned long long *__restrict__ ad, const unsign
         if (p >= 0)
             out[6 + p] = bad ? 0.0
                              : -2.0 * pscale[p] *
-                                   (acc128_value(ad + 2 * s) - n_events * vol_over_n * acc128_value(an + 2 * s) / I);
+                                   (acc128_value(ad + 2 * s) - nI * vol_over_n * acc128_value(an + 2 * s) / I);
     }
+}
+
+// Eq. 14 with a background: alpha = P / I_eps from the point sum of the pass that
+// ran first, into the device table (its hi + lo pair).
+__device__ __forceinline__ void store_alpha(ModelDev *md, double I, double purity, unsigned *status)
+{
+    double a = 0.0;
+    if (I > 0.0 && isfinite(I)) a = purity / I;
+    else atomicOr(status, 1u);
+    md->mahi = (float)a;
+    md->malo = (float)(a - (double)md->mahi);
+}
+
+__global__ void k_mix_alpha(const unsigned long long *__restrict__ an, double vol_over_n,
+                            double purity, ModelDev *__restrict__ md, unsigned *__restrict__ status)
+{
+    if (threadIdx.x == 0) store_alpha(md, vol_over_n * acc128_value(an), purity, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -126,7 +148,8 @@ __global__ void __launch_bounds__(256) k_finish_gram(
     const double *__restrict__ pscale, int nslot, int ncol, int nparam, double n_events,
     double lnpq, double vol_over_n, const double *__restrict__ params, const double *__restrict__ G,
     const unsigned *__restrict__ status, double *__restrict__ out, int with_grad, double n_points,
-    int partials)
+    int partials, const unsigned long long *__restrict__ ar, ModelDev *__restrict__ alpha_md,
+    double purity)
 {
     extern __shared__ double sG[];   // dim x dim, staged once with independent loads
     __shared__ double u[96], v[96], Gu[96], Gv[96];
@@ -167,6 +190,10 @@ __global__ void __launch_bounds__(256) k_finish_gram(
     }
     __syncthreads();
     const double q = qsh;
+    if (alpha_md) {   // Eq. 14 with a background: only alpha = P / I_eps, before the data pass
+        if (t == 0) store_alpha(alpha_md, vol_over_n * q, purity, const_cast<unsigned *>(status));
+        return;
+    }
     if (partials) {
         // Shard partials (layout of k_partials) with T = V (u^T G u + v^T G v).
         const double volume = vol_over_n * n_points;
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(256) k_finish_gram(
         const double I = vol_over_n * q;
         unsigned st = *status;
         const double rd0 = acc128_value(ad);
-        const double nll = -2.0 * (rd0 + lnpq - n_events * log(I));
+        const double nll = ar ? -2.0 * (rd0 + lnpq) : -2.0 * (rd0 + lnpq - n_events * log(I));
         if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
         out[0] = st ? INFINITY : nll;
         out[1] = rd0;
@@ -211,6 +238,7 @@ __global__ void __launch_bounds__(256) k_finish_gram(
     if (!with_grad) return;
     __syncthreads();
     const double Iv = Ish;
+    const double nI = ar ? acc128_value(ar) : n_events;   // coefficient of dI / I
     for (int p = t; p < nparam; p += blockDim.x) out[6 + p] = 0.0;
     __syncthreads();
     for (int s = 1 + t; s < nslot; s += blockDim.x) {
@@ -218,7 +246,7 @@ __global__ void __launch_bounds__(256) k_finish_gram(
         if (p < 0 || p >= dim || Iv == 0.0) continue;
         const int k = p >> 1;
         const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1]) : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
-        out[6 + p] = -2.0 * pscale[p] * (acc128_value(ad + 2 * s) - n_events * vol_over_n * dq / Iv);
+        out[6 + p] = -2.0 * pscale[p] * (acc128_value(ad + 2 * s) - nI * vol_over_n * dq / Iv);
     }
 }
 
@@ -434,6 +462,9 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         md->n_col = ncol;
         md->n_float = st->n_float;
         md->n_param = npar;
+        md->mahi = md->malo = 0.f;   // alpha: written once I_eps is known
+        md->mbhi = (float)st->mix_beta;
+        md->mblo = (float)(st->mix_beta - (double)md->mbhi);
     }
     __syncthreads();
     if (t == 0) {
@@ -535,19 +566,26 @@ cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc)
 
 // PDF of Eq. 5 with the phase-space density: P(e) = S(e) p(e) q(e) / I, in
 // place over S (FP32, n events).
-__global__ void k_pdf_scale(const float *__restrict__ rec, int64_t npad, int64_t n, float inv_I,
+// PDF per data event from S: p q [alpha eps S + beta hb] (Eq. 14; alpha = P / I,
+// eps = 1 and beta = 0 without templates), in FP64 and rounded once.
+__global__ void k_pdf_scale(const float *__restrict__ rec, int64_t npad, int64_t n, double alpha,
+                            double beta, const float *__restrict__ eps, const float *__restrict__ hb,
                             float *__restrict__ S)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x)
-        S[e] = S[e] * rec[REC_P * npad + e] * rec[REC_Q * npad + e] * inv_I;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double g = alpha * (eps ? (double)eps[e] : 1.0) * (double)S[e];
+        if (hb) g += beta * (double)hb[e];
+        S[e] = (float)((double)rec[REC_P * npad + e] * (double)rec[REC_Q * npad + e] * g);
+    }
 }
 
-cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double inv_I, float *S,
-                             cudaStream_t s)
+cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double alpha, double beta,
+                             const float *eps, const float *hb, float *S, cudaStream_t s)
 {
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
-    k_pdf_scale<<<(int)std::max<int64_t>(1, blocks), 256, 0, s>>>(rec, npad, n, (float)inv_I, S);
+    k_pdf_scale<<<(int)std::max<int64_t>(1, blocks), 256, 0, s>>>(rec, npad, n, alpha, beta, eps,
+                                                                    hb, S);
     return cudaGetLastError();
 }
 
@@ -561,10 +599,17 @@ cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *o
 cudaError_t launch_finish(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                           const double *pscale, int nslot, int nparam, double n_events,
                           double lnpq, double vol_over_n, const unsigned *status, double *out,
-                          cudaStream_t s)
+                          cudaStream_t s, const unsigned long long *ar)
 {
     k_finish<<<1, 128, 0, s>>>(ad, an, slot_param, pscale, nslot, nparam, n_events, lnpq,
-                               vol_over_n, status, out);
+                               vol_over_n, status, out, ar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mix_alpha(const unsigned long long *an, double vol_over_n, double purity,
+                             ModelDev *md, unsigned *status, cudaStream_t s)
+{
+    k_mix_alpha<<<1, 32, 0, s>>>(an, vol_over_n, purity, md, status);
     return cudaGetLastError();
 }
 
@@ -572,7 +617,8 @@ cudaError_t launch_finish_gram(const unsigned long long *ad, const int *slot_par
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
                                const unsigned *status, double *out, int with_grad, cudaStream_t s,
-                               double n_points, int partials)
+                               double n_points, int partials, const unsigned long long *ar,
+                               ModelDev *alpha_md, double purity)
 {
     const size_t smem = (size_t)4 * ncol * ncol * sizeof(double);   // dim x dim
     if (smem > 48 * 1024) {
@@ -582,7 +628,7 @@ cudaError_t launch_finish_gram(const unsigned long long *ad, const int *slot_par
     }
     k_finish_gram<<<1, 256, smem, s>>>(ad, slot_param, pscale, nslot, ncol, nparam, n_events, lnpq,
                                        vol_over_n, params, G, status, out, with_grad, n_points,
-                                       partials);
+                                       partials, ar, alpha_md, purity);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,10 @@ struct LaunchArgs {
     bool all_fixed = false;          // no mass or width floats (with lcache: all lineshapes cached)
     bool kstar_fixed = false;        // no K* mass or width floats (with lcache: K* lineshapes cached)
     bool z_float = false;            // some Z mass and width float
+    // Eq. 14 with a background (data sets): eps and hb per event, and the
+    // accumulator of the signal probabilities r = alpha eps S / g.
+    const float *mix_eps = nullptr, *mix_hb = nullptr;
+    unsigned long long *acc_r = nullptr;
 };
 
 // Resident CTAs per SM of the adjoint kernels (their __launch_bounds__).  The
@@ -49,12 +53,16 @@ cudaError_t launch_grad(const LaunchArgs &a, bool norm);
 cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc);
 cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *out,
                                cudaStream_t s);
-cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double inv_I, float *S,
-                             cudaStream_t s);
+cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double alpha, double beta,
+                             const float *eps, const float *hb, float *S, cudaStream_t s);
 cudaError_t launch_finish(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                           const double *pscale, int nslot, int nparam, double n_events,
                           double lnpq, double vol_over_n, const unsigned *status, double *out,
-                          cudaStream_t s);
+                          cudaStream_t s, const unsigned long long *ar = nullptr);
+// Eq. 14 with a background: alpha = P / I_eps into the device table, I_eps =
+// vol_over_n times the point sum in an.
+cudaError_t launch_mix_alpha(const unsigned long long *an, double vol_over_n, double purity,
+                             ModelDev *md, unsigned *status, cudaStream_t s);
 
 // couplings_only: refresh the folded couplings of a table whose masses and
 // widths are all fixed and which has had one full build.
@@ -67,7 +75,9 @@ cudaError_t launch_finish_gram(const unsigned long long *ad, const int *slot_par
                                int nslot, int ncol, int nparam, double n_events, double lnpq,
                                double vol_over_n, const double *params, const double *G,
                                const unsigned *status, double *out, int with_grad, cudaStream_t s,
-                               double n_points = 0.0, int partials = 0);
+                               double n_points = 0.0, int partials = 0,
+                               const unsigned long long *ar = nullptr, ModelDev *alpha_md = nullptr,
+                               double purity = 1.0);
 cudaError_t launch_partials(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,
                             const double *pscale, int nslot, int nparam, double n_events,
                             double lnpq, double n_points, double volume, const unsigned *status,
@@ -144,5 +154,27 @@ struct PrepArgs {
 };
 cudaError_t launch_prepare(const PrepArgs &a);
 int prepare_block();
+
+// Eq. 14 templates of one set (k_templates): per point eps and hb, or for a
+// normalisation set the weight record rewritten as w0 eps; per-block FP64
+// partials of sum ln eps (data) or sum w0 hb (points).
+struct TplDev {
+    const float *h;   // nullptr: unset
+    int nx, ny;
+    double xlo, xhi, ylo, yhi;
+};
+struct TplArgs {
+    const float *rec;
+    int64_t npad, n;
+    float *eps, *hb;          // data sets: per-event outputs (npad values each)
+    const float *w0;          // normalisation sets: weights as loaded
+    float *wout;              // normalisation sets: the weight record to rewrite
+    TplDev t[4];              // efficiency x masses, x angles; background x masses, x angles
+    double mB, mpsi, mK, mpi;
+    double *part;             // per-block partials (grid values)
+    int grid;
+    cudaStream_t stream;
+};
+cudaError_t launch_templates(const TplArgs &a);
 
 }  // namespace amp4d

@@ -159,6 +159,69 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_prepare(PrepArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Eq. 14 templates.  Per point, in FP64: x = m^2 and y = m^2_psipi, the latter in
+// the K pi frame, where the J/psi has momentum p* = p m_B / m along the K pi
+// flight axis and the pi momentum q at angle theta_K* to it:
+//   m^2_psipi = m_psi^2 + m_pi^2 + 2 (E_psi E_pi - p* q cos theta_K*).
+// eps = effM(x, y) effA(cos theta_psi, phi) (1 without an efficiency) and
+// hb = bkgM(x, y) bkgA(cos theta_psi, phi) (0 without a background), each
+// template read at the bin holding the point.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double tpl_read(const TplDev &t, double x, double y)
+{
+    if (!(x >= t.xlo && x <= t.xhi && y >= t.ylo && y <= t.yhi)) return 0.0;
+    int ix = (int)floor((x - t.xlo) * t.nx / (t.xhi - t.xlo));
+    int iy = (int)floor((y - t.ylo) * t.ny / (t.yhi - t.ylo));
+    ix = ix < t.nx ? ix : t.nx - 1;
+    iy = iy < t.ny ? iy : t.ny - 1;
+    return (double)t.h[(int64_t)iy * t.nx + ix];
+}
+
+__global__ void __launch_bounds__(PREP_BLOCK) k_templates(TplArgs a)
+{
+    __shared__ double red[PREP_BLOCK / 32];
+    double part = 0.0;
+    const int64_t np = a.npad;
+    for (int64_t e = blockIdx.x * (int64_t)PREP_BLOCK + threadIdx.x; e < np;
+         e += (int64_t)gridDim.x * PREP_BLOCK) {
+        const double m = a.rec[REC_M * np + e], cK = a.rec[REC_CK * np + e];
+        const double cpsi = a.rec[REC_CPSI * np + e], phi = a.rec[REC_PHI * np + e];
+        const double p = two_body(a.mB, m, a.mpsi), q = two_body(m, a.mK, a.mpi);
+        const double ps = p * a.mB / m;
+        const double Epsi = sqrt(a.mpsi * a.mpsi + ps * ps), Epi = sqrt(a.mpi * a.mpi + q * q);
+        const double x = m * m;
+        const double y = a.mpsi * a.mpsi + a.mpi * a.mpi + 2.0 * (Epsi * Epi - ps * q * cK);
+        const double eps = a.t[0].h ? tpl_read(a.t[0], x, y) * tpl_read(a.t[1], cpsi, phi) : 1.0;
+        const double hb = a.t[2].h ? tpl_read(a.t[2], x, y) * tpl_read(a.t[3], cpsi, phi) : 0.0;
+        const bool real = e < a.n;
+        if (a.wout) {
+            const double w0 = a.w0[e];
+            a.wout[e] = (float)(w0 * eps);
+            if (real) part += w0 * hb;
+        } else {
+            a.eps[e] = (float)eps;
+            a.hb[e] = (float)hb;
+            if (real) part += log(eps);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < PREP_BLOCK / 32; ++i) t += red[i];
+        a.part[blockIdx.x] = t;
+    }
+}
+
+cudaError_t launch_templates(const TplArgs &a)
+{
+    k_templates<<<a.grid, PREP_BLOCK, 0, a.stream>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prepare(const PrepArgs &a)
 {
     if (a.has_z)

@@ -62,7 +62,7 @@ def test_binding_records_match_header_layout(tmp_path):
         pytest.skip("no gcc")
     import paper_2007_14931_gb300 as A
     recs = {"amp4d_resonance": A.amp4d_resonance, "amp4d_particle_masses": A.amp4d_particle_masses,
-            "amp4d_mlp_cfg": A.amp4d_mlp_cfg}
+            "amp4d_mlp_cfg": A.amp4d_mlp_cfg, "amp4d_hist2d": A.amp4d_hist2d}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "amp4d.h"', "int main(void) {"]
     for name, cls in recs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

@@ -396,6 +396,39 @@ def test_eq14_pdf_integrates_to_one():
     assert abs(est - 1.0) < 4 * sem + 0.0
 
 
+def test_eq14_mean_signal_probability_is_the_purity():
+    """For events drawn from f, the signal probability r = P eps S p q / (I_eps f)
+    has mean P: signal events thinned by the efficiency and background events
+    drawn from p q hb, mixed P : 1 - P, give sum r / N = P within its binomial-like
+    spread (a wrong mixing weight or normalisation moves it)."""
+    cfg = W.CONFIGS["kstar10"]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    mo = O.Model(res)
+    em, ea, bm, ba, P = W.eq14_templates(7)
+    mo.set_template(0, em, ea)
+    mo.set_template(1, bm, ba, purity=P)
+    rng = np.random.default_rng(8)
+    n = 8000
+    n_sig = int(round(P * n))
+    sig, _, _ = mo.generate(p, 3 * n_sig, 9)
+    eps, _, _ = mo.templates(sig)
+    keep = rng.uniform(size=len(eps)) < eps
+    sig = [np.asarray(a)[keep][:n_sig] for a in sig]
+    u = W.uniform_points(60 * (n - n_sig), 10, box=(W.M_LO, W.M_END - 1e-6))
+    _, pq = mo.density(p, u)
+    _, hb, _ = mo.templates(u)
+    w = pq * hb
+    keep = rng.uniform(size=len(w)) * w.max() < w
+    bkg = [np.asarray(a)[keep][:n - n_sig] for a in u]
+    ev = [np.concatenate([a, b]) for a, b in zip(sig, bkg)]
+    assert len(ev[0]) == n
+    _, _, aux, rc = mo.nll_eq14(p, ev, W.uniform_points(200_000, 11))
+    assert rc == 0
+    # r lies in [0, 1]: its spread is at most 1/2 per event
+    assert abs(aux[4] / n - P) < 4 * 0.5 / math.sqrt(n)
+
+
 def test_eq14_gradient_matches_central_differences():
     res, p, ev, nm = _eq14_case("kstar10_z", 400, 800)
     cfg = W.CONFIGS["kstar10_z"]
