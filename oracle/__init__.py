@@ -66,8 +66,9 @@ def lib():
             L.or_nll.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d, _d,
                                  C.c_int64, C.c_double, _d, _d, _d]
             L.or_gram.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, _d, C.c_int64, _d]
-            L.or_nll_eq14.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d, _d,
-                                      _d, C.c_int64, C.c_double, _d, _d, _d]
+            L.or_nll_eq14.argtypes = [C.c_void_p, _d, _d, _d, _d, _d, _d, C.c_int64, _d, _d, _d,
+                                      _d, _d, C.c_int64, C.c_double, _d, _d, _d]
+            L.or_model_set_mistag.argtypes = [C.c_void_p, C.c_double]
             L.or_model_set_template.argtypes = [C.c_void_p, C.c_int, _d, C.c_int, C.c_int, _d,
                                                 _d, C.c_int, C.c_int, _d, C.c_double]
             L.or_tpl_value.restype = C.c_double
@@ -298,19 +299,26 @@ class Model:
         lib().or_templates(self.h, _pd(m), _pd(cK), _pd(cpsi), _pd(phi), len(m), _pd(out))
         return out[:, 0], out[:, 1], out[:, 2]
 
-    def nll_eq14(self, params, events, norm_pts, w=None, volume=None, grad=False):
+    def set_mistag(self, w):
+        if lib().or_model_set_mistag(self.h, float(w)) != 0:
+            raise ValueError("oracle: mistag must lie in [0, 0.5]")
+
+    def nll_eq14(self, params, events, norm_pts, w=None, volume=None, grad=False, tag=None):
         """Eq. 14: (-2 ln L, gradient or None, aux, status); aux = [sum ln(f/pq),
-        sum ln pq, I_eps, B, sum of signal probabilities]."""
+        sum ln pq, I_eps, B, sum of signal probabilities].  tag: +1 (B0) / -1
+        (B0bar) per event, None for all B0."""
         import workloads as W
         volume = W.BOX_VOLUME if volume is None else volume
         ev = [_f64(a) for a in events]
+        tg = _f64(tag) if tag is not None else None
         nm = [_f64(a) for a in norm_pts]
         wf = _f64(w) if w is not None else None
         out = C.c_double()
         g = np.zeros(self.n_params) if grad else None
         aux = np.zeros(5)
         pr = _f64(params)
-        rc = lib().or_nll_eq14(self.h, _pd(pr), *(_pd(a) for a in ev), len(ev[0]),
+        rc = lib().or_nll_eq14(self.h, _pd(pr), *(_pd(a) for a in ev),
+                               _pd(tg) if tg is not None else None, len(ev[0]),
                                *(_pd(a) for a in nm), _pd(wf) if wf is not None else None,
                                len(nm[0]), float(volume), C.byref(out), _pd(g) if grad else None,
                                _pd(aux))

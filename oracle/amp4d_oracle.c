@@ -15,6 +15,7 @@
  *   - LASS K pi S-wave: effective-range term + K0*(1430) Breit-Wigner   Eq. 7, Eq. 8, Eq. 9
  *   - Z -> J/psi pi amplitude with Z-frame angles and alignment alpha  Eq. 10
  *   - efficiency x signal + background with a fixed purity             Eq. 14
+ *   - B0bar events (phi -> -phi) and flavour mistag                    Eq. 12 text
  *   - parity relation of the Z helicity couplings                      Eq. 11
  *   - unbinned -2 ln L with a numerical (MC) normalisation             Introduction,
  *                                                                     State of the art
@@ -52,6 +53,12 @@
  *     normalisation points with their weights.  S is normalised with the
  *     efficiency-weighted points.  The purity P is fixed.
  *
+ *   - Flavour: the signal density of a B0bar-tagged event is S at -phi (the
+ *     charge-conjugate mode differs only in the sign of phi); with a mistag
+ *     fraction w an event tagged t has density (1 - w) S(t phi) + w S(-t phi).
+ *     The box is symmetric in phi and p q does not depend on phi, so with a
+ *     phi-even efficiency every tag has the normalisation I_eps.
+ *
  * Parameters of a model: [Re c_k, Im c_k] per basis column k, then [M_R, G_R]
  * for every resonance flagged as floating, in resonance order.
  */
@@ -85,6 +92,7 @@ typedef struct {
     struct { double *h; int nx, ny; double xlo, xhi, ylo, yhi; } tpl[4];
     int has_eff, has_bkg;
     double purity;
+    double mistag;   /* flavour mistag fraction w */
     double lass_a[OR_MAXR], lass_b[OR_MAXR], lass_R[OR_MAXR]; /* Eq. 7-8 constants */
     int col_res[OR_MAXC], col_lam[OR_MAXC];
     int has_z;
@@ -886,6 +894,14 @@ int or_model_set_template(or_model *mo, int which, const double *hm, int nxm, in
     return 0;
 }
 
+/* Flavour mistag fraction w in [0, 0.5] (Eq. 12 text).  Returns 0, or -1. */
+int or_model_set_mistag(or_model *mo, double w)
+{
+    if (!(w >= 0.0 && w <= 0.5)) return -1;
+    mo->mistag = w;
+    return 0;
+}
+
 static double tpl_at(const or_model *mo, int t, double x, double y)
 {
     return tpl_value(mo->tpl[t].h, mo->tpl[t].nx, mo->tpl[t].ny, mo->tpl[t].xlo, mo->tpl[t].xhi,
@@ -920,6 +936,8 @@ void or_templates(const or_model *mo, const double *m, const double *cK, const d
 /*
  * -2 ln L of Eq. 14.  Per event the PDF in (m, cK, cpsi, phi) is
  *   f = p q [ P eps S / I_eps + (1 - P) hb / B ],
+ * with S the flavour-tagged density (1 - w) S(t phi) + w S(-t phi) for tag t
+ * (tag NULL: every event B0),
  *   I_eps = (V / N_mc) sum_n w_n eps_n S_n,   B = (V / N_mc) sum_n w_n hb_n,
  * over the normalisation points (w = p q when nw is NULL); without a background
  * P = 1.  NLL = -2 sum_e ln f_e and
@@ -929,9 +947,10 @@ void or_templates(const or_model *mo, const double *m, const double *cK, const d
  * Returns -1 (NLL = +inf) if some f_e <= 0, p q <= 0 or I_eps <= 0.
  */
 int or_nll_eq14(const or_model *mo, const double *params, const double *m, const double *cK,
-                const double *cpsi, const double *phi, int64_t n, const double *nm,
-                const double *ncK, const double *ncpsi, const double *nphi, const double *nw,
-                int64_t n_mc, double volume, double *nll, double *grad, double *aux)
+                const double *cpsi, const double *phi, const double *tag, int64_t n,
+                const double *nm, const double *ncK, const double *ncpsi, const double *nphi,
+                const double *nw, int64_t n_mc, double volume, double *nll, double *grad,
+                double *aux)
 {
     const int NP = or_num_params(mo);
     const double P = mo->has_bkg ? mo->purity : 1.0;
@@ -974,12 +993,21 @@ int or_nll_eq14(const or_model *mo, const double *params, const double *m, const
         nsum sl = {0, 0}, spq = {0, 0}, sr = {0, 0};
         nsum sg[2 * OR_MAXC + 2 * OR_MAXR];
         memset(sg, 0, sizeof(sg));
-        double dS[2 * OR_MAXC + 2 * OR_MAXR];
+        double dS[2 * OR_MAXC + 2 * OR_MAXR], dSb[2 * OR_MAXC + 2 * OR_MAXR];
         int64_t e1 = (b + 1) * OR_BLOCK < n ? (b + 1) * OR_BLOCK : n;
         for (int64_t e = b * OR_BLOCK; e < e1; ++e) {
-            double pq, eps, hb;
-            const double S = event_S(mo, params, Mp, Gp, m[e], cK[e], cpsi[e], phi[e],
-                                     grad ? dS : NULL, &pq, NULL);
+            double pq, pqb, eps, hb;
+            /* flavour: density (1 - w) S(t phi) + w S(-t phi), templates at the observed phi */
+            const double t = tag ? tag[e] : 1.0, w = mo->mistag;
+            double S = event_S(mo, params, Mp, Gp, m[e], cK[e], cpsi[e], t * phi[e],
+                               grad ? dS : NULL, &pq, NULL);
+            if (w > 0.0) {
+                const double Sb = event_S(mo, params, Mp, Gp, m[e], cK[e], cpsi[e], -t * phi[e],
+                                          grad ? dSb : NULL, &pqb, NULL);
+                S = (1.0 - w) * S + w * Sb;
+                if (grad)
+                    for (int i = 0; i < NP; ++i) dS[i] = (1.0 - w) * dS[i] + w * dSb[i];
+            }
             point_templates(mo, m[e], cK[e], cpsi[e], phi[e], &eps, &hb);
             const double sig = P * eps * S / Ie;
             const double g = sig + (P < 1.0 ? (1.0 - P) * hb / Bs : 0.0);   /* f / (p q) */

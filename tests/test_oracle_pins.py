@@ -450,6 +450,95 @@ def test_eq14_gradient_matches_central_differences():
         assert abs(g[i] - fd) <= 1e-5 * max(1.0, abs(g[i]))
 
 
+# ---------------------------------------------------------------- flavour (B0bar: phi -> -phi; mistag)
+def _phi_even(hist):
+    """The angular template made even in phi (its y axis, range symmetric about 0)."""
+    return W.Hist2D(((hist.h + hist.h[::-1, :]) / 2).astype(np.float32), hist.range)
+
+
+def _flavour_case(name="kstar10_z", n_ev=1500, n_mc=4000, seed=41):
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    ev = W.peaked_points(n_ev, seed, res)
+    nm = W.uniform_points(n_mc, seed + 1)
+    tag = np.where(np.random.default_rng(seed + 2).uniform(size=n_ev) < 0.5, 1.0, -1.0)
+    return res, p, ev, nm, tag
+
+
+def test_flavour_tag_is_the_mirrored_event():
+    """No mistag: a B0bar-tagged event has the density of the B0 event at -phi
+    (with a phi-even efficiency the template values agree too)."""
+    res, p, ev, nm, tag = _flavour_case()
+    mirrored = (ev[0], ev[1], ev[2], (tag * ev[3]).astype(np.float32))
+    em, ea, bm, ba, P = W.eq14_templates(12)
+    for templates in (False, True):
+        a, b = O.Model(res), O.Model(res)
+        if templates:
+            for mo in (a, b):
+                mo.set_template(0, em, _phi_even(ea))
+                mo.set_template(1, bm, _phi_even(ba), purity=P)
+        nll_t, g_t, _, rc = a.nll_eq14(p, ev, nm, grad=True, tag=tag)
+        nll_m, g_m, _, rc2 = b.nll_eq14(p, mirrored, nm, grad=True)
+        assert rc == 0 and rc2 == 0
+        assert nll_t == pytest.approx(nll_m, rel=1e-13)
+        assert np.allclose(g_t, g_m, rtol=1e-11, atol=1e-11 * np.max(np.abs(g_m)))
+
+
+def test_half_mistag_makes_the_tag_uninformative():
+    """w = 1/2: the density (S(phi) + S(-phi)) / 2 of an event does not depend
+    on its tag."""
+    res, p, ev, nm, tag = _flavour_case()
+    mo = O.Model(res)
+    mo.set_mistag(0.5)
+    n1, g1, _, _ = mo.nll_eq14(p, ev, nm, grad=True, tag=tag)
+    n2, g2, _, _ = mo.nll_eq14(p, ev, nm, grad=True, tag=-tag)
+    n3, _, _, _ = mo.nll_eq14(p, ev, nm)
+    assert n1 == pytest.approx(n2, rel=1e-14) and n1 == pytest.approx(n3, rel=1e-14)
+    assert np.allclose(g1, g2, rtol=1e-12, atol=1e-12 * np.max(np.abs(g1)))
+    with pytest.raises(ValueError):
+        mo.set_mistag(0.6)
+
+
+def test_one_normalisation_serves_both_flavours():
+    """The box is symmetric in phi and p q even in it, so int S(-phi) p q = int
+    S(phi) p q: over a phi-mirrored point sample the two sums are equal, and an
+    independent sample's sum agrees within its Monte Carlo error."""
+    res, p, _, _, _ = _flavour_case()
+    mo = O.Model(res)
+    u = W.uniform_points(100_000, 45)
+    um = (u[0], u[1], u[2], -u[3])
+    both = tuple(np.concatenate([a, b]) for a, b in zip(u, um))
+    I_u, I_m = mo.norm(p, u), mo.norm(p, um)
+    I_b = mo.norm(p, both)
+    assert I_b == pytest.approx(0.5 * (I_u + I_m), rel=1e-13)
+    S, pq = mo.density(p, u)
+    sem = W.BOX_VOLUME * np.std(S * pq) / math.sqrt(len(S))
+    assert abs(I_u - I_m) < 4 * math.sqrt(2) * sem
+
+
+def test_flavour_gradient_matches_central_differences():
+    res, p, ev, nm, tag = _flavour_case("kstar10_z", 400, 800)
+    fl = ["K*(892)", "Z(4430)"]
+    mo = O.Model(res, float_names=fl)
+    p = W.couplings_to_params(W.draw_couplings(res, W.CONFIGS["kstar10_z"].coupling_seed),
+                              W.float_mg_values(res, fl))
+    em, ea, bm, ba, P = W.eq14_templates(13)
+    mo.set_template(0, em, _phi_even(ea))
+    mo.set_template(1, bm, ba, purity=P)
+    mo.set_mistag(0.07)
+    _, g, _, rc = mo.nll_eq14(p, ev, nm, grad=True, tag=tag)
+    assert rc == 0
+    rng = np.random.default_rng(14)
+    for i in sorted(rng.choice(len(p), 12, replace=False)) + [len(p) - 1, len(p) - 4]:
+        h = 1e-6 * max(1.0, abs(p[i]))
+        up, dn = p.copy(), p.copy()
+        up[i] += h
+        dn[i] -= h
+        fd = (mo.nll_eq14(up, ev, nm, tag=tag)[0] - mo.nll_eq14(dn, ev, nm, tag=tag)[0]) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-5 * max(1.0, abs(g[i]))
+
+
 # ---------------------------------------------------------------- kinematics
 def test_kstar_angles_round_trip():
     mo = _all_model()
