@@ -1,7 +1,18 @@
-// Instantiation of the per-event kernels for at most 10 K* resonances.
+// Dispatch of the per-event kernels for at most 10 K* resonances; the kernels
+// for each number of Z resonances are instantiated in amp4d_eval_nk10_z*.cu,
+// which compile in parallel.
 #include "amp4d_eval.cuh"
 
 namespace amp4d {
+extern template cudaError_t launch_eval_t<10, 0>(const LaunchArgs &, int);
+extern template cudaError_t launch_eval_t<10, 1>(const LaunchArgs &, int);
+extern template cudaError_t launch_eval_t<10, 2>(const LaunchArgs &, int);
+extern template cudaError_t launch_grad_t<10, 0>(const LaunchArgs &, bool);
+extern template cudaError_t launch_grad_t<10, 1>(const LaunchArgs &, bool);
+extern template cudaError_t launch_grad_t<10, 2>(const LaunchArgs &, bool);
+extern template cudaError_t launch_lcache_t<10, 0>(const LaunchArgs &, float2 *);
+extern template cudaError_t launch_lcache_t<10, 1>(const LaunchArgs &, float2 *);
+extern template cudaError_t launch_lcache_t<10, 2>(const LaunchArgs &, float2 *);
 template cudaError_t launch_eval_nk<10>(const LaunchArgs &, int);
 template cudaError_t launch_grad_nk<10>(const LaunchArgs &, bool);
 template cudaError_t launch_lcache_nk<10>(const LaunchArgs &, float2 *);
