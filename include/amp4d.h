@@ -199,6 +199,25 @@ amp4d_status amp4d_set_background(amp4d_model *model, const amp4d_hist2d *mass,
                                   const amp4d_hist2d *angle, double purity, void *stream);
 
 /*
+ * Flavour of the data events (text after Eq. 12: the charge-conjugate decay,
+ * identified by the K charge, differs only in the sign of phi, and a fraction
+ * of the events may be mis-tagged).  tag: n_events FP32 values, +1 (B0) or -1
+ * (B0bar), host or device memory, copied; NULL makes every event B0.  The
+ * signal density of an event tagged t is
+ *   (1 - w) S(m, cK, cpsi, t phi) + w S(m, cK, cpsi, -t phi),   w = mistag in [0, 0.5],
+ * S at -phi being S with sin phi, sin phi~ and sin alpha negated (the mirror
+ * through the K pi decay plane).  The box is symmetric in phi and p q does not
+ * depend on it, so every tag shares the normalisation I (or I_eps): with tags
+ * or a mistag an efficiency must be even in phi (its angular template's phi range
+ * symmetric about 0 and its contents mirror-symmetric), else STATE.  Templates
+ * are read at the observed phi.  amp4d_eval_density returns the tagged density.
+ * amp4d_set_events resets every tag to +1; the mistag stays.  Synchronous.
+ * Errors: ARG (a tag not +-1, w out of range), STATE (no events, an efficiency
+ * not even in phi), CUDA, OOM.
+ */
+amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mistag, void *stream);
+
+/*
  * -2 ln L at params (host, amp4d_num_params doubles); *nll is host memory.
  * On AMP4D_ERR_DOMAIN *nll = +INFINITY (the minimiser treats it as a bad step).
  */

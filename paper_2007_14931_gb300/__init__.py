@@ -185,6 +185,7 @@ amp4d_set_efficiency = _proto("amp4d_set_efficiency", C.c_int,
                               [_vp, C.POINTER(amp4d_hist2d), C.POINTER(amp4d_hist2d), _vp])
 amp4d_set_background = _proto("amp4d_set_background", C.c_int,
                               [_vp, C.POINTER(amp4d_hist2d), C.POINTER(amp4d_hist2d), C.c_double, _vp])
+amp4d_set_flavour = _proto("amp4d_set_flavour", C.c_int, [_vp, _vp, C.c_double, _vp])
 amp4d_gram_selftest = _proto("amp4d_gram_selftest", C.c_int, [_vp, C.c_int64, _vp, _vp])
 amp4d_generate = _proto("amp4d_generate", C.c_int, [_vp, _d, C.c_uint64, C.c_int64, _vp, _vp, _vp, _vp, _vp])
 amp4d_proposal_train = _proto("amp4d_proposal_train", C.c_int,
@@ -208,7 +209,7 @@ amp4d_shard_last_error = _proto("amp4d_shard_last_error", C.c_char_p, [])
 amp4d_profile_enable = _proto("amp4d_profile_enable", C.c_int, [_vp, C.c_int])
 amp4d_profile_read = _proto("amp4d_profile_read", C.c_int, [_vp, _d, C.POINTER(C.c_int64)])
 
-EXPORTED = ["amp4d_set_efficiency", "amp4d_set_background",
+EXPORTED = ["amp4d_set_efficiency", "amp4d_set_background", "amp4d_set_flavour",
             "amp4d_model_create", "amp4d_model_destroy", "amp4d_last_error", "amp4d_num_columns",
             "amp4d_num_params", "amp4d_set_events", "amp4d_set_norm_points", "amp4d_eval_nll",
             "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
@@ -386,6 +387,18 @@ class Model:
         (hm, km), (ha, ka) = self._hist(mass), self._hist(angle)
         self._check(amp4d_set_background(self.h, C.byref(hm), C.byref(ha), float(purity),
                                          _stream_ptr(stream)))
+
+    def set_flavour(self, tag, mistag=0.0, stream=None):
+        """Flavour tags of the data events (+1 B0, -1 B0bar; FP32 host array or
+        CUDA tensor, None for all B0) and the mistag fraction w."""
+        if tag is None:
+            ptr = None
+        elif hasattr(tag, "data_ptr"):
+            ptr = tag.data_ptr()
+        else:
+            tag = np.ascontiguousarray(tag, dtype=np.float32)
+            ptr = tag.ctypes.data
+        self._check(amp4d_set_flavour(self.h, ptr, float(mistag), _stream_ptr(stream)))
 
     def fit_fractions(self, params, stream=None):
         """Fit fraction of every resonance (Eq. 13), in creation order (host float64)."""

@@ -37,6 +37,7 @@ struct EventSet {
     // normalisation set keeps its weights as loaded in w0 and its weight record
     // holds w0 eps.
     float *eps = nullptr, *hb = nullptr, *w0 = nullptr;
+    float *tag = nullptr;       // data: flavour tags (+1 B0, -1 B0bar); the stored phi is tag x phi
     double lneps = 0.0;         // data: sum ln eps over the events
     double whb = 0.0;           // points: sum w0 hb
 };
@@ -90,6 +91,8 @@ struct amp4d_model {
     TplDev tpl[4] = {};
     bool has_eff = false, has_bkg = false;
     double purity = 1.0;
+    bool eff_phi_even = true;    // the angular efficiency template is even in phi
+    double mistag = 0.0;         // flavour mistag fraction
     bool kstar_fixed = true;     // no K* has a floating mass or width
     bool z_float = false;        // some Z has a floating mass and width
     // learned proposal
@@ -177,7 +180,7 @@ amp4d_status load_set(amp4d_model *model, EventSet &s, const float *m, const flo
     if (s.rec) { cudaFree(s.rec); s.rec = nullptr; }
     if (s.part) { cudaFree(s.part); s.part = nullptr; }
     if (s.lcache) { cudaFree(s.lcache); s.lcache = nullptr; }
-    for (float **b : {&s.eps, &s.hb, &s.w0})
+    for (float **b : {&s.eps, &s.hb, &s.w0, &s.tag})
         if (*b) { cudaFree(*b); *b = nullptr; }
     s.lneps = s.whb = 0.0;
     s.lcache_valid = false;
@@ -276,6 +279,7 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.kstar_fixed = mo->kstar_fixed;
     a.z_float = mo->z_float;
     a.acc = (&s == &mo->ev) ? mo->d_acc : mo->d_acc + 2 * mo->nslot;
+    a.mt = (&s == &mo->ev) && mo->mistag > 0.0;
     if (&s == &mo->ev && mo->has_bkg && mo->purity < 1.0 && s.eps && s.hb) {
         a.mix_eps = s.eps;
         a.mix_hb = s.hb;
@@ -505,6 +509,7 @@ ModelStatic make_static(const amp4d_model *mo)
     // Eq. 14: beta = (1 - P) / B, B = (V / n) sum w0 hb over the normalisation points
     const double B = mo->mc.n > 0 ? mo->mc.volume / (double)mo->mc.n * mo->mc.whb : 0.0;
     s.mix_beta = (mixing(mo) && B > 0.0) ? (1.0 - mo->purity) / B : 0.0;
+    s.mistag = mo->mistag;
     for (size_t i = 0; i < mo->internal.size(); ++i) {
         const int u = mo->internal[i];
         const amp4d_resonance &r = mo->res[u];
@@ -568,6 +573,7 @@ amp4d_status apply_templates(amp4d_model *model, EventSet &s, bool is_norm, cuda
     a.eps = is_norm ? nullptr : s.eps;
     a.hb = is_norm ? nullptr : s.hb;
     a.w0 = is_norm ? s.w0 : nullptr;
+    a.tag = is_norm ? nullptr : s.tag;
     a.wout = wrec;
     for (int i = 0; i < 4; ++i) a.t[i] = model->tpl[i];
     if (!model->has_eff) a.t[0].h = a.t[1].h = nullptr;
@@ -627,6 +633,24 @@ amp4d_status set_template_pair(amp4d_model *model, int t0, const amp4d_hist2d *m
     CK(cudaStreamSynchronize(st));
     return AMP4D_OK;
 }
+
+// Whether the angular efficiency template (slot 1: x = cos theta_psi, y = phi) is
+// even in phi: a range symmetric about 0 and mirror-symmetric contents.
+amp4d_status angular_template_phi_even(amp4d_model *model, int t, bool *even)
+{
+    const TplDev &d = model->tpl[t];
+    *even = false;
+    if (!(d.ylo == -d.yhi)) return AMP4D_OK;
+    std::vector<float> h((size_t)d.nx * d.ny);
+    CK(cudaMemcpy(h.data(), d.h, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int iy = 0; iy < d.ny; ++iy)
+        for (int ix = 0; ix < d.nx; ++ix)
+            if (h[(size_t)iy * d.nx + ix] != h[(size_t)(d.ny - 1 - iy) * d.nx + ix]) return AMP4D_OK;
+    *even = true;
+    return AMP4D_OK;
+}
+
+bool flavour_active(const amp4d_model *m) { return m->mistag > 0.0 || m->ev.tag != nullptr; }
 
 amp4d_status reapply_templates(amp4d_model *model, cudaStream_t st)
 {
@@ -749,7 +773,7 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
         if (s->rec) cudaFree(s->rec);
         if (s->part) cudaFree(s->part);
         if (s->lcache) cudaFree(s->lcache);
-        for (float *b : {s->eps, s->hb, s->w0})
+        for (float *b : {s->eps, s->hb, s->w0, s->tag})
             if (b) cudaFree(b);
     }
     for (float *t : model->d_tpl)
@@ -808,8 +832,53 @@ amp4d_status amp4d_set_efficiency(amp4d_model *model, const amp4d_hist2d *mass,
         amp4d_status rc = set_template_pair(model, 0, mass, angle, st);
         if (rc) return rc;
     }
+    bool even = true;
+    if (mass) {
+        amp4d_status rc = angular_template_phi_even(model, 1, &even);
+        if (rc) return rc;
+    }
+    if (mass && !even && flavour_active(model))
+        return fail(model, AMP4D_ERR_STATE, "with flavour tags or a mistag the efficiency must be even in phi");
     model->has_eff = mass != nullptr;
+    model->eff_phi_even = even;
     return reapply_templates(model, st);
+}
+
+amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mistag, void *stream)
+{
+    if (!model) return AMP4D_ERR_ARG;
+    if (!(mistag >= 0.0 && mistag <= 0.5)) return fail(model, AMP4D_ERR_ARG, "mistag must lie in [0, 0.5]");
+    EventSet &s = model->ev;
+    if (tag && s.n == 0) return fail(model, AMP4D_ERR_STATE, "set_events must come first");
+    if ((tag || mistag > 0.0) && model->has_eff && !model->eff_phi_even)
+        return fail(model, AMP4D_ERR_STATE, "with flavour tags or a mistag the efficiency must be even in phi");
+    CK(cudaSetDevice(model->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    float *nt = nullptr;
+    if (tag) {
+        std::vector<float> h((size_t)s.n);
+        CK(cudaMemcpy(h.data(), tag, h.size() * sizeof(float), cudaMemcpyDefault));
+        for (int64_t e = 0; e < s.n; ++e)
+            if (h[e] != 1.0f && h[e] != -1.0f) {
+                char buf[96];
+                std::snprintf(buf, sizeof buf, "tag %lld is not +1 or -1", (long long)e);
+                return fail(model, AMP4D_ERR_ARG, buf);
+            }
+        if (cudaMalloc(&nt, (size_t)s.n * sizeof(float)) != cudaSuccess)
+            return fail(model, AMP4D_ERR_OOM, "tag allocation failed");
+        CK(cudaMemcpy(nt, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (s.n > 0 && (s.tag || nt)) {
+        const int grid = (int)std::min<int64_t>((s.npad + prepare_block() - 1) / prepare_block(), model->nsm * 8);
+        CK(launch_flavour(s.rec, s.npad, s.n, s.tag, nt, model->nZ > 0, grid, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (s.tag) cudaFree(s.tag);
+    s.tag = nt;
+    model->mistag = mistag;
+    amp4d_status rc = apply_templates(model, s, false, st);
+    if (rc == AMP4D_OK) rc = refresh_static(model);
+    return rc;
 }
 
 amp4d_status amp4d_set_background(amp4d_model *model, const amp4d_hist2d *mass,

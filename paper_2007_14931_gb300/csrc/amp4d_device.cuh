@@ -77,6 +77,7 @@ struct ResStatic {
 struct ModelStatic {
     double mB, mpsi, mK, mpi;
     double mix_beta;   // Eq. 14: (1 - P) / B with a background, else 0
+    double mistag;     // flavour mistag fraction w
     int n_res, n_col, n_float, n_param;
     ResStatic res[AMP4D_MAX_RES];
 };
@@ -104,6 +105,8 @@ struct ModelDev {
     // Eq. 14 with a background: alpha = P / I_eps (written each evaluation once
     // I_eps is known) and beta = (1 - P) / B, each hi + lo.
     float mahi, malo, mbhi, mblo;
+    // Flavour mistag fraction w (hi + lo) and 1 - w.
+    float mwhi, mwlo, m1w;
 };
 
 // ----------------------------------------------------------------------------
@@ -154,6 +157,12 @@ __device__ __forceinline__ void cfma_conj(float2 &a, float2 b, float2 c)
 {
     a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
     a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
+}
+// a += conj(b c)
+__device__ __forceinline__ void cfma_conjp(float2 &a, float2 b, float2 c)
+{
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(-b.x, c.y, fmaf(-b.y, c.x, a.y));
 }
 // a += (hi + lo) * c, with the low part inside the FMA chain of the high-part
 // product, so the constant hi + lo is applied before each term is rounded (an

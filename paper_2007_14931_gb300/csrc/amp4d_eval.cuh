@@ -66,6 +66,8 @@ template <int NK, int NZ>
 struct EvState {
     float2 a[2];
     float S;
+    float2 ab[2];                 // flavour mistag: the amplitudes at -phi (every angular phase conjugated)
+    float Sb;                     // and S there
     float2 B0[NK], B1[NK];        // K* k: A_k d0 and A_k d1 (l = 0 and l = +1; l = -1 is -B1)
     float2 Psi[3][2];
     float2 AZ[NZ > 0 ? NZ : 1];
@@ -90,7 +92,11 @@ __device__ __forceinline__ float2 cached_or_computed(const ResDev &rs, bool have
 // lc (nullable): basis cache [resonance][lcn] of lineshapes A'_R per event e.
 // FX: every resonance is fixed and lc is given, so every lineshape comes from
 // the cache and the masses and momenta (records M, P, Q, MZ, PZ, QZ) are unused.
-template <int NK, int NZ, bool FX = false>
+// MT (flavour mistag): also the amplitudes and S at -phi.  The mirror phi -> -phi
+// flips sin phi, sin phi~ and sin alpha and leaves every cosine, mass and
+// momentum unchanged, so the mirrored amplitude is the same coupling sums with
+// every angular phase factor (e^{i l phi}, e^{i l' phi~}, e^{i xi alpha}) conjugated.
+template <int NK, int NZ, bool FX = false, bool MT = false>
 __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                                            EvState<NK, NZ> &ev,
                                            const float2 *__restrict__ lc = nullptr,
@@ -157,6 +163,13 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
         cfma(a, ev.Psi[1][x], u[1]);
         cfma(a, ev.Psi[2][x], u[2]);
         ev.a[x] = a;
+        if constexpr (MT) {
+            float2 b = make_float2(0.f, 0.f);
+            cfma_conj(b, ev.Psi[0][x], u[0]);
+            cfma_conj(b, ev.Psi[1][x], u[1]);
+            cfma_conj(b, ev.Psi[2][x], u[2]);
+            ev.ab[x] = b;
+        }
     }
     if constexpr (NZ > 0) {
         float mZ = 0.f, pZ = 0.f, qZ = 0.f, invmZ = 0.f;
@@ -193,10 +206,43 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
                 if (rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
                 if (rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
                 cfma(ev.a[x], LA, s);
+                if constexpr (MT) {
+                    const float2 c0 = make_float2(o0.x, -o0.y), c1 = make_float2(o1.x, -o1.y);
+                    float2 sb = make_float2(0.f, 0.f);
+                    if (rs.zcol0 >= 0) cfma2p(sb, md.zp[z][0], c0, make_float2(c0.y, c0.x));
+                    if (rs.zcol1 >= 0) cfma2p(sb, md.zp[z][1], c1, make_float2(c1.y, c1.x));
+                    cfma(ev.ab[x], LA, sb);
+                }
             }
         }
     }
     ev.S = cabs2(ev.a[0]) + cabs2(ev.a[1]);
+    if constexpr (MT) ev.Sb = cabs2(ev.ab[0]) + cabs2(ev.ab[1]);
+}
+
+// The flavour-tagged density (1 - w) S + w S(-phi) = S + w (S(-phi) - S).
+template <bool MT, int NK, int NZ>
+__device__ __forceinline__ float observed_S(const ModelDev &md, const EvState<NK, NZ> &ev)
+{
+    if constexpr (!MT) return ev.S;
+    const float d = ev.Sb - ev.S;
+    return fmaf(md.mwhi, d, fmaf(md.mwlo, d, ev.S));
+}
+
+// Adjoint vectors w_l = sum_xi conj(as_xi) Psi_{l xi} of the scaled amplitudes,
+// with the mistag term conj(asb_xi Psi_{l xi}) for the mirrored amplitudes.
+template <bool MT>
+__device__ __forceinline__ float2 adj_w(const float2 (&as)[2], const float2 (&asb)[2],
+                                        const float2 (&psi)[2])
+{
+    float2 t = make_float2(0.f, 0.f);
+    cfma_conj(t, as[0], psi[0]);
+    cfma_conj(t, as[1], psi[1]);
+    if constexpr (MT) {
+        cfma_conjp(t, asb[0], psi[0]);
+        cfma_conjp(t, asb[1], psi[1]);
+    }
+    return t;
 }
 
 // Evaluation of NE events at once when every K* lineshape comes from the basis
@@ -204,7 +250,7 @@ __device__ __forceinline__ void eval_event(const ModelDev &md, const float *r,
 // holds the records of event e[j]; lc is the basis cache [resonance][lcn].  ZF:
 // a Z resonance whose mass and width float is computed (Eq. 2-3) from the
 // Z-chain records, the others come from the cache.
-template <int NK, int NZ, int NE, bool ZF = false>
+template <int NK, int NZ, int NE, bool ZF = false, bool MT = false>
 __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
                                                EvState<NK, NZ> (&ev)[NE],
                                                const float2 *__restrict__ lc, int64_t lcn,
@@ -272,6 +318,13 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             cfma(a, ev[j].Psi[1][x], u[j][1]);
             cfma(a, ev[j].Psi[2][x], u[j][2]);
             ev[j].a[x] = a;
+            if constexpr (MT) {
+                float2 b = make_float2(0.f, 0.f);
+                cfma_conj(b, ev[j].Psi[0][x], u[j][0]);
+                cfma_conj(b, ev[j].Psi[1][x], u[j][1]);
+                cfma_conj(b, ev[j].Psi[2][x], u[j][2]);
+                ev[j].ab[x] = b;
+            }
         }
     if constexpr (NZ > 0) {
         float2 ephz[NE];
@@ -322,12 +375,22 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
                     if (rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
                     if (rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
                     cfma(ev[j].a[x], LA, s);
+                    if constexpr (MT) {
+                        const float2 c0 = make_float2(o0.x, -o0.y), c1 = make_float2(o1.x, -o1.y);
+                        float2 sb = make_float2(0.f, 0.f);
+                        if (rs.zcol0 >= 0) cfma2p(sb, md.zp[z][0], c0, make_float2(c0.y, c0.x));
+                        if (rs.zcol1 >= 0) cfma2p(sb, md.zp[z][1], c1, make_float2(c1.y, c1.x));
+                        cfma(ev[j].ab[x], LA, sb);
+                    }
                 }
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < NE; ++j) ev[j].S = cabs2(ev[j].a[0]) + cabs2(ev[j].a[1]);
+    for (int j = 0; j < NE; ++j) {
+        ev[j].S = cabs2(ev[j].a[0]) + cabs2(ev[j].a[1]);
+        if constexpr (MT) ev[j].Sb = cabs2(ev[j].ab[0]) + cabs2(ev[j].ab[1]);
+    }
 }
 
 // Compensated FP32 accumulator.
@@ -417,7 +480,7 @@ __device__ __forceinline__ constexpr bool record_used(int k)
                     (!ZF && (k == REC_MZ || k == REC_PZ || k == REC_QZ)));
 }
 
-template <int NK, int NZ, int MODE, int BLOCK, bool FX, bool MIX = false>
+template <int NK, int NZ, int MODE, int BLOCK, bool FX, bool MIX = false, bool MT = false>
 __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, int64_t npad,
                                                 int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                 unsigned long long *__restrict__ acc, float *__restrict__ S_out,
@@ -439,14 +502,17 @@ __global__ void __launch_bounds__(BLOCK) k_eval(const float *__restrict__ rec, i
 #pragma unroll
         for (int k = 0; k < NREC; ++k) v[k] = record_used<FX>(k) ? __ldg(rec + k * npad + e) : 0.f;
         EvState<NK, NZ> ev;
-        eval_event<NK, NZ, FX>(md, v, ev, lc, npad, e);
+        eval_event<NK, NZ, FX, MT>(md, v, ev, lc, npad, e);
         if (MODE == MODE_SUM_LNS) {
             float scale, r;
-            if (!data_term<MIX>(md, ev.S, meps, mhb, e, ksum, esum, scale, r)) { bad = true; continue; }
+            if (!data_term<MIX>(md, observed_S<MT>(md, ev), meps, mhb, e, ksum, esum, scale, r)) {
+                bad = true;
+                continue;
+            }
         } else if (MODE == MODE_SUM_WS) {
             ksum.add(__ldg(rec + wrec * npad + e) * ev.S);
         } else {
-            S_out[e] = ev.S;
+            S_out[e] = observed_S<MT>(md, ev);
         }
     }
     if (MODE == MODE_WRITE) return;
@@ -528,7 +594,8 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // e + stride, ... (each load of a warp stays coalesced).  The constants of a
 // resonance and each gradient slot pair are read once for the NE events.  An
 // event index beyond n repeats a valid event with zero weight.
-template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, bool ZF, bool MIX = false>
+template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, bool ZF, bool MIX = false,
+          bool MT = false>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
                                                          unsigned long long *__restrict__ acc,
@@ -565,15 +632,16 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                 v[j][k] = record_used<true, ZF>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
         }
         EvState<NK, NZ> ev[NE];
-        eval_events_fx<NK, NZ, NE, ZF>(md, v, ev, lc, npad, e);
-        float2 as[NE][2];
+        eval_events_fx<NK, NZ, NE, ZF, MT>(md, v, ev, lc, npad, e);
+        float2 as[NE][2], asb[NE][2];
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
             float scale = 0.f;
             if (valid[j]) {
                 if (!NORM) {
                     float r = 0.f;
-                    if (!data_term<MIX>(md, ev[j].S, meps, mhb, e[j], acc0, esum, scale, r)) {
+                    if (!data_term<MIX>(md, observed_S<MT>(md, ev[j]), meps, mhb, e[j], acc0, esum,
+                                        scale, r)) {
                         bad = true;
                         scale = 0.f;
                     } else if constexpr (MIX) {
@@ -585,19 +653,19 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                     scale = 2.0f * w;
                 }
             }
+            // mistag: (1 - w) on the amplitudes, w on the mirrored ones
+            const float sa = MT ? scale * md.m1w : scale, sb = scale * md.mwhi;
 #pragma unroll
-            for (int x = 0; x < 2; ++x) as[j][x] = cscale(ev[j].a[x], scale);
+            for (int x = 0; x < 2; ++x) {
+                as[j][x] = cscale(ev[j].a[x], sa);
+                asb[j][x] = MT ? cscale(ev[j].ab[x], sb) : make_float2(0.f, 0.f);
+            }
         }
         float2 wl[NE][3];
 #pragma unroll
         for (int j = 0; j < NE; ++j)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                float2 t = make_float2(0.f, 0.f);
-                cfma_conj(t, as[j][0], ev[j].Psi[l][0]);
-                cfma_conj(t, as[j][1], ev[j].Psi[l][1]);
-                wl[j][l] = t;
-            }
+            for (int l = 0; l < 3; ++l) wl[j][l] = adj_w<MT>(as[j], asb[j], ev[j].Psi[l]);
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             if (k >= nK) continue;
@@ -627,6 +695,10 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                     for (int x = 0; x < 2; ++x) {
                         cfma_conj(w0, as[j][x], ev[j].Om0[z][x]);
                         cfma_conj(w1, as[j][x], ev[j].Om1[z][x]);
+                        if constexpr (MT) {
+                            cfma_conjp(w0, asb[j][x], ev[j].Om0[z][x]);
+                            cfma_conjp(w1, asb[j][x], ev[j].Om1[z][x]);
+                        }
                     }
                     const float2 A = ev[j].AZ[z];
                     g0.x = fmaf(A.x, w0.x, fmaf(-A.y, w0.y, g0.x));
@@ -672,7 +744,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 // is one float2 at p * BLOCK + t, so each update is one 64-bit load and store
 // and a warp's accesses cover every bank twice (two wavefronts, no conflict).
 // Events are read one per iteration with coalesced scalar loads.
-template <int NK, int NZ, bool NORM, int BLOCK, bool MIX = false>
+template <int NK, int NZ, bool NORM, int BLOCK, bool MIX = false, bool MT = false>
 __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *__restrict__ rec, int64_t npad,
                                                    int64_t n, int wrec, const ModelDev *__restrict__ gmd,
                                                    unsigned long long *__restrict__ acc,
@@ -699,11 +771,14 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
 #pragma unroll
         for (int k = 0; k < NREC; ++k) v[k] = __ldg(rec + k * npad + e);
         EvState<NK, NZ> ev;
-        eval_event<NK, NZ>(md, v, ev, lc, npad, e);
+        eval_event<NK, NZ, false, MT>(md, v, ev, lc, npad, e);
         float scale;
         if (!NORM) {
             float r = 0.f;
-            if (!data_term<MIX>(md, ev.S, meps, mhb, e, acc0, esum, scale, r)) { bad = true; continue; }
+            if (!data_term<MIX>(md, observed_S<MT>(md, ev), meps, mhb, e, acc0, esum, scale, r)) {
+                bad = true;
+                continue;
+            }
             if constexpr (MIX) rsum.add(r);
         } else {
             const float w = __ldg(rec + wrec * npad + e);
@@ -714,7 +789,12 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
         // (normalisation) factor, so every slot update below is two FMAs.
         float2 as[2];
 #pragma unroll
-        for (int x = 0; x < 2; ++x) as[x] = cscale(ev.a[x], scale);
+        for (int x = 0; x < 2; ++x) as[x] = cscale(ev.a[x], MT ? scale * md.m1w : scale);
+        float2 asb[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if constexpr (MT) {
+#pragma unroll
+            for (int x = 0; x < 2; ++x) asb[x] = cscale(ev.ab[x], scale * md.mwhi);
+        }
         // w_l = sum_xi conj(as_xi) Psi_{l xi}
         float2 wl[3];
 #pragma unroll
@@ -722,6 +802,10 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
             float2 t = make_float2(0.f, 0.f);
             cfma_conj(t, as[0], ev.Psi[l][0]);
             cfma_conj(t, as[1], ev.Psi[l][1]);
+            if constexpr (MT) {
+                cfma_conjp(t, asb[0], ev.Psi[l][0]);
+                cfma_conjp(t, asb[1], ev.Psi[l][1]);
+            }
             wl[l] = t;
         }
 #pragma unroll
@@ -764,6 +848,10 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
                 for (int x = 0; x < 2; ++x) {
                     cfma_conj(w0, as[x], ev.Om0[z][x]);
                     cfma_conj(w1, as[x], ev.Om1[z][x]);
+                    if constexpr (MT) {
+                        cfma_conjp(w0, asb[x], ev.Om0[z][x]);
+                        cfma_conjp(w1, asb[x], ev.Om1[z][x]);
+                    }
                 }
                 const float2 A = ev.AZ[z];
                 float2 g0 = g[(3 * NK + 2 * z) * BLOCK], g1 = g[(3 * NK + 2 * z + 1) * BLOCK];
@@ -803,22 +891,26 @@ cudaError_t launch_eval_fx(const LaunchArgs &a, int mode)
 {
     return with_const_table(a.md, a.stream, [&]() {
         switch (mode) {
-        case MODE_SUM_LNS:
-            if (a.mix_eps)
-                k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX, true><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                    a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache, a.mix_eps,
-                    a.mix_hb);
-            else
-                k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                    a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
+        case MODE_SUM_LNS: {
+            auto kern = k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX, false, false>;
+            if (a.mix_eps && a.mt) kern = k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX, true, true>;
+            else if (a.mix_eps) kern = k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX, true, false>;
+            else if (a.mt) kern = k_eval<NK, NZ, MODE_SUM_LNS, EVAL_BLOCK, FX, false, true>;
+            kern<<<a.grid, EVAL_BLOCK, 0, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out,
+                                                     a.status, a.lcache, a.mix_eps, a.mix_hb);
             break;
+        }
         case MODE_SUM_WS:
             k_eval<NK, NZ, MODE_SUM_WS, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
                 a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
             break;
         default:
-            k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
-                a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
+            if (a.mt)
+                k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK, FX, false, true><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                    a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
+            else
+                k_eval<NK, NZ, MODE_WRITE, EVAL_BLOCK, FX><<<a.grid, EVAL_BLOCK, 0, a.stream>>>(
+                    a.rec, a.npad, a.n, a.wrec, a.md, a.acc, a.out, a.status, a.lcache);
             break;
         }
         return cudaGetLastError();
@@ -842,9 +934,15 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
         auto kern = a.z_float ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, true>
                               : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, false>;
         if constexpr (!NORM) {
-            if (mix)
-                kern = a.z_float ? k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, true>
-                                 : k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, true>;
+            switch ((a.z_float ? 4 : 0) | (mix ? 2 : 0) | (a.mt ? 1 : 0)) {
+            case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, false, true>; break;
+            case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, true, false>; break;
+            case 3: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, true, true>; break;
+            case 5: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, false, true>; break;
+            case 6: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, true, false>; break;
+            case 7: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, true, true>; break;
+            default: break;
+            }
         }
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -859,7 +957,9 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
     } else {
         auto kern = k_grad<NK, NZ, NORM, GRAD_BLOCK>;
         if constexpr (!NORM) {
-            if (mix) kern = k_grad<NK, NZ, false, GRAD_BLOCK, true>;
+            if (mix && a.mt) kern = k_grad<NK, NZ, false, GRAD_BLOCK, true, true>;
+            else if (mix) kern = k_grad<NK, NZ, false, GRAD_BLOCK, true, false>;
+            else if (a.mt) kern = k_grad<NK, NZ, false, GRAD_BLOCK, false, true>;
         }
         if (smem > 48 * 1024) {   // above the default dynamic shared-memory limit
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -465,6 +465,9 @@ __global__ void k_build_table(const ModelStatic *__restrict__ st, const double *
         md->mahi = md->malo = 0.f;   // alpha: written once I_eps is known
         md->mbhi = (float)st->mix_beta;
         md->mblo = (float)(st->mix_beta - (double)md->mbhi);
+        md->mwhi = (float)st->mistag;
+        md->mwlo = (float)(st->mistag - (double)md->mwhi);
+        md->m1w = (float)(1.0 - st->mistag);
     }
     __syncthreads();
     if (t == 0) {

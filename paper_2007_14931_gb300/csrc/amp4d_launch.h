@@ -31,6 +31,7 @@ struct LaunchArgs {
     // accumulator of the signal probabilities r = alpha eps S / g.
     const float *mix_eps = nullptr, *mix_hb = nullptr;
     unsigned long long *acc_r = nullptr;
+    bool mt = false;                 // data sets with a flavour mistag: S and S(-phi) per event
 };
 
 // Resident CTAs per SM of the adjoint kernels (their __launch_bounds__).  The
@@ -168,6 +169,7 @@ struct TplArgs {
     int64_t npad, n;
     float *eps, *hb;          // data sets: per-event outputs (npad values each)
     const float *w0;          // normalisation sets: weights as loaded
+    const float *tag;         // data sets: flavour tags (the stored phi is tag x observed phi), or null
     float *wout;              // normalisation sets: the weight record to rewrite
     TplDev t[4];              // efficiency x masses, x angles; background x masses, x angles
     double mB, mpsi, mK, mpi;
@@ -176,5 +178,9 @@ struct TplArgs {
     cudaStream_t stream;
 };
 cudaError_t launch_templates(const TplArgs &a);
+// Flavour-align the stored events: the phi-odd records of event e are multiplied
+// by old_tag[e] x new_tag[e] (null = all +1).
+cudaError_t launch_flavour(float *rec, int64_t npad, int64_t n, const float *old_tag,
+                           const float *new_tag, int has_z, int grid, cudaStream_t st);
 
 }  // namespace amp4d

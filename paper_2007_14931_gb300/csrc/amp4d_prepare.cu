@@ -186,7 +186,9 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_templates(TplArgs a)
     for (int64_t e = blockIdx.x * (int64_t)PREP_BLOCK + threadIdx.x; e < np;
          e += (int64_t)gridDim.x * PREP_BLOCK) {
         const double m = a.rec[REC_M * np + e], cK = a.rec[REC_CK * np + e];
-        const double cpsi = a.rec[REC_CPSI * np + e], phi = a.rec[REC_PHI * np + e];
+        const double cpsi = a.rec[REC_CPSI * np + e];
+        // the stored phi is flavour-aligned (t phi); the templates take the observed phi
+        const double phi = a.rec[REC_PHI * np + e] * (a.tag ? (double)a.tag[e] : 1.0);
         const double p = two_body(a.mB, m, a.mpsi), q = two_body(m, a.mK, a.mpi);
         const double ps = p * a.mB / m;
         const double Epsi = sqrt(a.mpsi * a.mpsi + ps * ps), Epi = sqrt(a.mpi * a.mpi + q * q);
@@ -214,6 +216,34 @@ __global__ void __launch_bounds__(PREP_BLOCK) k_templates(TplArgs a)
         for (int i = 0; i < PREP_BLOCK / 32; ++i) t += red[i];
         a.part[blockIdx.x] = t;
     }
+}
+
+// Flavour: multiply the phi-odd records (phi, sin phi and, with a Z, sin phi~ and
+// sin alpha) of each event by f = old tag x new tag (+1 or -1), so that the stored
+// event is the flavour-aligned one.  Padding events follow the last event.
+__global__ void __launch_bounds__(PREP_BLOCK) k_flavour(float *rec, int64_t npad, int64_t n,
+                                                        const float *old_tag, const float *new_tag,
+                                                        int has_z)
+{
+    for (int64_t e = blockIdx.x * (int64_t)PREP_BLOCK + threadIdx.x; e < npad;
+         e += (int64_t)gridDim.x * PREP_BLOCK) {
+        const int64_t es = e < n ? e : n - 1;
+        const float f = (old_tag ? old_tag[es] : 1.0f) * (new_tag ? new_tag[es] : 1.0f);
+        if (f > 0.0f) continue;
+        rec[REC_PHI * npad + e] = -rec[REC_PHI * npad + e];
+        rec[REC_SPHI * npad + e] = -rec[REC_SPHI * npad + e];
+        if (has_z) {
+            rec[REC_SPZ * npad + e] = -rec[REC_SPZ * npad + e];
+            rec[REC_SA * npad + e] = -rec[REC_SA * npad + e];
+        }
+    }
+}
+
+cudaError_t launch_flavour(float *rec, int64_t npad, int64_t n, const float *old_tag,
+                           const float *new_tag, int has_z, int grid, cudaStream_t st)
+{
+    k_flavour<<<grid, PREP_BLOCK, 0, st>>>(rec, npad, n, old_tag, new_tag, has_z);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_templates(const TplArgs &a)
