@@ -365,7 +365,12 @@ amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, 
  * 1.5 x the largest S p q of 2^20 scan candidates (stream 2) and doubles, with a
  * restart, if a candidate exceeds it.  Accepted events keep candidate order.
  * m, cK, cpsi, phi: DEVICE outputs of n floats (caller-owned).  Synchronises.
- * Errors: ARG, DOMAIN (S p q vanishes or the candidate budget is exhausted), CUDA, OOM.
+ * With Eq. 14 templates the density is the model's PDF instead:
+ * p q [P eps S / I_eps + (1 - P) hb / B] with a background (I_eps and B over the
+ * normalisation points, which must be set), p q eps S with an efficiency alone.
+ * Generated events are B0 (untagged).
+ * Errors: ARG, STATE (a background without normalisation points), DOMAIN
+ * (S p q vanishes or the candidate budget is exhausted), CUDA, OOM.
  */
 amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t seed, int64_t n,
                             float *m, float *cK, float *cpsi, float *phi, void *stream);

@@ -1142,6 +1142,28 @@ amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t s
     CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
                        cudaMemcpyHostToDevice, st));
     CK(enqueue_table(model, model->d_params, st));
+    // With Eq. 14 templates the events follow f = p q [P eps S / I_eps + (1 - P) hb / B]
+    // (without a background, p q eps S): the accept-reject weight becomes
+    // alpha eps S + beta hb, alpha = P / I_eps and beta = (1 - P) / B from the
+    // normalisation points.
+    const bool tpl = model->has_eff || model->has_bkg;
+    const bool mix = mixing(model);
+    double g_alpha = 1.0, g_beta = 0.0;
+    if (mix) {
+        if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "generate with a background needs normalisation points");
+        if (!(model->mc.whb > 0.0)) return fail(model, AMP4D_ERR_DOMAIN, "the background template is 0 over the normalisation points");
+        LaunchArgs ln = args_for(model, model->mc, model->mc.part, nullptr, st, model->mc.grid_eval);
+        CK(launch_eval(ln, 1));
+        unsigned long long a2[2];
+        CK(cudaMemcpyAsync(a2, model->d_acc + 2 * model->nslot, sizeof a2, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double T = (double)(long long)a2[0] + (double)a2[1] * 0x1p-64;
+        const double von = model->mc.volume / (double)model->mc.n;
+        const double Ie = von * T, Bn = von * model->mc.whb;
+        if (!(Ie > 0.0)) return fail(model, AMP4D_ERR_DOMAIN, "generate: I_eps <= 0");
+        g_alpha = model->purity / Ie;
+        g_beta = (1.0 - model->purity) / Bn;
+    }
     const int64_t B = 1 << 22, nscan = 1 << 20;
     const int nrec = model->nZ > 0 ? REC_NZ : REC_NK;
     const int nblk = (int)((B + gen_tile() - 1) / gen_tile());
@@ -1154,8 +1176,9 @@ amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t s
     double *part = nullptr;
     auto cleanup = [&]() {
         for (void *ptr : {(void *)g.rec, (void *)S, (void *)ua, (void *)cnt, (void *)flag, (void *)off,
-                          (void *)part})
+                          (void *)part, (void *)g.eps, (void *)g.hb})
             if (ptr) cudaFree(ptr);
+        g.eps = g.hb = nullptr;
     };
 #define CKG(call)                                                                          \
     do {                                                                                   \
@@ -1173,6 +1196,10 @@ amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t s
     CKG(cudaMalloc(&flag, 2 * sizeof(unsigned)));
     CKG(cudaMalloc(&off, (nblk + 1) * sizeof(unsigned long long)));
     CKG(cudaMalloc(&part, (size_t)model->nsm * 8 * sizeof(double)));
+    if (tpl) {
+        CKG(cudaMalloc(&g.eps, B * sizeof(float)));
+        CKG(cudaMalloc(&g.hb, B * sizeof(float)));
+    }
     // Evaluate S p q at count candidates of the given Philox stream starting at first.
     auto eval_batch = [&](uint64_t first, int64_t count, uint32_t sid, float *uacc) -> cudaError_t {
         cudaError_t e = launch_gen_candidates(g.rec, B, count, first, sid, seed, model->m_lo,
@@ -1187,7 +1214,20 @@ amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t s
         if (e != cudaSuccess) return e;
         g.n = count;
         LaunchArgs la = args_for(model, g, part, S, st, model->nsm * 8);
-        return launch_eval(la, 2);
+        e = launch_eval(la, 2);
+        if (e != cudaSuccess || !tpl) return e;
+        TplArgs t{};
+        t.rec = g.rec; t.npad = B; t.n = count; t.eps = g.eps; t.hb = g.hb;
+        for (int i = 0; i < 4; ++i) t.t[i] = model->tpl[i];
+        if (!model->has_eff) t.t[0].h = t.t[1].h = nullptr;
+        if (!model->has_bkg) t.t[2].h = t.t[3].h = nullptr;
+        t.mB = model->mass.mB; t.mpsi = model->mass.mpsi; t.mK = model->mass.mK; t.mpi = model->mass.mpi;
+        t.part = part;
+        t.grid = (int)std::min<int64_t>((count + prepare_block() - 1) / prepare_block(), model->nsm * 8);
+        t.stream = st;
+        e = launch_templates(t);
+        if (e != cudaSuccess) return e;
+        return launch_eq14_density(S, g.eps, mix ? g.hb : nullptr, count, g_alpha, g_beta, st);
     };
     // f_max: 1.5 x the largest S p q over the scan candidates (stream 2)
     CKG(cudaMemsetAsync(flag, 0, 2 * sizeof(unsigned), st));

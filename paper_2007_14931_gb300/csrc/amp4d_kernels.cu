@@ -583,6 +583,27 @@ __global__ void k_pdf_scale(const float *__restrict__ rec, int64_t npad, int64_t
     }
 }
 
+// Eq. 14 density without the phase-space factor, for the generator: S <- alpha eps S
+// + beta hb (hb null: beta = 0), in FP64 and rounded once.
+__global__ void k_eq14_density(float *__restrict__ S, const float *__restrict__ eps,
+                               const float *__restrict__ hb, int64_t n, double alpha, double beta)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double g = alpha * (double)eps[e] * (double)S[e];
+        if (hb) g += beta * (double)hb[e];
+        S[e] = (float)g;
+    }
+}
+
+cudaError_t launch_eq14_density(float *S, const float *eps, const float *hb, int64_t n, double alpha,
+                                double beta, cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_eq14_density<<<(int)std::max<int64_t>(1, blocks), 256, 0, s>>>(S, eps, hb, n, alpha, beta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double alpha, double beta,
                              const float *eps, const float *hb, float *S, cudaStream_t s)
 {

@@ -54,6 +54,9 @@ cudaError_t launch_grad(const LaunchArgs &a, bool norm);
 cudaError_t launch_lcache(const LaunchArgs &a, float2 *lc);
 cudaError_t launch_reduce_cols(const double *part, int nblk, int ncol, double *out,
                                cudaStream_t s);
+// Generator with Eq. 14 templates: S <- alpha eps S + beta hb per candidate.
+cudaError_t launch_eq14_density(float *S, const float *eps, const float *hb, int64_t n, double alpha,
+                                double beta, cudaStream_t s);
 cudaError_t launch_pdf_scale(const float *rec, int64_t npad, int64_t n, double alpha, double beta,
                              const float *eps, const float *hb, float *S, cudaStream_t s);
 cudaError_t launch_finish(const unsigned long long *ad, const unsigned long long *an, const int *slot_param,

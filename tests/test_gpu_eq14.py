@@ -189,3 +189,43 @@ def test_eq14_unavailable_calls(A):
     with pytest.raises(A.Amp4dError) as e:
         gm.set_efficiency(bad, ea)
     assert e.value.code == A.AMP4D_ERR_ARG
+
+
+def test_generator_follows_eq14(A):
+    """With templates, amp4d_generate draws from the Eq. 14 PDF: the events'
+    mean signal probability is P, and their m_Kpi and cos theta_psi histograms
+    match the oracle's expectation (uniform-point integration of f) by chi^2."""
+    name = "kstar10_2z"
+    cfg = W.CONFIGS[name]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    em, ea, bm, ba, P = W.eq14_templates(cfg.template_seed)
+    gm = A.Model(res, path=A.AMP4D_PATH_CACHED)
+    nm = W.uniform_points(1 << 20, cfg.norm_seed)
+    gm.set_norm_points(*_dev(nm))
+    gm.set_efficiency(em, ea)
+    gm.set_background(bm, ba, P)
+    n = 200_000
+    ev = tuple(t.cpu().numpy() for t in gm.generate(p, n, 77))
+    om = O.Model(res)
+    om.set_template(0, em, ea)
+    om.set_template(1, bm, ba, purity=P)
+    _, _, aux, rc = om.nll_eq14(p, ev, nm)
+    assert rc == 0
+    assert abs(aux[4] / n - P) < 4 * 0.5 / math.sqrt(n)
+    # expected marginals: f at fresh uniform points
+    u = W.uniform_points(1_000_000, 78)
+    S, pq = om.density(p, u)
+    eps, hb, _ = om.templates(u)
+    f = pq * (P * eps * S / aux[2] + (1 - P) * hb / aux[3])
+    for var, lo, hi, nb in ((0, W.M_LO, W.M_HI, 30), (2, -1.0, 1.0, 10)):
+        edges = np.linspace(lo, hi, nb + 1)
+        obs, _ = np.histogram(ev[var], edges)
+        wsum, _ = np.histogram(u[var], edges, weights=f)
+        w2, _ = np.histogram(u[var], edges, weights=f * f)
+        exp = n * wsum / wsum.sum()
+        var_exp = (n / wsum.sum()) ** 2 * w2   # Monte Carlo error of the expectation
+        ok = exp > 20
+        chi2 = np.sum((obs[ok] - exp[ok]) ** 2 / (exp[ok] + var_exp[ok]))
+        print("var %d: chi2 %.1f / %d" % (var, chi2, ok.sum()))
+        assert chi2 < ok.sum() + 5 * math.sqrt(2 * ok.sum())
