@@ -92,9 +92,8 @@ struct amp4d_model {
     bool has_eff = false, has_bkg = false;
     double purity = 1.0;
     bool eff_phi_even = true;    // the angular efficiency template is even in phi
-    double mistag = 0.0;         // flavour mistag fraction
     bool kstar_fixed = true;     // no K* has a floating mass or width
-    bool z_float = false;        // some Z has a floating mass and width
+    double mistag = 0.0;         // flavour mistag fraction
     // learned proposal
     float *d_th = nullptr, *d_am = nullptr, *d_av = nullptr;   // FP32 master weights, Adam moments
     __nv_bfloat16 *d_wb = nullptr;                              // BF16 weights
@@ -253,6 +252,9 @@ cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t 
 // Grid of the adjoint kernel over a set: one full wave of the variant that runs.
 int grad_grid(const amp4d_model *mo, const EventSet &s)
 {
+    // the all-cached kernel: two events per thread at GRAD_CTAS_PER_SM_CACHED, or one
+    // per thread at GRAD_CTAS_PER_SM_KFLOAT (= GRAD_CTAS_PER_SM) with floated K*
+    static_assert(GRAD_CTAS_PER_SM_KFLOAT == GRAD_CTAS_PER_SM, "one-event grid");
     const bool cached = mo->path == AMP4D_PATH_CACHED && s.lcache_valid && mo->kstar_fixed;
     return cached ? s.grid_grad_cached : s.grid_grad;
 }
@@ -277,7 +279,6 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.nslot = mo->nslot;
     a.all_fixed = mo->n_float == 0;
     a.kstar_fixed = mo->kstar_fixed;
-    a.z_float = mo->z_float;
     a.acc = (&s == &mo->ev) ? mo->d_acc : mo->d_acc + 2 * mo->nslot;
     a.mt = (&s == &mo->ev) && mo->mistag > 0.0;
     if (&s == &mo->ev && mo->has_bkg && mo->purity < 1.0 && s.eps && s.hb) {
@@ -712,7 +713,6 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
         if (r.float_mg) {
             model->res_fpos[i] = model->n_float++;
             if (r.chain == AMP4D_CHAIN_KSTAR) model->kstar_fixed = false;
-            else model->z_float = true;
         }
         if (r.chain == AMP4D_CHAIN_KSTAR) {
             if (r.J == 0) { model->col_res.push_back(i); model->col_lam.push_back(0); }

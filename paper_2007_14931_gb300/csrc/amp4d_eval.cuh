@@ -245,12 +245,13 @@ __device__ __forceinline__ float2 adj_w(const float2 (&as)[2], const float2 (&as
     return t;
 }
 
-// Evaluation of NE events at once when every K* lineshape comes from the basis
-// cache: the per-resonance constants are read once for all NE events.  r[j]
-// holds the records of event e[j]; lc is the basis cache [resonance][lcn].  ZF:
-// a Z resonance whose mass and width float is computed (Eq. 2-3) from the
-// Z-chain records, the others come from the cache.
-template <int NK, int NZ, int NE, bool ZF = false, bool MT = false>
+// Evaluation of NE events at once with the lineshapes of fixed resonances from
+// the basis cache: the per-resonance constants are read once for all NE events.
+// r[j] holds the records of event e[j]; lc is the basis cache [resonance][lcn].
+// LFM: which floated resonances have their lineshape computed per event (Eq.
+// 2-3) from the mass and momentum records instead of the cache: 0 none, 1 the
+// floated Z, 2 every floated resonance (K* and Z).
+template <int NK, int NZ, int NE, int LFM = 0, bool MT = false>
 __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
                                                EvState<NK, NZ> (&ev)[NE],
                                                const float2 *__restrict__ lc, int64_t lcn,
@@ -287,6 +288,12 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
         }
 #pragma unroll
         for (int l = 0; l < 3; ++l) u[j][l] = make_float2(0.f, 0.f);
+        if constexpr (LFM == 2) {
+            ev[j].m = r[j][REC_M];
+            ev[j].p = r[j][REC_P];
+            ev[j].q = r[j][REC_Q];
+            ev[j].invm = __frcp_rn(ev[j].m);
+        }
     }
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
@@ -294,6 +301,9 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             const ResDev &rs = md.res[k];
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
+                if constexpr (LFM == 2) {
+                    if (rs.fpos >= 0) LK[j][k] = lineshape(rs, ev[j].m, ev[j].invm, ev[j].p, ev[j].q).A;
+                }
                 float d0, d1;
                 wigner_l0(rs, cc[j], sK[j], d0, d1);
                 const float2 b0 = cscale(LK[j][k], d0), b1 = cscale(LK[j][k], d1);
@@ -340,7 +350,7 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
             wigner_1(ctz, stz, d1t[j]);
         }
-        if constexpr (ZF) {
+        if constexpr (LFM >= 1) {
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
                 ev[j].mZ = r[j][REC_MZ];
@@ -355,7 +365,7 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
                 float2 LA = LZ[j][z];
-                if constexpr (ZF) {
+                if constexpr (LFM >= 1) {
                     if (rs.fpos >= 0) LA = lineshape(rs, ev[j].mZ, ev[j].invmZ, ev[j].pZ, ev[j].qZ).A;
                 }
                 float dz0, dz1;
@@ -471,13 +481,14 @@ __device__ __forceinline__ bool data_term(const ModelDev &md, float S, const flo
 // MODE_WRITE: S per event to out.
 enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
 
-// Records read by eval_event<.., FX>: all of them, or without the masses and
-// momenta when every lineshape comes from the cache.
-template <bool FX, bool ZF = false>
+// Records read by the all-cached kernels (FX): all but phi (its cosine and sine
+// are records); the K* (Z) masses and momenta only when floated K* (Z)
+// lineshapes are computed per event (LFM 2, LFM >= 1).
+template <bool FX, int LFM = 0>
 __device__ __forceinline__ constexpr bool record_used(int k)
 {
-    return !FX || !(k == REC_M || k == REC_PHI || k == REC_P || k == REC_Q ||
-                    (!ZF && (k == REC_MZ || k == REC_PZ || k == REC_QZ)));
+    return !FX || !(k == REC_PHI || (LFM < 2 && (k == REC_M || k == REC_P || k == REC_Q)) ||
+                    (LFM < 1 && (k == REC_MZ || k == REC_PZ || k == REC_QZ)));
 }
 
 template <int NK, int NZ, int MODE, int BLOCK, bool FX, bool MIX = false, bool MT = false>
@@ -594,7 +605,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // e + stride, ... (each load of a warp stays coalesced).  The constants of a
 // resonance and each gradient slot pair are read once for the NE events.  An
 // event index beyond n repeats a valid event with zero weight.
-template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, bool ZF, bool MIX = false,
+template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, int LFM, bool MIX = false,
           bool MT = false>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
@@ -629,10 +640,10 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             e[j] = valid[j] ? ej : e0;
 #pragma unroll
             for (int k = 0; k < NREC; ++k)
-                v[j][k] = record_used<true, ZF>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
+                v[j][k] = record_used<true, LFM>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
         }
         EvState<NK, NZ> ev[NE];
-        eval_events_fx<NK, NZ, NE, ZF, MT>(md, v, ev, lc, npad, e);
+        eval_events_fx<NK, NZ, NE, LFM, MT>(md, v, ev, lc, npad, e);
         float2 as[NE][2], asb[NE][2];
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
@@ -681,6 +692,30 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                 }
                 g[(3 * k + l) * BLOCK] = gp;
             }
+            if constexpr (LFM == 2) {
+                const ResDev &rs = md.res[k];
+                if (rs.fpos >= 0) {
+                    // floated K*: y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
+                    float2 gmk = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < NE; ++j) {
+                        float d0, d1;
+                        wigner_l0(rs, make_float2(ev[j].cK, ev[j].cK), ev[j].sK, d0, d1);
+                        float2 y = make_float2(0.f, 0.f);
+                        cfma(y, md.kc[k][0], cscale(wl[j][0], -d1));
+                        cfma(y, md.kc[k][1], cscale(wl[j][1], d0));
+                        cfma(y, md.kc[k][2], cscale(wl[j][2], d1));
+                        const LineOut L = lineshape(rs, ev[j].m, ev[j].invm, ev[j].p, ev[j].q);
+                        float2 dM, dG;
+                        lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
+                        gmk.x += cmul(dM, y).x;
+                        gmk.y += cmul(dG, y).x;
+                    }
+                    float2 &gm = g[(3 * NK + 2 * NZ + rs.fpos) * BLOCK];
+                    gm.x += gmk.x;
+                    gm.y += gmk.y;
+                }
+            }
         }
         if constexpr (NZ > 0) {
 #pragma unroll
@@ -705,7 +740,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                     g0.y = fmaf(-A.x, w0.y, fmaf(-A.y, w0.x, g0.y));
                     g1.x = fmaf(A.x, w1.x, fmaf(-A.y, w1.y, g1.x));
                     g1.y = fmaf(-A.x, w1.y, fmaf(-A.y, w1.x, g1.y));
-                    if constexpr (ZF) {
+                    if constexpr (LFM >= 1) {
                         if (rs.fpos >= 0) {
                             // y = sum_l' c_l' w_l', then scale dS/dM = Re(dA/dM y)
                             float2 y = make_float2(0.f, 0.f);
@@ -721,7 +756,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                 }
                 g[(3 * NK + 2 * z) * BLOCK] = g0;
                 g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
-                if constexpr (ZF) {
+                if constexpr (LFM >= 1) {
                     if (rs.fpos >= 0) {
                         float2 &gm = g[(3 * NK + 2 * NZ + rs.fpos) * BLOCK];
                         gm.x += gmg.x;
@@ -929,18 +964,27 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
 {
     const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
     constexpr int EPT = GRAD_EVENTS_PER_THREAD_CACHED, CPS = GRAD_CTAS_PER_SM_CACHED;
+    constexpr int CPS1 = GRAD_CTAS_PER_SM_KFLOAT;
     const bool mix = !NORM && a.mix_eps != nullptr;
     if constexpr (FX) {
-        auto kern = a.z_float ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, true>
-                              : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, false>;
+        // lfm: 0 all lineshapes cached; 1 the floated Z computed per event (two events
+        // per thread); 2 floated K* too (one event per thread, for registers)
+        const int lfm = a.all_fixed ? 0 : (a.kstar_fixed ? 1 : 2);
+        using KernT = decltype(&k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0>);
+        KernT kern = lfm == 0 ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0>
+                   : lfm == 1 ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1>
+                              : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, 1, CPS1, 2>;
         if constexpr (!NORM) {
-            switch ((a.z_float ? 4 : 0) | (mix ? 2 : 0) | (a.mt ? 1 : 0)) {
-            case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, false, true>; break;
-            case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, true, false>; break;
-            case 3: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, false, true, true>; break;
-            case 5: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, false, true>; break;
-            case 6: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, true, false>; break;
-            case 7: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, true, true, true>; break;
+            switch (lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
+            case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, true>; break;
+            case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false>; break;
+            case 3: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, true>; break;
+            case 5: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 1, false, true>; break;
+            case 6: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 1, true, false>; break;
+            case 7: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 1, true, true>; break;
+            case 9: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, 1, CPS1, 2, false, true>; break;
+            case 10: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, 1, CPS1, 2, true, false>; break;
+            case 11: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, 1, CPS1, 2, true, true>; break;
             default: break;
             }
         }
@@ -977,7 +1021,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
 template <int NK, int NZ>
 cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
 {
-    const bool fx = a.lcache && a.kstar_fixed;
+    const bool fx = a.lcache != nullptr;
     if (norm) return fx ? launch_grad_k<NK, NZ, true, true>(a) : launch_grad_k<NK, NZ, true, false>(a);
     return fx ? launch_grad_k<NK, NZ, false, true>(a) : launch_grad_k<NK, NZ, false, false>(a);
 }

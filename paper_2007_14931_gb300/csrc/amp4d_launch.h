@@ -25,8 +25,7 @@ struct LaunchArgs {
     const float2 *lcache = nullptr;  // basis cache of the set, or null (recompute)
     int nslot = 0;                   // gradient slots (grad_num_slots)
     bool all_fixed = false;          // no mass or width floats (with lcache: all lineshapes cached)
-    bool kstar_fixed = false;        // no K* mass or width floats (with lcache: K* lineshapes cached)
-    bool z_float = false;            // some Z mass and width float
+    bool kstar_fixed = false;        // no K* mass or width floats
     // Eq. 14 with a background (data sets): eps and hb per event, and the
     // accumulator of the signal probabilities r = alpha eps S / g.
     const float *mix_eps = nullptr, *mix_hb = nullptr;
@@ -41,6 +40,9 @@ struct LaunchArgs {
 constexpr int GRAD_CTAS_PER_SM = 4;
 constexpr int GRAD_CTAS_PER_SM_CACHED = 3;
 constexpr int GRAD_EVENTS_PER_THREAD_CACHED = 2;
+// With floated K* lineshapes computed per event the all-cached kernel takes one
+// event per thread (the two-event form spills).
+constexpr int GRAD_CTAS_PER_SM_KFLOAT = 4;
 
 int nk_bucket(int nk);
 // Gradient slots: ln S (or w S), 6 per K* of the bucket, 4 per Z, and 2 (mass,

@@ -180,6 +180,9 @@ CONFIGS = {
     "large": Config("large", 4, ALL_KSTAR + ["Z(4430)"], 5_000_000, 1 << 24),
     "large_float_z": Config("large_float_z", 5, ALL_KSTAR + ["Z(4430)"], 5_000_000, 1 << 24,
                             float_mg=["Z(4430)"]),
+    # The benchmark model with the K*(892) and Z(4430) masses and widths floating.
+    "large_float_kz": Config("large_float_kz", 10, ALL_KSTAR + ["Z(4430)"], 5_000_000, 1 << 24,
+                             float_mg=["K*(892)", "Z(4430)"]),
     # Z-sensitivity model: both Z states, their masses and widths floating.
     "kstar10_2z": Config("kstar10_2z", 6, ALL_KSTAR + ["Z(4200)", "Z(4430)"], 200_000, 2_000_000,
                          float_mg=["Z(4200)", "Z(4430)"]),
