@@ -156,3 +156,33 @@ def test_toy_pull_distributions(A):
     print("toy pulls: mean", np.round(mean, 2), "sd", np.round(sd, 2))
     assert np.all(np.abs(mean) < 0.6)
     assert np.all((sd > 0.6) & (sd < 1.5))
+
+
+def test_z_sensitivity(A):
+    """Fit validation, Z sensitivity: events generated with the ten K* alone and
+    fitted with the ten K* + Z(4200) + Z(4430) model give Z fit fractions
+    consistent with zero (the paper finds about 0.01 %)."""
+    res_g = W.CONFIGS["kstar10"].resonances
+    res_f = W.CONFIGS["kstar10_2z"].resonances
+    assert [r.name for r in res_f[:len(res_g)]] == [r.name for r in res_g]
+    cols_g, cols_f = W.columns(res_g), W.columns(res_f)
+    fixed = [k for k, (R, l) in enumerate(cols_g) if res_g[R].name == "K*(892)" and l == 0][0]
+    c_g = W.draw_couplings(res_g, W.CONFIGS["kstar10"].coupling_seed)
+    c_g = c_g / c_g[fixed]
+    gen = A.Model(res_g)
+    ev = gen.generate(W.couplings_to_params(c_g), 200_000, 909)
+    nm = W.uniform_points(1 << 21, 910)
+    m = A.Model(res_f, path=A.AMP4D_PATH_CACHED)
+    m.set_events(*ev)
+    m.set_norm_points(*(torch.from_numpy(a).cuda() for a in nm))
+    nz = len(cols_f) - len(cols_g)
+    rng = np.random.default_rng(911)
+    c0 = np.concatenate([W.perturbed_start(c_g), 0.02 * np.exp(1j * rng.uniform(-np.pi, np.pi, nz))])
+    c0[fixed] = 1.0
+    par = F.Parametrization(len(c0), 0, fixed_col=fixed, polar=False)
+    r = F.fit(m.eval_nll_grad, par, W.couplings_to_params(c0), tol=0.1)
+    assert r.converged
+    ff = m.fit_fractions(par.to_params(r.theta))
+    ffz = ff[len(res_g):]
+    print("Z fit fractions on K*-only data: %s" % ", ".join("%.2e" % x for x in ffz))
+    assert np.all(ffz < 1e-3)
