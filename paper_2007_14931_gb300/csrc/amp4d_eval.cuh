@@ -262,13 +262,30 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
     float sK[NE];
     float2 u[NE][3];
     float2 LK[NE][NK], LZ[NE][NZ > 0 ? NZ : 1];
+    if constexpr (NE == 2) {
+        // events e[0] and e[0] + 1 (even e[0]): one 16-byte load per resonance
 #pragma unroll
-    for (int j = 0; j < NE; ++j) {
+        for (int k = 0; k < NK; ++k) {
+            const float4 t = k < nK ? __ldg(reinterpret_cast<const float4 *>(lc + k * lcn + e[0]))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            LK[0][k] = make_float2(t.x, t.y);
+            LK[1][k] = make_float2(t.z, t.w);
+        }
 #pragma unroll
-        for (int k = 0; k < NK; ++k)
-            LK[j][k] = k < nK ? __ldg(lc + k * lcn + e[j]) : make_float2(0.f, 0.f);
+        for (int z = 0; z < NZ; ++z) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(lc + (nK + z) * lcn + e[0]));
+            LZ[0][z] = make_float2(t.x, t.y);
+            LZ[1][z] = make_float2(t.z, t.w);
+        }
+    } else {
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) LZ[j][z] = __ldg(lc + (nK + z) * lcn + e[j]);
+        for (int j = 0; j < NE; ++j) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+                LK[j][k] = k < nK ? __ldg(lc + k * lcn + e[j]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) LZ[j][z] = __ldg(lc + (nK + z) * lcn + e[j]);
+        }
     }
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
@@ -303,6 +320,14 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             for (int j = 0; j < NE; ++j) {
                 if constexpr (LFM == 2) {
                     if (rs.fpos >= 0) LK[j][k] = lineshape(rs, ev[j].m, ev[j].invm, ev[j].p, ev[j].q).A;
+                }
+                if (rs.J == 0) {
+                    // d^0_00 = 1, no l = +-1 terms: the same bits as the general form
+                    const float2 b0 = LK[j][k];
+                    ev[j].B0[k] = b0;
+                    ev[j].B1[k] = make_float2(0.f, 0.f);
+                    cfma2p(u[j][1], md.kp[k][1], b0, make_float2(b0.y, b0.x));
+                    continue;
                 }
                 float d0, d1;
                 wigner_l0(rs, cc[j], sK[j], d0, d1);
@@ -628,19 +653,38 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     int esum = 0;
     bool bad = false;
     const int nK = md.n_res - NZ;
+    // NE = 2: thread t takes the adjacent events 2t and 2t + 1 of its stride
+    // (8-byte record loads; e0 is even and npad a multiple of 4, so e0 + 1 < npad
+    // holds a real or a padding event); otherwise events e0 + j * stride.
     const int64_t estride = (int64_t)gridDim.x * BLOCK;
-    for (int64_t e0 = blockIdx.x * (int64_t)BLOCK + tid; e0 < n; e0 += NE * estride) {
+    const int64_t first = NE == 2 ? 2 * (blockIdx.x * (int64_t)BLOCK + tid) : blockIdx.x * (int64_t)BLOCK + tid;
+    for (int64_t e0 = first; e0 < n; e0 += NE * estride) {
         int64_t e[NE];
         bool valid[NE];
         float v[NE][NREC];
+        if constexpr (NE == 2) {
+            e[0] = e0;
+            e[1] = e0 + 1;
+            valid[0] = true;
+            valid[1] = e0 + 1 < n;
 #pragma unroll
-        for (int j = 0; j < NE; ++j) {
-            const int64_t ej = e0 + j * estride;
-            valid[j] = ej < n;
-            e[j] = valid[j] ? ej : e0;
+            for (int k = 0; k < NREC; ++k) {
+                const float2 t = record_used<true, LFM>(k)
+                                     ? __ldg(reinterpret_cast<const float2 *>(rec + k * npad + e0))
+                                     : make_float2(0.f, 0.f);
+                v[0][k] = t.x;
+                v[1][k] = t.y;
+            }
+        } else {
 #pragma unroll
-            for (int k = 0; k < NREC; ++k)
-                v[j][k] = record_used<true, LFM>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
+            for (int j = 0; j < NE; ++j) {
+                const int64_t ej = e0 + j * estride;
+                valid[j] = ej < n;
+                e[j] = valid[j] ? ej : e0;
+#pragma unroll
+                for (int k = 0; k < NREC; ++k)
+                    v[j][k] = record_used<true, LFM>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
+            }
         }
         EvState<NK, NZ> ev[NE];
         eval_events_fx<NK, NZ, NE, LFM, MT>(md, v, ev, lc, npad, e);
@@ -680,8 +724,10 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             if (k >= nK) continue;
+            const bool j0 = md.res[k].J == 0;   // only the l = 0 slot moves (B1 = 0)
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
+                if (j0 && l != 1) continue;
                 float2 gp = g[(3 * k + l) * BLOCK];
 #pragma unroll
                 for (int j = 0; j < NE; ++j) {
