@@ -266,14 +266,14 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
         // events e[0] and e[0] + 1 (even e[0]): one 16-byte load per resonance
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
-            const float4 t = k < nK ? __ldg(reinterpret_cast<const float4 *>(lc + k * lcn + e[0]))
+            const float4 t = k < nK ? __ldcs(reinterpret_cast<const float4 *>(lc + k * lcn + e[0]))
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             LK[0][k] = make_float2(t.x, t.y);
             LK[1][k] = make_float2(t.z, t.w);
         }
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(lc + (nK + z) * lcn + e[0]));
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(lc + (nK + z) * lcn + e[0]));
             LZ[0][z] = make_float2(t.x, t.y);
             LZ[1][z] = make_float2(t.z, t.w);
         }
@@ -655,7 +655,9 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     const int nK = md.n_res - NZ;
     // NE = 2: thread t takes the adjacent events 2t and 2t + 1 of its stride
     // (8-byte record loads; e0 is even and npad a multiple of 4, so e0 + 1 < npad
-    // holds a real or a padding event); otherwise events e0 + j * stride.
+    // holds a real or a padding event); otherwise events e0 + j * stride.  The
+    // records and cached lineshapes are read once per launch: evict-first loads
+    // (ld.global.cs) keep them from displacing the small per-evaluation data in L2.
     const int64_t estride = (int64_t)gridDim.x * BLOCK;
     const int64_t first = NE == 2 ? 2 * (blockIdx.x * (int64_t)BLOCK + tid) : blockIdx.x * (int64_t)BLOCK + tid;
     for (int64_t e0 = first; e0 < n; e0 += NE * estride) {
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 #pragma unroll
             for (int k = 0; k < NREC; ++k) {
                 const float2 t = record_used<true, LFM>(k)
-                                     ? __ldg(reinterpret_cast<const float2 *>(rec + k * npad + e0))
+                                     ? __ldcs(reinterpret_cast<const float2 *>(rec + k * npad + e0))
                                      : make_float2(0.f, 0.f);
                 v[0][k] = t.x;
                 v[1][k] = t.y;
