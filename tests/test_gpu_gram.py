@@ -227,13 +227,14 @@ def test_fit_fractions_match_oracle(A, name):
     assert np.allclose(ff, ff_o, rtol=1e-7, atol=1e-10)
 
 
-@pytest.mark.parametrize("name", ["large_float_z", "kstar10_2z"])
+@pytest.mark.parametrize("name", ["large_float_z", "kstar10_2z", "large_float_kz"])
 def test_cached_path_floated_z_matches_oracle(A, name):
-    """K* fixed (lineshapes from the basis cache) and the Z masses and widths
-    floating: the two-events-per-thread kernel computes the Z lineshapes and
-    their mass/width adjoint per event, for the data and the per-point
-    normalisation.  NLL and full gradient (couplings, Z masses and widths)
-    against the oracle, at the start point and after the Z parameters move."""
+    """Fixed lineshapes from the basis cache and some masses and widths floating
+    (the Z; or K*(892) and the Z): the all-cached kernel computes the floated
+    lineshapes and their mass/width adjoint per event, for the data and the
+    per-point normalisation.  NLL and full gradient (couplings, masses and
+    widths) against the oracle, at the start point and after the floated masses
+    move."""
     cfg = W.CONFIGS[name]
     res = cfg.resonances
     fl = cfg.float_mg
@@ -248,7 +249,7 @@ def test_cached_path_floated_z_matches_oracle(A, name):
     nz = 2 * len(fl)
     for shift in (0.0, 0.02):
         pp = p.copy()
-        pp[-nz::2] += shift            # every floated Z mass
+        pp[-nz::2] += shift            # every floated mass
         nll_o, g_o, _, rc = om.nll(pp, ev, nm, grad=True)
         assert rc == 0
         nll, g = gm.eval_nll_grad(pp)
