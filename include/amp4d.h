@@ -234,7 +234,9 @@ amp4d_status amp4d_eval_nll_grad(amp4d_model *model, const double *params, doubl
 
 /*
  * The terms of the NLL: out[0] = sum_e ln S_e, out[1] = sum_e ln(p_e q_e),
- * out[2] = I, out[3] = number of data events (host, 4 doubles).
+ * out[2] = I, out[3] = number of data events (host, 4 doubles).  With an
+ * efficiency (Eq. 14) out[1] also holds sum_e ln eps_e and I is I_eps; with a
+ * background out[0] is sum_e ln(f_e / (p_e q_e)) and NLL = -2 (out[0] + out[1]).
  */
 amp4d_status amp4d_eval_terms(amp4d_model *model, const double *params, double *out,
                               void *stream);
@@ -263,7 +265,8 @@ amp4d_status amp4d_eval_pdf(amp4d_model *model, const double *params, float *pdf
  * amp4d_num_params doubles.  out: DEVICE memory of 6 + amp4d_num_params doubles
  * receiving [0] NLL (+inf on a domain error), [1] sum ln S, [2] sum ln(p q),
  * [3] I, [4] N, [5] status bits (1: S <= 0 / I <= 0, 2: invalid parameters),
- * [6 ..] the gradient (what = AMP4D_EVAL_NLL_GRAD).  Both buffers are owned by
+ * [6 ..] the gradient (what = AMP4D_EVAL_NLL_GRAD).  With Eq. 14 templates [1]
+ * to [3] change as described at amp4d_eval_terms.  Both buffers are owned by
  * the caller and must stay valid until the stream has executed the work.
  * Evaluations of one model must not overlap in time: they share the model's
  * partial-sum buffers.  Errors: ARG, STATE (no events), CUDA.
@@ -281,7 +284,10 @@ amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *para
  *       on the Gram path T = V (u^T G u + v^T G v)), [4] M (points),
  *   [5] status bits (1: S <= 0 at a data event, 2: invalid parameters),
  *   [6 .. 6+P) d(sum ln S)/dtheta, [6+P .. 6+2P) dT/dtheta  (what = NLL_GRAD),
- * P = amp4d_num_params.  No logarithm of I is taken per shard.
+ * P = amp4d_num_params.  No logarithm of I is taken per shard.  With an
+ * efficiency (Eq. 14) [1] also holds sum ln eps and T uses the efficiency-
+ * weighted points; with a background the call returns STATE (the data sum needs
+ * the union's I first).
  * amp4d_eval_partials: params and out are HOST memory (6 or 6 + 2P doubles),
  * synchronous.  amp4d_enqueue_partials: params and out are DEVICE memory owned
  * by the caller, enqueued on the stream without synchronising, with the same
