@@ -229,3 +229,36 @@ def test_generator_follows_eq14(A):
         chi2 = np.sum((obs[ok] - exp[ok]) ** 2 / (exp[ok] + var_exp[ok]))
         print("var %d: chi2 %.1f / %d" % (var, chi2, ok.sum()))
         assert chi2 < ok.sum() + 5 * math.sqrt(2 * ok.sum())
+
+
+def test_efficiency_shards_combine_to_the_union(A):
+    """With an efficiency alone the shard partials carry sum ln eps and the
+    efficiency-weighted T; combined they give the single model's evaluation."""
+    from paper_2007_14931_gb300.shard import shard_range
+    cfg = W.CONFIGS["kstar10_z"]
+    res = cfg.resonances
+    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    em, ea, _, _, _ = W.eq14_templates(cfg.template_seed)
+    ev = W.peaked_points(30_001, 5, res)
+    nm = W.uniform_points(80_003, 6)
+
+    def model(e, n):
+        m = A.Model(res, path=A.AMP4D_PATH_CACHED)
+        m.set_efficiency(em, ea)
+        m.set_events(*_dev(e))
+        m.set_norm_points(*_dev(n))
+        return m
+    whole = model(ev, nm)
+    nll_w, g_w = whole.eval_nll_grad(p)
+    parts = []
+    for r in range(3):
+        a, b = shard_range(len(ev[0]), r, 3)
+        c, d = shard_range(len(nm[0]), r, 3)
+        parts.append(model(tuple(x[a:b] for x in ev), tuple(x[c:d] for x in nm)).eval_partials(p))
+    nll, g, out = A.combine_partials(np.stack(parts))
+    assert abs(nll - nll_w) < 1e-4
+    assert np.max(np.abs(g - g_w)) <= 1e-6 * np.max(np.abs(g_w))
+    om = O.Model(res)
+    om.set_template(0, em, ea)
+    nll_o, _, _, rc = om.nll_eq14(p, ev, nm)
+    assert rc == 0 and abs(nll - nll_o) < 1e-3
