@@ -289,6 +289,58 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
     dll = learned[1][0].theta - learned[0][0].theta
     dll[1:nph:2] = (dll[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
     spread_l = (V.T @ dll) * np.sqrt(lam / 2.0)
+    # A proposal aimed at the whole Gram matrix rather than at S: trained on the
+    # mixture sum_k |B_k|^2 p q (per-column samples mixed by the Gram diagonal).
+    m.set_norm_points(*(torch.from_numpy(a).cuda() for a in nm))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.proposal_train_gram(p_true, n=1 << 20, seed=12)
+    torch.cuda.synchronize()
+    t_train_g = time.perf_counter() - t0
+    gram_t = []
+    for sd in (201, 202):
+        pts, w = m.proposal_sample(cfg.n_norm, sd)
+        m.set_norm_points(*pts, w=w, volume=1.0)
+        rg = F.fit(m.eval_nll_grad, par, p0, tol=tol)
+        dg = rg.theta - par.from_params(p_true)
+        dg[1:nph:2] = (dg[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
+        gram_t.append((rg, dg))
+    pg = [(V.T @ dg) * np.sqrt(lam / 2.0) for _, dg in gram_t]
+    dgg = gram_t[1][0].theta - gram_t[0][0].theta
+    dgg[1:nph:2] = (dgg[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
+    spread_g = (V.T @ dgg) * np.sqrt(lam / 2.0)
+    gram_out = {"proposal_train_s": t_train_g,
+                "converged": [bool(rg.converged) for rg, _ in gram_t],
+                "rms_pull_vs_truth": [float(np.sqrt(np.mean(x ** 2))) for x in pg],
+                "max_abs_pull_vs_truth": [float(np.max(np.abs(x))) for x in pg],
+                "rms_shift_between_normalisation_samples": float(np.sqrt(np.mean(spread_g ** 2))),
+                "note": "proposal trained on sum_k |B_k|^2 p q (per-column samples mixed by G_kk)"}
+    # Hessian-free measures on the likelihood of the first uniform sample (f = -2 ln L):
+    # the sum of squared pulls of a minimum against the truth is f(truth) - f(min),
+    # and the squared distance between two minima a, b in units of the errors is
+    # 2 [f(a) + f(b) - 2 f((a + b) / 2)] (exact for a quadratic f), each per free
+    # parameter.  Unlike the eigen-direction pulls they do not depend on the
+    # finite-difference HESSE matrix.
+    m.set_norm_points(*(torch.from_numpy(a).cuda() for a in nm))
+
+    def f_at(th):
+        return m.eval_nll(par.to_params(th))
+
+    def midpoint(a, b):
+        dd = b - a
+        dd[1:nph:2] = (dd[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
+        return a + 0.5 * dd
+
+    def shift_chi2(a, b):
+        return 2.0 * (f_at(a) + f_at(b) - 2.0 * f_at(midpoint(a, b))) / par.n_free
+
+    th_true = par.from_params(p_true)
+    chi2 = {"truth_vs_uniform_fit": (f_at(th_true) - f_at(r.theta)) / par.n_free,
+            "uniform_sample_shift": shift_chi2(r.theta, r2.theta),
+            "learned_S_sample_shift": shift_chi2(learned[0][0].theta, learned[1][0].theta),
+            "gram_targeted_sample_shift": shift_chi2(gram_t[0][0].theta, gram_t[1][0].theta),
+            "note": "per free parameter, on the first uniform sample's likelihood; 1 is one "
+                    "standard deviation per parameter"}
     learned_out = {"proposal_train_s": t_train,
                    "converged": [bool(rl.converged) for rl, _ in learned],
                    "rms_pull_vs_truth": [float(np.sqrt(np.mean(x ** 2))) for x in pl],
@@ -304,6 +356,8 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
             "rms_shift_between_normalisation_samples": float(np.sqrt(np.mean(spread ** 2))),
             "events_over_points": cfg.n_events / cfg.n_norm,
             "learned_normalisation": learned_out,
+            "gram_targeted_normalisation": gram_out,
+            "chi2_per_free_parameter": chi2,
             "note": "GPU closure fit: MIGRAD-style variable metric with the analytic adjoint gradient, "
                     "HESSE (re-run from the HESSE matrix until its EDM is below tolerance); pulls in "
                     "units of the statistical error along the Hessian directions the data constrain; "

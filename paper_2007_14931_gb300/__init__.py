@@ -432,6 +432,28 @@ class Model:
                                          C.byref(cfg), int(seed), C.byref(loss), _stream_ptr(stream)))
         return loss.value
 
+    def proposal_train_gram(self, params, n=1 << 20, seed=12, gen_seed=5000, **kw):
+        """Train the proposal toward the whole normalisation Gram matrix: the
+        target density sum_k |B_k|^2 p q, drawn column by column (the model with a
+        unit coupling at column k has density |B_k|^2 p q) in proportion to the
+        Gram diagonal G_kk over the current normalisation points.  params gives the
+        masses and widths (its couplings are not used).  Returns the training loss."""
+        import torch
+        p = self._params(params)
+        self.build_gram(p)
+        G = self.get_gram()
+        K = self.n_cols
+        gdiag = np.array([G[2 * k, 2 * k] + G[2 * k + 1, 2 * k + 1] for k in range(K)])
+        n_k = np.maximum(1, np.round(n * gdiag / gdiag.sum())).astype(int)
+        pieces = []
+        for k in range(K):
+            pk = np.zeros_like(p)
+            pk[2 * k] = 1.0
+            pk[2 * K:] = p[2 * K:]
+            pieces.append(self.generate(pk, int(n_k[k]), gen_seed + k))
+        events = tuple(torch.cat([pc[i] for pc in pieces]) for i in range(4))
+        return self.proposal_train(events, seed=seed, **kw)
+
     def proposal_sample(self, n, seed, stream=None):
         """n importance-sampled points and weights w = p q / q (device float32 tensors)."""
         import torch
