@@ -626,10 +626,12 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
     }
 }
 
-// All-cached adjoint kernel with NE events per thread and iteration: event e and
-// e + stride, ... (each load of a warp stays coalesced).  The constants of a
-// resonance and each gradient slot pair are read once for the NE events.  An
-// event index beyond n repeats a valid event with zero weight.
+// All-cached adjoint kernel with NE events per thread and iteration (NE = 2: an
+// adjacent pair 2t, 2t + 1; NE = 1: one event), every warp load coalesced.  The
+// constants of a resonance and each gradient slot pair are read once for the NE
+// events.  An event index at or beyond n holds a padding or repeated event that
+// gets zero weight.  LFM selects which floated lineshapes are computed per event
+// (eval_events_fx), MIX the Eq. 14 background, MT the flavour mistag.
 template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, int LFM, bool MIX = false,
           bool MT = false>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
