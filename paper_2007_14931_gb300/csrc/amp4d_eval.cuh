@@ -321,8 +321,9 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
                 if constexpr (LFM == 2) {
                     if (rs.fpos >= 0) LK[j][k] = lineshape(rs, ev[j].m, ev[j].invm, ev[j].p, ev[j].q).A;
                 }
-                if (rs.J == 0) {
+                if (NE == 2 && rs.J == 0) {
                     // d^0_00 = 1, no l = +-1 terms: the same bits as the general form
+                    // (with one event per thread the branch costs more than it saves)
                     const float2 b0 = LK[j][k];
                     ev[j].B0[k] = b0;
                     ev[j].B1[k] = make_float2(0.f, 0.f);
@@ -728,7 +729,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             if (k >= nK) continue;
-            const bool j0 = md.res[k].J == 0;   // only the l = 0 slot moves (B1 = 0)
+            const bool j0 = NE == 2 && md.res[k].J == 0;   // only the l = 0 slot moves (B1 = 0)
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
                 if (j0 && l != 1) continue;
