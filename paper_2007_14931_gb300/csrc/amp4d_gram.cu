@@ -204,6 +204,36 @@ __device__ __forceinline__ void for_each_basis(const ModelDev &md, const float *
     }
 }
 
+// The same basis values with both muon helicities of a column together:
+// fn(column, B'_c,+1, B'_c,-1).
+template <int NK, int NZ, typename F>
+__device__ __forceinline__ void for_each_basis_pair(const ModelDev &md, const float *r, F &&fn)
+{
+    EvState<NK, NZ> ev;
+    eval_event<NK, NZ>(md, r, ev);
+    const int nK = md.n_res - NZ;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        if (k >= nK) continue;
+        const ResDev &rs = md.res[k];
+        const float2 Bl[3] = {make_float2(-ev.B1[k].x, -ev.B1[k].y), ev.B0[k], ev.B1[k]};
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            if (rs.J == 0 && l != 1) continue;
+            const int col = rs.J == 0 ? rs.col : rs.col + l;
+            fn(col, cmul(Bl[l], ev.Psi[l][0]), cmul(Bl[l], ev.Psi[l][1]));
+        }
+    }
+    if constexpr (NZ > 0) {
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) {
+            const ResDev &rs = md.zr[z];
+            if (rs.zcol0 >= 0) fn(rs.zcol0, cmul(ev.AZ[z], ev.Om0[z][0]), cmul(ev.AZ[z], ev.Om0[z][1]));
+            if (rs.zcol1 >= 0) fn(rs.zcol1, cmul(ev.AZ[z], ev.Om1[z][0]), cmul(ev.AZ[z], ev.Om1[z][1]));
+        }
+    }
+}
+
 template <int NREC>
 __device__ __forceinline__ void load_point(const float *__restrict__ rec, int64_t npad, int64_t e,
                                            float v[NREC])
@@ -260,6 +290,27 @@ __device__ __forceinline__ void store_digits_int(uint8_t *tile, int ci, int k, i
 __device__ __forceinline__ void store_digits(uint8_t *tile, int ci, int k, float x, float s)
 {
     store_digits_int(tile, ci, k, __float2int_rn(x * s));
+}
+
+// The digits of two values at k and k + 1 (k even: adjacent 2-byte slots of one
+// 4-byte word), one 32-bit store per digit; the same digits as store_digits.
+__device__ __forceinline__ void store_digits2(uint8_t *tile, int ci, int k, float x0, float x1, float s)
+{
+    const int X[2] = {__float2int_rn(x0 * s), __float2int_rn(x1 * s)};
+    int dg[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int d1 = (X[i] + (1 << 23)) >> 24;
+        const int r1 = X[i] - (d1 << 24);
+        const int d2 = (r1 + (1 << 15)) >> 16;
+        const int r2 = r1 - (d2 << 16);
+        const int d3 = (r2 + 128) >> 8;
+        dg[i][0] = d1; dg[i][1] = d2; dg[i][2] = d3; dg[i][3] = r2 - (d3 << 8);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<__nv_bfloat162 *>(tile + tile_off(a * 64 + ci, k)) =
+            __floats2bfloat162_rn((float)dg[0][a], (float)dg[1][a]);
 }
 
 __device__ __forceinline__ long long rshift_round(long long v, int s)
@@ -320,6 +371,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     if (warp < 4) {
         // ------------------------------------------------------------ producers
         int64_t it = 0;  // chunk iteration of this CTA
+        float vn[NREC];  // records of the next point, loaded one round ahead
+        float wn = 0.f;
+        int64_t next_e = -1;
+        bool have_next = false;
         for (int64_t c = blockIdx.x; c < nchunks && !*abort_flag; c += gridDim.x, ++it) {
             for (int rnd = 0; rnd < GT_CHUNK_POINTS / GT_PROD && !*abort_flag; ++rnd) {
                 const int j = rnd * GT_PROD + tid;             // point within chunk
@@ -335,12 +390,27 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
                         for (int ci = 0; ci < 64; ++ci)
                             store_digits_int(tile, ci, k0 + x, __ldg(synth + (e * 2 + x) * 64 + ci));
                 } else if (e < n) {
+                    // this point's records were loaded one round ahead (below)
+                    if (!have_next || next_e != e) {
+                        load_point<NREC>(rec, npad, e, vn);
+                        wn = __ldg(rec + wrec * npad + e);
+                    }
                     float v[NREC];
-                    load_point<NREC>(rec, npad, e, v);
-                    const float sw = sqrtf(__ldg(rec + wrec * npad + e));
-                    for_each_basis<NK, NZ>(md, v, [&](int col, int x, float2 b) {
-                        store_digits(tile, 2 * col, k0 + x, b.x * sw, S.scale[2 * col]);
-                        store_digits(tile, 2 * col + 1, k0 + x, b.y * sw, S.scale[2 * col + 1]);
+#pragma unroll
+                    for (int q = 0; q < NREC; ++q) v[q] = vn[q];
+                    const float sw = sqrtf(wn);
+                    // prefetch the records of this thread's next point
+                    const int jn = j + GT_PROD;
+                    const int64_t cn = jn < GT_CHUNK_POINTS ? c : c + gridDim.x;
+                    next_e = cn * GT_CHUNK_POINTS + (jn < GT_CHUNK_POINTS ? jn : jn - GT_CHUNK_POINTS);
+                    have_next = next_e < n;
+                    if (have_next) {
+                        load_point<NREC>(rec, npad, next_e, vn);
+                        wn = __ldg(rec + wrec * npad + next_e);
+                    }
+                    for_each_basis_pair<NK, NZ>(md, v, [&](int col, float2 b0, float2 b1) {
+                        store_digits2(tile, 2 * col, k0, b0.x * sw, b1.x * sw, S.scale[2 * col]);
+                        store_digits2(tile, 2 * col + 1, k0, b0.y * sw, b1.y * sw, S.scale[2 * col + 1]);
                     });
                 } else {
                     for (int ci = 0; ci < (SYNTH ? 64 : 2 * ncol); ++ci)
