@@ -155,8 +155,8 @@ amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const flo
 
 /*
  * Binned 2D template (efficiency and background of Eq. 14).  h: nx * ny FP32
- * contents, h[iy * nx + ix] (host or device memory; copied by the setters, the
- * caller keeps ownership).  The content at (x, y) is that of the bin
+ * contents, finite and >= 0, h[iy * nx + ix] (host or device memory; copied by
+ * the setters, the caller keeps ownership; ARG otherwise).  The content at (x, y) is that of the bin
  * ix = floor((x - x_lo) * nx / (x_hi - x_lo)), iy likewise, evaluated in FP64 in
  * that order; the upper edge belongs to the last bin and the template is 0
  * outside [x_lo, x_hi] x [y_lo, y_hi].
@@ -190,9 +190,8 @@ amp4d_status amp4d_set_efficiency(amp4d_model *model, const amp4d_hist2d *mass,
  * weights as loaded.  With a background (P < 1) each evaluation computes I_eps
  * before the data pass (the Gram quadratic form, or the point sum first).  The
  * NLL is -2 sum ln f; in the evaluation outputs "sum ln S" becomes
- * sum ln(f / (p q)) and I is I_eps.  Shard partials and fit fractions are not
- * available with a background (STATE); fit fractions need a model without an
- * efficiency too (they are defined on S).  mass = angle = NULL removes it.
+ * sum ln(f / (p q)) and I is I_eps.  Shard partials are not available with a
+ * background (STATE).  mass = angle = NULL removes it.
  * Synchronous.  Errors: ARG, CUDA, OOM.
  */
 amp4d_status amp4d_set_background(amp4d_model *model, const amp4d_hist2d *mass,
@@ -346,8 +345,11 @@ amp4d_status amp4d_get_gram(amp4d_model *model, double *G, void *stream);
  * to one (interference).  Computed from the normalisation Gram matrix, built at
  * params when a mass or width floats or none is valid yet (which synchronises).
  * params: host, amp4d_num_params doubles; ff: host, one double per resonance in
- * the order given to amp4d_model_create.  Errors: ARG, STATE (no points),
- * DOMAIN (I <= 0), TIMEOUT, CUDA.
+ * the order given to amp4d_model_create.  With Eq. 14 templates the fractions
+ * are still those of S: the Gram is built over the points' weights as loaded
+ * (without the efficiency), and the efficiency-weighted normalisation is rebuilt
+ * on the next evaluation.  Errors: ARG, STATE (no points), DOMAIN (I <= 0),
+ * TIMEOUT, CUDA.
  */
 amp4d_status amp4d_fit_fractions(amp4d_model *model, const double *params, double *ff, void *stream);
 

@@ -621,6 +621,18 @@ amp4d_status set_template_pair(amp4d_model *model, int t0, const amp4d_hist2d *m
             !std::isfinite(h->x_hi) || !std::isfinite(h->y_lo) || !std::isfinite(h->y_hi))
             return fail(model, AMP4D_ERR_ARG, "bad template (null contents, bins or ranges)");
     }
+    // contents must be finite and >= 0 (an efficiency or a density)
+    for (int j = 0; j < 2; ++j) {
+        const amp4d_hist2d *h = src[j];
+        std::vector<float> c((size_t)h->nx * h->ny);
+        CK(cudaMemcpy(c.data(), h->h, c.size() * sizeof(float), cudaMemcpyDefault));
+        for (size_t i = 0; i < c.size(); ++i)
+            if (!(c[i] >= 0.0f) || !std::isfinite(c[i])) {
+                char buf[96];
+                std::snprintf(buf, sizeof buf, "template bin %zu is negative or not finite", i);
+                return fail(model, AMP4D_ERR_ARG, buf);
+            }
+    }
     for (int j = 0; j < 2; ++j) {
         const amp4d_hist2d *h = src[j];
         const int t = t0 + j;
@@ -1038,18 +1050,28 @@ amp4d_status amp4d_fit_fractions(amp4d_model *model, const double *params, doubl
 {
     if (!model || !params || !ff) return AMP4D_ERR_ARG;
     if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "set_norm_points must come first");
-    if (model->has_eff || model->has_bkg)
-        return fail(model, AMP4D_ERR_STATE,
-                    "fit fractions are defined on S: use a model without efficiency or background");
-    // The Gram matrix at these masses and widths (fixed-mass models reuse it).
-    if (model->n_float > 0 || !model->gram_valid) {
-        const amp4d_status rc = amp4d_build_gram(model, params, stream);
-        if (rc) return rc;
-    } else {
-        const amp4d_status rc = check_params(model, params);
-        if (rc) return rc;
-    }
     cudaStream_t st = (cudaStream_t)stream;
+    // Fit fractions are defined on S over phase space.  With an efficiency the
+    // weight record holds w0 eps: the Gram for them is built over the weights as
+    // loaded (w0), and the efficiency-weighted record is restored afterwards (the
+    // evaluation Gram is then rebuilt on the next evaluation).
+    const bool unweight = model->has_eff && model->mc.w0;
+    float *wrec = model->mc.rec + (size_t)model->mc.wrec * model->mc.npad;
+    const size_t wbytes = (size_t)model->mc.npad * sizeof(float);
+    if (unweight) {
+        CK(cudaMemcpyAsync(wrec, model->mc.w0, wbytes, cudaMemcpyDeviceToDevice, st));
+        model->gram_valid = false;
+    }
+    // The Gram matrix at these masses and widths (fixed-mass models reuse it).
+    amp4d_status rc0 = AMP4D_OK;
+    if (model->n_float > 0 || !model->gram_valid) rc0 = amp4d_build_gram(model, params, stream);
+    else rc0 = check_params(model, params);
+    if (unweight) {
+        const amp4d_status rc1 = apply_templates(model, model->mc, true, st);   // w0 eps again
+        model->gram_valid = false;
+        if (rc0 == AMP4D_OK) rc0 = rc1;
+    }
+    if (rc0) return rc0;
     const int K = model->n_col, dim = 2 * K;
     std::vector<double> G((size_t)dim * dim), kap(model->n_param);
     CK(cudaMemcpyAsync(G.data(), model->d_G, G.size() * sizeof(double), cudaMemcpyDeviceToHost, st));

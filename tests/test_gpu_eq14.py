@@ -178,9 +178,6 @@ def test_eq14_unavailable_calls(A):
     with pytest.raises(A.Amp4dError) as e:
         gm.eval_partials(p)
     assert e.value.code == A.AMP4D_ERR_STATE
-    with pytest.raises(A.Amp4dError) as e:
-        gm.fit_fractions(p)
-    assert e.value.code == A.AMP4D_ERR_STATE
     em, ea, bm, ba, _ = W.eq14_templates(1)
     with pytest.raises(A.Amp4dError) as e:
         gm.set_background(bm, ba, 1.5)
@@ -189,6 +186,12 @@ def test_eq14_unavailable_calls(A):
     with pytest.raises(A.Amp4dError) as e:
         gm.set_efficiency(bad, ea)
     assert e.value.code == A.AMP4D_ERR_ARG
+    for v in (-0.1, float("nan"), float("inf")):
+        h = em.h.copy()
+        h[3, 4] = v
+        with pytest.raises(A.Amp4dError) as e:
+            gm.set_efficiency(W.Hist2D(h, em.range), ea)
+        assert e.value.code == A.AMP4D_ERR_ARG
 
 
 def test_generator_follows_eq14(A):
@@ -262,3 +265,20 @@ def test_efficiency_shards_combine_to_the_union(A):
     om.set_template(0, em, ea)
     nll_o, _, _, rc = om.nll_eq14(p, ev, nm)
     assert rc == 0 and abs(nll - nll_o) < 1e-3
+
+
+@pytest.mark.parametrize("path", ["plain", "cached"])
+def test_fit_fractions_with_templates_are_those_of_S(A, path):
+    """Fit fractions (Eq. 13) are defined on S: with efficiency and background
+    set they equal, bit for bit, those of a model without templates on the same
+    points, and the Eq. 14 evaluation afterwards is unchanged."""
+    pth = A.AMP4D_PATH_PLAIN if path == "plain" else A.AMP4D_PATH_CACHED
+    res, p, om, gm, ev, nm = _case(A, "kstar10_2z", pth, float_names=[])
+    nll0, g0 = gm.eval_nll_grad(p)
+    ff = gm.fit_fractions(p)
+    plain = A.Model(res, path=pth)
+    plain.set_events(*_dev(ev))
+    plain.set_norm_points(*_dev(nm))
+    assert np.array_equal(ff, plain.fit_fractions(p))
+    nll1, g1 = gm.eval_nll_grad(p)
+    assert nll1 == nll0 and np.array_equal(g1, g0)
