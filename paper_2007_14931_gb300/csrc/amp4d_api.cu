@@ -878,12 +878,20 @@ amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mist
             }
         if (cudaMalloc(&nt, (size_t)s.n * sizeof(float)) != cudaSuccess)
             return fail(model, AMP4D_ERR_OOM, "tag allocation failed");
-        CK(cudaMemcpy(nt, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+        const cudaError_t e = cudaMemcpy(nt, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(nt);
+            return fail(model, AMP4D_ERR_CUDA, std::string("set_flavour: ") + cudaGetErrorString(e));
+        }
     }
     if (s.n > 0 && (s.tag || nt)) {
         const int grid = (int)std::min<int64_t>((s.npad + prepare_block() - 1) / prepare_block(), model->nsm * 8);
-        CK(launch_flavour(s.rec, s.npad, s.n, s.tag, nt, model->nZ > 0, grid, st));
-        CK(cudaStreamSynchronize(st));
+        cudaError_t e = launch_flavour(s.rec, s.npad, s.n, s.tag, nt, model->nZ > 0, grid, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            if (nt) cudaFree(nt);
+            return fail(model, AMP4D_ERR_CUDA, std::string("set_flavour: ") + cudaGetErrorString(e));
+        }
     }
     if (s.tag) cudaFree(s.tag);
     s.tag = nt;
