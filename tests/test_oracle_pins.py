@@ -517,6 +517,30 @@ def test_one_normalisation_serves_both_flavours():
     assert abs(I_u - I_m) < 4 * math.sqrt(2) * sem
 
 
+def test_phi_even_efficiency_keeps_one_normalisation():
+    """With an efficiency even in phi, int eps S(-phi) p q = int eps S(phi) p q:
+    over a phi-mirrored point sample the efficiency-weighted sums of the two
+    flavours' densities are equal; with an efficiency odd-skewed in phi they
+    differ.  This is why tags and a mistag share I_eps only for a phi-even
+    efficiency."""
+    res, p, _, _, _ = _flavour_case()
+    em, ea, _, _, _ = W.eq14_templates(15)
+    u = W.uniform_points(50_000, 46)
+    both = tuple(np.concatenate([a, b]) for a, b in zip(u, (u[0], u[1], u[2], -u[3])))
+    mirrored = (both[0], both[1], both[2], -both[3])
+    for ang, even in ((_phi_even(ea), True), (ea, False)):
+        mo = O.Model(res)
+        mo.set_template(0, em, ang)
+        eps, _, _ = mo.templates(both)
+        S, pq = mo.density(p, both)
+        Sm, _ = mo.density(p, mirrored)
+        a, b = np.sum(eps * S * pq), np.sum(eps * Sm * pq)
+        if even:
+            assert a == pytest.approx(b, rel=1e-12)
+        else:
+            assert abs(a / b - 1) > 1e-4
+
+
 def test_flavour_gradient_matches_central_differences():
     res, p, ev, nm, tag = _flavour_case("kstar10_z", 400, 800)
     fl = ["K*(892)", "Z(4430)"]
