@@ -433,12 +433,12 @@ amp4d_status amp4d_grid_sample(const float *gcell, const int *nb, double alpha, 
  * are DEVICE memory; out is DEVICE memory of 4546 doubles receiving the
  * gradient of the KL objective and then its value (same arithmetic as
  * amp4d_mlp_loss_grad).  All are caller-owned.  The call is stream-ordered and
- * does not synchronise; it allocates nothing: its scratch (about 1.2 MB) is a
+ * does not synchronise; it allocates nothing: its scratch (about 2.3 MB) is a
  * file-scope device array that every GPU which loads the library holds until
  * the process exits.  nd and nu must not exceed AMP4D_NOALLOC_MAX_ROWS, else
- * AMP4D_ERR_ARG.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) for the device; make that first call before
- * any stream capture.  Every call uses the same array, so calls whose work
+ * AMP4D_ERR_ARG.  Each call looks up that array's device address in the
+ * current context (cudaGetSymbolAddress); the first call on a device may load
+ * the library's device code there, so make it before any stream capture.  Every call uses the same array, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race: order them on
  * one stream.  amp4d_noalloc_last_error describes the last failure.
  */

@@ -85,7 +85,29 @@ def mlp_loss_grad(theta, xd, xu, stream=None):
 
 def mlp_loss_grad_noalloc(theta_dev, xd, xu, out_dev, stream=None):
     """Allocation-free KL gradient: all arguments are torch cuda tensors; out_dev (4546
-    float64) receives the gradient and then the loss.  Stream-ordered, no sync."""
+    float64) receives the gradient and then the loss.  Stream-ordered, no sync.
+
+    The C entry point sees only raw pointers, so every tensor is checked here and a
+    mismatch raises ValueError; nothing is converted or copied, since a copy would
+    allocate."""
+    import torch
+
+    def need(ok, what):
+        if not ok:
+            raise ValueError("mlp_loss_grad_noalloc: " + what)
+
+    ts = {"theta_dev": theta_dev, "xd": xd, "xu": xu, "out_dev": out_dev}
+    for k, t in ts.items():
+        need(isinstance(t, torch.Tensor) and t.is_cuda, "%s must be a CUDA tensor" % k)
+        need(t.is_contiguous(), "%s must be contiguous" % k)
+    need(len({t.device for t in ts.values()}) == 1, "all tensors must be on one device")
+    need(theta_dev.dtype == torch.float32 and theta_dev.numel() == MLP_NUM_PARAMS,
+         "theta_dev must hold %d float32" % MLP_NUM_PARAMS)
+    for k, x in (("xd", xd), ("xu", xu)):
+        need(x.dtype == torch.float32 and x.dim() == 2 and x.shape[1] == 4,
+             "%s must be float32 of shape (n, 4)" % k)
+    need(out_dev.dtype == torch.float64 and out_dev.numel() >= MLP_NUM_PARAMS + 1,
+         "out_dev must hold at least %d float64" % (MLP_NUM_PARAMS + 1))
     rc = amp4d_mlp_loss_grad_noalloc(theta_dev.data_ptr(), xd.data_ptr(), xd.shape[0],
                                      xu.data_ptr(), xu.shape[0], out_dev.data_ptr(),
                                      _stream_ptr(stream))

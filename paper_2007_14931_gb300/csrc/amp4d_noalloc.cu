@@ -9,47 +9,40 @@
 // every GPU that loads the library holds until the process exits, and the
 // entry point below takes only caller-owned inputs and outputs.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_bf16.h>
 
 #include "../../include/amp4d.h"
 #include "amp4d_launch.h"
+#include "amp4d_mlp.cuh"
 
 namespace amp4d {
 
 namespace {
 
-constexpr int NA_MLP_P = 4545;
-constexpr int NA_ROWS_PER_BLOCK = 128;
-constexpr int NA_MAX_BLOCKS = 2 * (AMP4D_NOALLOC_MAX_ROWS / NA_ROWS_PER_BLOCK);
-constexpr size_t NA_PART_FLOATS = (size_t)NA_MAX_BLOCKS * (NA_MLP_P + 1);   // multiple of 64
-constexpr size_t NA_SCRATCH_FLOATS = NA_PART_FLOATS + (NA_MLP_P + 1) / 2 + 64;
+// At most one CTA per MLP_GRAD_TILE rows of each set, one partial row each.
+constexpr int NA_MAX_BLOCKS = 2 * ((AMP4D_NOALLOC_MAX_ROWS + MLP_GRAD_TILE - 1) / MLP_GRAD_TILE);
+constexpr size_t NA_PART_FLOATS = (size_t)NA_MAX_BLOCKS * (MLP_P + 1);   // multiple of 64
+static_assert(NA_PART_FLOATS % 64 == 0, "the BF16 weights start 256-byte aligned");
+constexpr size_t NA_SCRATCH_FLOATS = NA_PART_FLOATS + (MLP_P + 1) / 2 + 64;
 
 // Partial sums (NA_MAX_BLOCKS x 4546 floats), then the BF16 weights.
 static __device__ __align__(256) float g_noalloc_scratch[NA_SCRATCH_FLOATS];
 
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_na_mutex;
-void *g_na_addr[NA_MAX_DEVICES] = {};
 thread_local const char *g_na_error = "";
 
-// Device address of the scratch array on the current device, looked up once per
-// device (host code cannot use the symbol itself as a device pointer).
+// Device address of the scratch array in the current context.  Host code cannot
+// use the symbol itself as a device pointer.  The address is looked up on every
+// call rather than cached: a context that was reset and re-created reloads the
+// module, and a cached address would then point into freed memory.  The lookup
+// is a host-side query that neither allocates nor synchronises once the module
+// is loaded (the first call on a device may load it).
 cudaError_t scratch_address(float **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_addr[dev] = p;
-    }
-    *out = static_cast<float *>(g_na_addr[dev]);
+    *out = static_cast<float *>(p);
     return cudaSuccess;
 }
 
@@ -70,6 +63,10 @@ extern "C" amp4d_status amp4d_mlp_loss_grad_noalloc(const float *theta, const fl
     if (nd < 1 || nu < 1 || nd > AMP4D_NOALLOC_MAX_ROWS || nu > AMP4D_NOALLOC_MAX_ROWS) {
         g_na_error = "mlp_loss_grad_noalloc: nd and nu must lie in [1, AMP4D_NOALLOC_MAX_ROWS = 4096]"
                      " (the size of the static scratch)";
+        return AMP4D_ERR_ARG;
+    }
+    if (mlp_grad_blocks(nd, nu) > NA_MAX_BLOCKS) {
+        g_na_error = "mlp_loss_grad_noalloc: the gradient kernel needs more partial rows than the static scratch holds";
         return AMP4D_ERR_ARG;
     }
     float *scratch = nullptr;

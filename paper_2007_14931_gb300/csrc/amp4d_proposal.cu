@@ -23,6 +23,7 @@
 
 #include "amp4d_device.cuh"
 #include "amp4d_launch.h"
+#include "amp4d_mlp.cuh"
 
 namespace amp4d {
 
@@ -209,190 +210,7 @@ cudaError_t launch_gen_scatter(const float *rec, int64_t npad, int64_t n, const 
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// MLP: parameter layout W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3.
-// ---------------------------------------------------------------------------
-constexpr int MH = 64;
-constexpr int MLP_P = MH * 4 + MH + MH * MH + MH + MH + 1;  // 4545
-constexpr int OFF_B1 = MH * 4, OFF_W2 = OFF_B1 + MH, OFF_B2 = OFF_W2 + MH * MH;
-constexpr int OFF_W3 = OFF_B2 + MH, OFF_B3 = OFF_W3 + MH;
-
-__device__ __forceinline__ float softplusf_(float o) { return o > 20.0f ? o : log1pf(expf(o)); }
-__device__ __forceinline__ float sigmoidf_(float o) { return 1.0f / (1.0f + expf(-o)); }
-
-// Block-wide copy of the BF16 weights into shared memory as FP32.
-__device__ __forceinline__ void load_weights(const __nv_bfloat16 *__restrict__ wb, float *ws)
-{
-    for (int i = threadIdx.x; i < MLP_P; i += blockDim.x) ws[i] = __bfloat162float(wb[i]);
-    __syncthreads();
-}
-
-struct MlpAct {
-    float h1[MH], h2[MH], o, g;
-};
-
-__device__ __forceinline__ void mlp_forward(const float *ws, const float x[4], MlpAct &a)
-{
-#pragma unroll 8
-    for (int i = 0; i < MH; ++i) {
-        float z = ws[OFF_B1 + i];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) z = fmaf(ws[i * 4 + k], x[k], z);
-        a.h1[i] = tanhf(z);
-    }
-#pragma unroll 4
-    for (int i = 0; i < MH; ++i) {
-        float z = ws[OFF_B2 + i];
-#pragma unroll
-        for (int j = 0; j < MH; ++j) z = fmaf(ws[OFF_W2 + i * MH + j], a.h1[j], z);
-        a.h2[i] = tanhf(z);
-    }
-    float o = ws[OFF_B3];
-#pragma unroll
-    for (int j = 0; j < MH; ++j) o = fmaf(ws[OFF_W3 + j], a.h2[j], o);
-    a.o = o;
-    a.g = softplusf_(o);
-}
-
-// g(x) for n points x (n x 4, row-major in [-1, 1]^4).
-__global__ void __launch_bounds__(128) k_mlp_forward(const __nv_bfloat16 *__restrict__ wb,
-                                                     const float *__restrict__ x, int64_t n,
-                                                     float *__restrict__ g)
-{
-    extern __shared__ float ws[];
-    load_weights(wb, ws);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const float xv[4] = {x[4 * e], x[4 * e + 1], x[4 * e + 2], x[4 * e + 3]};
-        MlpAct a;
-        mlp_forward(ws, xv, a);
-        g[e] = a.g;
-    }
-}
-
-// Cell-centre values of the grid: cell c = ((i0 nb1 + i1) nb2 + i2) nb3 + i3.
-__global__ void __launch_bounds__(128) k_mlp_grid(const __nv_bfloat16 *__restrict__ wb, int nb0,
-                                                  int nb1, int nb2, int nb3, float *__restrict__ g)
-{
-    extern __shared__ float ws[];
-    load_weights(wb, ws);
-    const int64_t nc = (int64_t)nb0 * nb1 * nb2 * nb3;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = c;
-        const int i3 = (int)(r % nb3); r /= nb3;
-        const int i2 = (int)(r % nb2); r /= nb2;
-        const int i1 = (int)(r % nb1); r /= nb1;
-        const int i0 = (int)r;
-        const float xv[4] = {-1.0f + (2.0f * i0 + 1.0f) / nb0, -1.0f + (2.0f * i1 + 1.0f) / nb1,
-                             -1.0f + (2.0f * i2 + 1.0f) / nb2, -1.0f + (2.0f * i3 + 1.0f) / nb3};
-        MlpAct a;
-        mlp_forward(ws, xv, a);
-        g[c] = a.g;
-    }
-}
-
-// Gradient of the KL objective, per block of MLP_TB points (data blocks first).
-// Per point: forward, dO = coef sigmoid(o) (coef = -1/(nd g) for data, 1 for
-// uniform points), backward deltas; then block sums of the outer products.
-// part[b][0..4544] = gradient contribution, [4545] = sum ln g (data) or sum g.
-constexpr int MLP_TB = 128;
-
-__global__ void __launch_bounds__(MLP_TB) k_mlp_grad(const __nv_bfloat16 *__restrict__ wb,
-                                                     const float *__restrict__ xd, int64_t nd,
-                                                     const float *__restrict__ xu, int64_t nu,
-                                                     int nblk_d, float *__restrict__ part)
-{
-    extern __shared__ float sm[];
-    float *ws = sm;                               // MLP_P
-    float *X = ws + MLP_P + 3;                    // [MLP_TB][4]
-    float *H1 = X + MLP_TB * 4;                   // [MLP_TB][MH]
-    float *H2 = H1 + MLP_TB * MH;
-    float *D2 = H2 + MLP_TB * MH;
-    float *D1 = D2 + MLP_TB * MH;
-    float *DO = D1 + MLP_TB * MH;                 // [MLP_TB]
-    float *LS = DO + MLP_TB;                      // [MLP_TB]
-    load_weights(wb, ws);
-    const bool data = blockIdx.x < nblk_d;
-    const int64_t p = (data ? (int64_t)blockIdx.x : (int64_t)(blockIdx.x - nblk_d)) * MLP_TB + threadIdx.x;
-    const int64_t np = data ? nd : nu;
-    const float *xs = data ? xd : xu;
-    const int t = threadIdx.x;
-    if (p < np) {
-        const float xv[4] = {xs[4 * p], xs[4 * p + 1], xs[4 * p + 2], xs[4 * p + 3]};
-        MlpAct a;
-        mlp_forward(ws, xv, a);
-        const float coef = data ? -1.0f / ((float)nd * a.g) : 1.0f;
-        const float dO = coef * sigmoidf_(a.o);
-        for (int k = 0; k < 4; ++k) X[t * 4 + k] = xv[k];
-        for (int j = 0; j < MH; ++j) {
-            H1[t * MH + j] = a.h1[j];
-            H2[t * MH + j] = a.h2[j];
-            D2[t * MH + j] = dO * ws[OFF_W3 + j] * (1.0f - a.h2[j] * a.h2[j]);
-        }
-        for (int j = 0; j < MH; ++j) {
-            float s = 0.0f;
-            for (int i = 0; i < MH; ++i) s = fmaf(ws[OFF_W2 + i * MH + j], D2[t * MH + i], s);
-            D1[t * MH + j] = s * (1.0f - a.h1[j] * a.h1[j]);
-        }
-        DO[t] = dO;
-        LS[t] = data ? logf(a.g) : a.g;
-    } else {
-        for (int k = 0; k < 4; ++k) X[t * 4 + k] = 0.0f;
-        for (int j = 0; j < MH; ++j) H1[t * MH + j] = H2[t * MH + j] = D2[t * MH + j] = D1[t * MH + j] = 0.0f;
-        DO[t] = 0.0f;
-        LS[t] = 0.0f;
-    }
-    __syncthreads();
-    float *out = part + (int64_t)blockIdx.x * (MLP_P + 1);
-    for (int q = t; q < MLP_P + 1; q += MLP_TB) {
-        float s = 0.0f;
-        if (q < OFF_B1) {                 // W1[j][k] = sum D1[j] X[k]
-            const int j = q / 4, k = q % 4;
-            for (int r = 0; r < MLP_TB; ++r) s = fmaf(D1[r * MH + j], X[r * 4 + k], s);
-        } else if (q < OFF_W2) {          // b1
-            const int j = q - OFF_B1;
-            for (int r = 0; r < MLP_TB; ++r) s += D1[r * MH + j];
-        } else if (q < OFF_B2) {          // W2[i][j] = sum D2[i] H1[j]
-            const int i = (q - OFF_W2) / MH, j = (q - OFF_W2) % MH;
-            for (int r = 0; r < MLP_TB; ++r) s = fmaf(D2[r * MH + i], H1[r * MH + j], s);
-        } else if (q < OFF_W3) {          // b2
-            const int i = q - OFF_B2;
-            for (int r = 0; r < MLP_TB; ++r) s += D2[r * MH + i];
-        } else if (q < OFF_B3) {          // W3[j] = sum dO H2[j]
-            const int j = q - OFF_W3;
-            for (int r = 0; r < MLP_TB; ++r) s = fmaf(DO[r], H2[r * MH + j], s);
-        } else if (q == OFF_B3) {
-            for (int r = 0; r < MLP_TB; ++r) s += DO[r];
-        } else {                          // sum ln g (data) or sum g (uniform)
-            for (int r = 0; r < MLP_TB; ++r) s += LS[r];
-        }
-        out[q] = s;
-    }
-}
-
-// grad = sum over data blocks + (sum over uniform blocks) / S_u; loss terms.
-// out: grad[MLP_P] (FP64), then [MLP_P] = loss.
-__global__ void k_mlp_grad_finish(const float *__restrict__ part, int nblk_d, int nblk_u,
-                                  int64_t nd, int64_t nu, double *__restrict__ out)
-{
-    __shared__ double su_sh;
-    if (threadIdx.x == 0) {
-        double su = 0.0, sl = 0.0;
-        for (int b = 0; b < nblk_u; ++b) su += part[(int64_t)(nblk_d + b) * (MLP_P + 1) + MLP_P];
-        for (int b = 0; b < nblk_d; ++b) sl += part[(int64_t)b * (MLP_P + 1) + MLP_P];
-        su_sh = su;
-        out[MLP_P] = -sl / (double)nd + log(16.0 * su / (double)nu);
-    }
-    __syncthreads();
-    const double su = su_sh;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < MLP_P; q += gridDim.x * blockDim.x) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < nblk_d; ++k) a += part[(int64_t)k * (MLP_P + 1) + q];
-        for (int k = 0; k < nblk_u; ++k) b += part[(int64_t)(nblk_d + k) * (MLP_P + 1) + q];
-        out[q] = a + b / su;
-    }
-}
+// The MLP kernels (forward, grid, KL gradient) are in amp4d_mlp.cu.
 
 // One Adam step on the FP32 master weights, refreshing the BF16 copy.
 __global__ void k_adam(float *__restrict__ th, float *__restrict__ m, float *__restrict__ v,
@@ -543,45 +361,6 @@ __global__ void k_grid_sample(const double *__restrict__ cdf, int nb0, int nb1, 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-int mlp_num_params() { return MLP_P; }
-
-cudaError_t launch_mlp_forward(const __nv_bfloat16 *wb, const float *x, int64_t n, float *g,
-                               cudaStream_t st)
-{
-    const size_t smem = MLP_P * sizeof(float);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, 152 * 8));
-    k_mlp_forward<<<grid, 128, smem, st>>>(wb, x, n, g);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_grid(const __nv_bfloat16 *wb, const int nb[4], float *g, cudaStream_t st)
-{
-    const size_t smem = MLP_P * sizeof(float);
-    const int64_t nc = (int64_t)nb[0] * nb[1] * nb[2] * nb[3];
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nc + 127) / 128, 152 * 8));
-    k_mlp_grid<<<grid, 128, smem, st>>>(wb, nb[0], nb[1], nb[2], nb[3], g);
-    return cudaGetLastError();
-}
-
-size_t mlp_grad_smem() { return (MLP_P + 3 + MLP_TB * 4 + 4 * MLP_TB * MH + 2 * MLP_TB) * sizeof(float); }
-
-cudaError_t launch_mlp_grad(const __nv_bfloat16 *wb, const float *xd, int64_t nd, const float *xu,
-                            int64_t nu, float *part, double *out, cudaStream_t st)
-{
-    const int nbd = (int)((nd + MLP_TB - 1) / MLP_TB), nbu = (int)((nu + MLP_TB - 1) / MLP_TB);
-    const size_t smem = mlp_grad_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_mlp_grad<<<nbd + nbu, MLP_TB, smem, st>>>(wb, xd, nd, xu, nu, nbd, part);
-    k_mlp_grad_finish<<<(MLP_P + 255) / 256, 256, 0, st>>>(part, nbd, nbu, nd, nu, out);
-    return cudaGetLastError();
-}
-
-int mlp_grad_blocks(int64_t nd, int64_t nu)
-{
-    return (int)((nd + MLP_TB - 1) / MLP_TB + (nu + MLP_TB - 1) / MLP_TB);
-}
-
 cudaError_t launch_adam(float *th, float *m, float *v, const double *grad, float lr, float b1,
                         float b2, float eps, int64_t t, __nv_bfloat16 *wb, cudaStream_t st)
 {

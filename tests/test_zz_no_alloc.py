@@ -48,3 +48,41 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(A):
     with pytest.raises(A.Amp4dError) as e:
         A.mlp_loss_grad_noalloc(torch.from_numpy(th).cuda(), xd, xu, out)
     assert e.value.code == A.AMP4D_ERR_ARG and "4096" in str(e.value)
+
+
+def test_noalloc_back_to_back_calls_share_the_scratch_in_stream_order(A):
+    """Two calls with different inputs enqueued on one stream with no synchronisation
+    between them reuse the same static scratch: stream order alone must keep them
+    apart.  A loop of further calls must leave the device's free memory unchanged."""
+    inputs = [_inputs(seed, nd, nu) for seed, nd, nu in [(5, 777, 1500), (6, 2048, 333)]]
+    refs = [A.mlp_loss_grad(th, xd, xu) for th, xd, xu in inputs]
+    ths = [torch.from_numpy(th).cuda() for th, _, _ in inputs]
+    outs = [torch.full((4546,), float("nan"), dtype=torch.float64, device="cuda") for _ in inputs]
+    st = torch.cuda.current_stream()
+    A.mlp_loss_grad_noalloc(ths[0], inputs[0][1], inputs[0][2], outs[0], stream=st)   # warm-up
+    torch.cuda.synchronize()
+    for out in outs:
+        out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for th, (_, xd, xu), out in zip(ths, inputs, outs):
+            A.mlp_loss_grad_noalloc(th, xd, xu, out, stream=st)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    for out, (ref_loss, ref_grad) in zip(outs, refs):
+        o = out.cpu().numpy()
+        assert o[-1] == pytest.approx(ref_loss, rel=1e-12, abs=1e-12)
+        assert np.allclose(o[:-1], ref_grad, rtol=1e-12, atol=1e-12 * np.max(np.abs(ref_grad)))
+
+
+def test_noalloc_binding_rejects_tensors_the_abi_cannot_check(A):
+    th, xd, xu = _inputs(7, 64, 64)
+    thd = torch.from_numpy(th).cuda()
+    out = torch.zeros(4546, dtype=torch.float64, device="cuda")
+    wide = torch.zeros((64, 6), dtype=torch.float32, device="cuda")
+    for args in [(thd.double(), xd, xu, out), (thd, wide[:, :4], xu, out), (thd, xd, xu, out[:100]),
+                 (thd, xd, xu, out.float()), (thd, xd.cpu(), xu, out), (thd[:-1], xd, xu, out)]:
+        with pytest.raises(ValueError):
+            A.mlp_loss_grad_noalloc(*args)
