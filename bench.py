@@ -148,8 +148,8 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) per data event of the cached adjoint kernel, from one
-# ncu capture of the current kernel on 4e6 events of the same model
-# (profiles/k_grad_cached_kstar10_z_4M_events.md: 512.19 MB read + 3.23 MB written).
+# ncu capture of the current kernel on 4e6 events of the same model (512.19 MB
+# read + 3.23 MB written).
 # Scaled by events to the launch; None when the kernel has changed since.
 K_GRAD_DRAM_BYTES_PER_EVENT = (512.193536e6 + 3.225344e6) / 4e6
 

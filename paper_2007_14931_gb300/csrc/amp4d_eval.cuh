@@ -245,6 +245,31 @@ __device__ __forceinline__ float2 adj_w(const float2 (&as)[2], const float2 (&as
     return t;
 }
 
+// Adjoint factors of a floated resonance's lineshape, with the double-float
+// couplings (each low part inside its product, as in the coherent sum): for a
+// K* k, y = sum_l c'_{k,l} d_l w_l, where the l = -1 basis factor is -A d1 and
+// kp[k][0] holds -c'_{k,-1}; for a Z z, y = sum_l' c'_{z,l'} w_l'.  A coupling
+// rounded to FP32 would leave a relative error of up to 2^-24 in y that differs
+// between the data events and the normalisation points (their angular
+// distributions differ), so it would not cancel in the mass and width gradient.
+__device__ __forceinline__ float2 kstar_adj_y(const ModelDev &md, int k, float d0, float d1,
+                                              const float2 (&wl)[3])
+{
+    const float2 t0 = cscale(wl[0], d1), t1 = cscale(wl[1], d0), t2 = cscale(wl[2], d1);
+    float2 y = make_float2(0.f, 0.f);
+    cfma2p(y, md.kp[k][0], t0, make_float2(t0.y, t0.x));
+    cfma2p(y, md.kp[k][1], t1, make_float2(t1.y, t1.x));
+    cfma2p(y, md.kp[k][2], t2, make_float2(t2.y, t2.x));
+    return y;
+}
+__device__ __forceinline__ float2 z_adj_y(const ModelDev &md, const ResDev &rs, int z, float2 w0, float2 w1)
+{
+    float2 y = make_float2(0.f, 0.f);
+    if (rs.zcol0 >= 0) cfma2p(y, md.zp[z][0], w0, make_float2(w0.y, w0.x));
+    if (rs.zcol1 >= 0) cfma2p(y, md.zp[z][1], w1, make_float2(w1.y, w1.x));
+    return y;
+}
+
 // Evaluation of NE events at once with the lineshapes of fixed resonances from
 // the basis cache: the per-resonance constants are read once for all NE events.
 // r[j] holds the records of event e[j]; lc is the basis cache [resonance][lcn].
@@ -610,15 +635,20 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
         for (int ww = 0; ww < BLOCK / 32; ++ww) t += red[ww];
         acc128_add(acc, t, status);
     }
-    // Block sums of every gradient slot, in thread order, as compensated FP32
-    // (Neumaier) sums written once in FP64: the FP32 slot values are summed to
-    // about 2^-48 of sum |x| without the FP64 pipe, which on this GPU runs at a
-    // small fraction of the FP32 rate.
+    // Block sums of every gradient slot as compensated FP32 (Neumaier) sums
+    // written once in FP64: the FP32 slot values are summed to about 2^-48 of
+    // sum |x| without the FP64 pipe, which on this GPU runs at a small fraction of
+    // the FP32 rate.  Thread s sums slot s over the threads j in the rotated
+    // order (j + pair index) mod BLOCK: the 16 pairs and 2 components a warp reads
+    // at once then sit in 32 different banks (in thread order every read of a
+    // warp fell into 2 banks, 16-way conflicts).  The order is fixed per slot.
+    static_assert((BLOCK & (BLOCK - 1)) == 0, "BLOCK is a power of two");
     for (int s2 = 1 + tid; s2 < nslot; s2 += BLOCK) {
         const float *col = reinterpret_cast<const float *>(gsl + ((s2 - 1) >> 1) * BLOCK) + ((s2 - 1) & 1);
+        const int rot = (s2 - 1) >> 1;
         float sm = 0.f, cm = 0.f;
         for (int j = 0; j < BLOCK; ++j) {
-            const float x = col[2 * j];
+            const float x = col[2 * ((j + rot) & (BLOCK - 1))];
             const float t = sm + x;
             cm += (fabsf(sm) >= fabsf(x)) ? (sm - t) + x : (x - t) + sm;
             sm = t;
@@ -752,10 +782,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                     for (int j = 0; j < NE; ++j) {
                         float d0, d1;
                         wigner_l0(rs, make_float2(ev[j].cK, ev[j].cK), ev[j].sK, d0, d1);
-                        float2 y = make_float2(0.f, 0.f);
-                        cfma(y, md.kc[k][0], cscale(wl[j][0], -d1));
-                        cfma(y, md.kc[k][1], cscale(wl[j][1], d0));
-                        cfma(y, md.kc[k][2], cscale(wl[j][2], d1));
+                        const float2 y = kstar_adj_y(md, k, d0, d1, wl[j]);
                         const LineOut L = lineshape(rs, ev[j].m, ev[j].invm, ev[j].p, ev[j].q);
                         float2 dM, dG;
                         lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
@@ -794,9 +821,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                     if constexpr (LFM >= 1) {
                         if (rs.fpos >= 0) {
                             // y = sum_l' c_l' w_l', then scale dS/dM = Re(dA/dM y)
-                            float2 y = make_float2(0.f, 0.f);
-                            if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
-                            if (rs.zcol1 >= 0) cfma(y, md.zc[z][1], w1);
+                            const float2 y = z_adj_y(md, rs, z, w0, w1);
                             const LineOut L = lineshape(rs, ev[j].mZ, ev[j].invmZ, ev[j].pZ, ev[j].qZ);
                             float2 dM, dG;
                             lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
@@ -912,10 +937,7 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
                 // y = sum_l c_{k,l} d_l w_l, then scale dS/dM = Re(dA/dM y)
                 float d0, d1;
                 wigner_l0(rs, make_float2(ev.cK, ev.cK), ev.sK, d0, d1);
-                float2 y = make_float2(0.f, 0.f);
-                cfma(y, md.kc[k][0], cscale(wl[0], -d1));
-                cfma(y, md.kc[k][1], cscale(wl[1], d0));
-                cfma(y, md.kc[k][2], cscale(wl[2], d1));
+                const float2 y = kstar_adj_y(md, k, d0, d1, wl);
                 const LineOut L = lineshape(rs, ev.m, ev.invm, ev.p, ev.q);
                 float2 dM, dG;
                 lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
@@ -948,9 +970,7 @@ __global__ void __launch_bounds__(BLOCK, GRAD_CTAS_PER_SM) k_grad(const float *_
                 g[(3 * NK + 2 * z) * BLOCK] = g0;
                 g[(3 * NK + 2 * z + 1) * BLOCK] = g1;
                 if (rs.fpos >= 0) {
-                    float2 y = make_float2(0.f, 0.f);
-                    if (rs.zcol0 >= 0) cfma(y, md.zc[z][0], w0);
-                    if (rs.zcol1 >= 0) cfma(y, md.zc[z][1], w1);
+                    const float2 y = z_adj_y(md, rs, z, w0, w1);
                     const LineOut L = lineshape(rs, ev.mZ, ev.invmZ, ev.pZ, ev.qZ);
                     float2 dM, dG;
                     lineshape_derivs(rs, L.A, L.invD, L.MG, dM, dG);
