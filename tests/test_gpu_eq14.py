@@ -3,7 +3,7 @@
 The templates are seeded 2D Bernstein shapes binned over the two mass variables
 and the two angles (the paper's generic real-life shapes), with the purity of
 its real-life test (85 %).  Tolerances are those of the signal-only parity tests:
-|dNLL| < 1e-3, gradient <= 1e-5 |g|_inf, I relative 1e-8, per-event PDF
+|dNLL| < 1e-3, gradient <= 1e-6 |g|_inf, I relative 1e-8, per-event PDF
 relative 2e-5 where the interference is well conditioned."""
 import math
 
@@ -15,6 +15,10 @@ pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
+
+# Gradient parity bound: every component within 1e-6 |g|_inf of the oracle's
+# gradient (the scope table's "absolute <= 1e-6 |g|_inf" form).
+GRAD_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -94,7 +98,7 @@ def test_eq14_nll_grad_parity(A, path, name, fl):
     assert abs(nll - nll_o) < 1e-3
     assert t[2] == pytest.approx(aux[2], rel=1e-8)      # I_eps
     assert t[1] == pytest.approx(aux[1], rel=1e-12)     # sum ln(p q)
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
     # NLL-only kernels and a second parameter point
     assert gm.eval_nll(p) == pytest.approx(nll, abs=1e-4)
     p2 = p.copy()
@@ -102,7 +106,7 @@ def test_eq14_nll_grad_parity(A, path, name, fl):
     nll2_o, g2_o, _, _ = om.nll_eq14(p2, ev, nm, grad=True)
     nll2, g2 = gm.eval_nll_grad(p2)
     assert abs(nll2 - nll2_o) < 1e-3
-    assert np.max(np.abs(g2 - g2_o)) <= 1e-5 * np.max(np.abs(g2_o))
+    assert np.max(np.abs(g2 - g2_o)) <= GRAD_TOL * np.max(np.abs(g2_o))
 
 
 @pytest.mark.parametrize("path", ["plain", "cached"])
@@ -115,7 +119,7 @@ def test_efficiency_only(A, path):
     assert rc == 0
     nll, g = gm.eval_nll_grad(p)
     assert abs(nll - nll_o) < 1e-3
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
     assert gm.eval_terms(p)[2] == pytest.approx(aux[2], rel=1e-8)
 
 
@@ -128,7 +132,7 @@ def test_eq14_model_distributed_data(A):
     nll_o, g_o, aux, rc = om.nll_eq14(p, ev, nm, grad=True)
     nll, g = gm.eval_nll_grad(p)
     assert rc == 0 and abs(nll - nll_o) < 1e-3
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
 
 
 def test_eq14_pdf_parity(A):
@@ -159,7 +163,7 @@ def test_eq14_purity_limits(A, purity):
     if purity == 0.0:
         assert np.all(g_o == 0.0) and np.all(np.abs(g) == 0.0)
     else:
-        assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+        assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
 
 
 def test_templates_can_be_removed(A):
@@ -170,7 +174,7 @@ def test_templates_can_be_removed(A):
     nll_o, g_o, _, _ = plain.nll(p, ev, nm, grad=True)
     nll, g = gm.eval_nll_grad(p)
     assert abs(nll - nll_o) < 1e-3
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
 
 
 def test_eq14_unavailable_calls(A):

@@ -1,7 +1,7 @@
 """Flavour tags and mistag (text after Eq. 12) on the GPU path, against the FP64
 oracle, which evaluates S at t phi and -t phi from recomputed kinematics (the
 GPU conjugates the angular phase factors of the same coupling sums).
-Tolerances as in the signal parity tests: |dNLL| < 1e-3, gradient <= 1e-5
+Tolerances as in the signal parity tests: |dNLL| < 1e-3, gradient <= 1e-6
 |g|_inf, per-event density relative 1e-5 where well conditioned."""
 import math
 
@@ -13,6 +13,10 @@ pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
+
+# Gradient parity bound: every component within 1e-6 |g|_inf of the oracle's
+# gradient (the scope table's "absolute <= 1e-6 |g|_inf" form).
+GRAD_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +73,7 @@ def test_flavour_parity(A, path, name, fl, w):
     print("%s %s fl=%s w=%g: dNLL %.3e max|dg|/|g| %.3e" % (
         name, path, fl, w, nll - nll_o, np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
     assert abs(nll - nll_o) < 1e-3
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
     assert gm.eval_nll(p) == pytest.approx(nll, abs=1e-4)
 
 
@@ -80,7 +84,7 @@ def test_flavour_with_efficiency_and_background(A, path):
     nll_o, g_o, aux, rc = om.nll_eq14(p, ev, nm, grad=True, tag=tag)
     nll, g = gm.eval_nll_grad(p)
     assert rc == 0 and abs(nll - nll_o) < 1e-3
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
 
 
 def test_tagged_density(A):

@@ -5,10 +5,13 @@ Tolerances (stated by the method's accuracy targets):
       kappa = sum_xi (sum_k |c_k B_k,xi|)^2 / S <= 100, else absolute
       1e-5 * sum_xi (sum_k |c_k B_k,xi|)^2;
   NLL: |dNLL| <= 1e-3 (the target at 10^6 events; smaller sets are tighter);
-  gradient: per component <= 1e-6 relative or <= 1e-5 |g|_inf absolute.  The
-      NLL gradient is a difference of a data sum and N dI/I, each ~N times
-      larger than their difference near the optimum; FP32 per-event arithmetic
-      (relative ~1e-8 coherent over a resonance peak) leaves ~1e-6 |g|_inf;
+  gradient: per component <= 1e-6 |g|_inf absolute (GRAD_TOL).  The NLL
+      gradient is a difference of a data sum and N dI/I, each ~N times larger
+      than their difference near the optimum, so a coherent relative error of
+      the per-event FP32 terms is amplified by that ratio.  At the generating
+      point of a small sample |g|_inf is a statistical fluctuation and can be
+      accidentally small; there the scale is max(|g|_inf, the gradient's
+      statistical scale) (_gradient_scale);
   normalisation integral I: relative 1e-9.
 """
 import math
@@ -21,6 +24,10 @@ pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
+
+# Gradient parity bound: every component within 1e-6 |g|_inf of the oracle's
+# gradient (the scope table's "absolute <= 1e-6 |g|_inf" form).
+GRAD_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +42,7 @@ def _dev(pts):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in pts]
 
 
-def _setup(A, name, n_ev, n_mc, float_names=None, data="peaked", seed_shift=0):
+def _setup(A, name, n_ev, n_mc, float_names=None, data="peaked", seed_shift=0, path=None):
     cfg = W.CONFIGS[name]
     res = cfg.resonances
     fl = cfg.float_mg if float_names is None else float_names
@@ -49,7 +56,7 @@ def _setup(A, name, n_ev, n_mc, float_names=None, data="peaked", seed_shift=0):
     else:
         ev, _, _ = om.generate(p, n_ev, cfg.data_seed + seed_shift)
     nm = W.uniform_points(n_mc, cfg.norm_seed + seed_shift)
-    gm = A.Model(res, float_names=fl)
+    gm = A.Model(res, float_names=fl, path=A.AMP4D_PATH_PLAIN if path is None else path)
     gm.set_events(*_dev(ev))
     gm.set_norm_points(*_dev(nm))
     return cfg, res, c, p, om, gm, ev, nm
@@ -103,6 +110,23 @@ def test_nll_terms_parity(A, name):
     assert abs(nll - nll_o) < 1e-3 + 2.0 * spread
 
 
+def _gradient_scale(om, p, ev, k=16):
+    """Statistical scale of the -2 ln L gradient of a sample of N events at p:
+    2 sqrt(N Var(t)) for the per-event terms t = d ln S / d theta, the largest
+    over the components.  Var(t) comes from the spread of the oracle's data sums
+    over k equal parts of the sample.  At the generating point the gradient of a
+    given sample is a fluctuation of this size; it can happen to be much smaller
+    (its largest component, like any other, fluctuates), and the 1e-6 bound is
+    then taken relative to this scale."""
+    n = len(ev[0])
+    P = om.n_params
+    empty = tuple(np.zeros(0, np.float32) for _ in range(4))
+    sums = np.array([om.partials(p, tuple(a[idx] for a in ev), empty)[6:6 + P]
+                     for idx in np.array_split(np.arange(n), k)])
+    var_t = sums.var(axis=0, ddof=1) / (n / k)
+    return float(np.max(2.0 * np.sqrt(n * var_t)))
+
+
 @pytest.mark.parametrize("name", ["tiny", "kstar10_z", "kstar10_2z", "lass_z"])
 def test_nll_grad_parity_model_data(A, name):
     n = 20_000 if name == "tiny" else 8_000
@@ -110,8 +134,11 @@ def test_nll_grad_parity_model_data(A, name):
     nll_o, g_o, _, rc = om.nll(p, ev, nm, grad=True)
     nll, g = gm.eval_nll_grad(p)
     assert abs(nll - nll_o) < 1e-3
-    tol = np.maximum(1e-6 * np.abs(g_o), 1e-5 * np.max(np.abs(g_o)))
-    assert np.all(np.abs(g - g_o) <= tol), np.max(np.abs(g - g_o) / np.max(np.abs(g_o)))
+    scale = max(np.max(np.abs(g_o)), _gradient_scale(om, p, ev))
+    print("%s: max |dg| / |g|inf %.3e, / statistical scale %.3e" % (
+        name, np.max(np.abs(g - g_o)) / np.max(np.abs(g_o)), np.max(np.abs(g - g_o)) / scale))
+    tol = np.maximum(1e-6 * np.abs(g_o), GRAD_TOL * scale)
+    assert np.all(np.abs(g - g_o) <= tol), np.max(np.abs(g - g_o) / scale)
     nll2 = gm.eval_nll(p)
     assert nll2 == pytest.approx(nll, abs=1e-4)  # NLL-only kernel: other summation order
 
@@ -126,7 +153,7 @@ def test_grad_parity_all_masses_floating(A):
     rel = np.abs(g - g_o) / np.maximum(np.abs(g_o), 1e-3 * np.max(np.abs(g_o)))
     print("all M/G floating: max rel %.3e, max |dg|/|g|inf %.3e" % (np.max(rel), np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
     assert np.max(rel) < 1e-3, np.argmax(rel)
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
 
 
 def test_deterministic(A):
@@ -167,7 +194,7 @@ def test_tiny_and_ragged_sizes(A, n):
     nll_o, g_o, _, _ = om.nll(p, ev, nm, grad=True)
     nll, g = gm.eval_nll_grad(p)
     assert abs(nll - nll_o) < 1e-4
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
     _check_density(om, p, c, ev, gm.eval_density(p, 0).cpu().numpy())
 
 
@@ -224,23 +251,48 @@ def test_nll_grad_1e6_model_events(A):
     t = gm.eval_terms(p)
     print("dNLL %.3e  d(sum lnS) %.3e  dI/I %.3e" % (nll - nll_o, t[0] - aux[0], t[2] / aux[2] - 1))
     assert abs(nll - nll_o) <= 1e-3
-    tol = np.maximum(1e-6 * np.abs(g_o), 1e-5 * np.max(np.abs(g_o)))
+    tol = np.maximum(1e-6 * np.abs(g_o), GRAD_TOL * np.max(np.abs(g_o)))
     print("1e6: max |dg|/|g|inf = %.3e" % (np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
     assert np.all(np.abs(g - g_o) <= tol), np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))
 
 
-def test_nll_full_size_large_workload(A):
-    """Full benchmark workload (5e6 events, 2^24 points, Z mass/width floating) in the
-    launch configuration the benchmark times: NLL and gradient against the oracle."""
-    cfg, res, c, p, om, gm, ev, nm = _setup(A, "large", 5_000_000, 1 << 24)
+def test_full_size_benchmarked_path(A):
+    """The benchmark's workload and launch configuration: 10 K* + Z(4430), 5e6
+    peaked data events, 2^24 uniform normalisation points, every mass and width
+    fixed, the cached path (all lineshapes from the basis cache, the two-event
+    adjoint kernel over a multi-sweep grid, the tensor-core Gram normalisation).
+    NLL and every gradient component against the oracle, at two parameter points
+    (the second one after the couplings-only table update)."""
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, "large", 5_000_000, 1 << 24, path=A.AMP4D_PATH_CACHED)
+    assert not cfg.float_mg
+    for k, pk in enumerate([p, p * (1.0 + 1e-3 * math.sin(0.7))]):
+        nll_o, g_o, aux, rc = om.nll(pk, ev, nm, grad=True)
+        assert rc == 0
+        nll, g = gm.eval_nll_grad(pk)
+        gi = np.max(np.abs(g_o))
+        print("large point %d: dNLL %.3e (NLL %.6f), max |dg|/|g|inf = %.3e" % (
+            k, nll - nll_o, nll_o, np.max(np.abs(g - g_o)) / gi))
+        # data not drawn from the model: the NLL is 5e7 and its gradient O(N)
+        assert abs(nll - nll_o) <= 1e-9 * abs(nll_o)
+        assert np.all(np.abs(g - g_o) <= GRAD_TOL * gi), np.argmax(np.abs(g - g_o))
+    assert gm.eval_terms(p)[3] == 5_000_000
+
+
+def test_full_size_floated_z_path(A):
+    """The floated-mass benchmark configuration (Z(4430) mass and width free):
+    5e6 events and 2^24 points, the per-point adjoint over the normalisation
+    points with the Z lineshape computed per event and point; NLL and gradient
+    against the oracle."""
+    cfg, res, c, p, om, gm, ev, nm = _setup(A, "large_float_z", 5_000_000, 1 << 24,
+                                            path=A.AMP4D_PATH_CACHED)
+    assert cfg.float_mg
     nll_o, g_o, aux, rc = om.nll(p, ev, nm, grad=True)
+    assert rc == 0
     nll, g = gm.eval_nll_grad(p)
-    print("large: dNLL %.3e (NLL %.6f)" % (nll - nll_o, nll_o))
-    # data not drawn from the model: the gradient is O(N) and per-event FP32 rounding no
-    # longer averages out around the optimum; held to 1e-9 of the NLL (4.9e7)
+    gi = np.max(np.abs(g_o))
+    print("large_float_z: dNLL %.3e, max |dg|/|g|inf = %.3e" % (nll - nll_o, np.max(np.abs(g - g_o)) / gi))
     assert abs(nll - nll_o) <= 1e-9 * abs(nll_o)
-    print("large: max |dg|/|g|inf = %.3e" % (np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.all(np.abs(g - g_o) <= GRAD_TOL * gi), np.argmax(np.abs(g - g_o))
 
 
 def test_density_bias(A):
@@ -303,8 +355,8 @@ def test_cached_all_fixed_ragged_sizes(A, n):
     assert nll_c2 == nll_c and np.array_equal(g_c2, g_c)
     tol_nll = 1e-4 + 1e-9 * abs(nll_o)
     assert abs(nll_c - nll_o) < tol_nll and abs(nll_p - nll_o) < tol_nll
-    assert np.max(np.abs(g_c - g_o)) <= 1e-5 * np.max(np.abs(g_o))
-    assert np.max(np.abs(g_c - g_p)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g_c - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
+    assert np.max(np.abs(g_c - g_p)) <= GRAD_TOL * np.max(np.abs(g_o))
 
 
 @pytest.mark.parametrize("R", [1.0, 2.0, 0.0])
@@ -339,4 +391,4 @@ def test_lass_density_near_threshold_and_pole(A, R):
         assert rc == 0
         nll, g = g2.eval_nll_grad(p)
         assert abs(nll - nll_o) < 1e-4 + 1e-9 * abs(nll_o)
-        assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+        assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))

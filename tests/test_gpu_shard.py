@@ -5,7 +5,7 @@ and the union rebuilt by amp4d_combine_partials.
 
 Checked against the FP64 oracle's partials of the same shards and its -2 ln L
 of the union, with the tolerances of the single-model parity tests (NLL
-|dNLL| < 1e-3, gradient <= 1e-5 |g|_inf, I relative 1e-8, sum ln S absolute
+|dNLL| < 1e-3, gradient <= 1e-6 |g|_inf, I relative 1e-8, sum ln S absolute
 5e-4 per shard), and against the single-model GPU evaluation of the union."""
 import numpy as np
 import pytest
@@ -15,6 +15,10 @@ pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
+
+# Gradient parity bound: every component within 1e-6 |g|_inf of the oracle's
+# gradient (the scope table's "absolute <= 1e-6 |g|_inf" form).
+GRAD_TOL = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -76,14 +80,14 @@ def test_shards_match_oracle_and_union(A, name, world):
     assert rc == 0
     assert abs(nll - nll_o) < 1e-3
     assert out[3] == pytest.approx(aux[2], rel=1e-8)
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
     # the union on one model: the same sums in another order
     whole = A.Model(res, float_names=cfg.float_mg)
     whole.set_events(*_dev(ev))
     whole.set_norm_points(*_dev(nm))
     nll_w, g_w = whole.eval_nll_grad(p)
     assert abs(nll - nll_w) < 1e-3
-    assert np.max(np.abs(g - g_w)) <= 1e-5 * np.max(np.abs(g_w))
+    assert np.max(np.abs(g - g_w)) <= GRAD_TOL * np.max(np.abs(g_w))
     assert parts.shape == (world, 6 + 2 * P)
 
 
@@ -98,7 +102,7 @@ def test_shards_on_the_gram_path(A):
     nll_o, g_o, aux, rc = om.nll(p, ev, nm, grad=True)
     assert abs(nll - nll_o) < 1e-3
     assert out[3] == pytest.approx(aux[2], rel=1e-8)
-    assert np.max(np.abs(g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
     for part, ((a, b), (c, d)) in zip(parts, cuts):
         o = om.partials(p, _cut(ev, a, b), _cut(nm, c, d))
         assert part[3] == pytest.approx(o[3], rel=1e-8)
