@@ -400,6 +400,23 @@ amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t s
 amp4d_status amp4d_proposal_train(amp4d_model *model, const float *m, const float *cK,
                                   const float *cpsi, const float *phi, int64_t n,
                                   const amp4d_mlp_cfg *cfg, uint64_t seed, double *loss, void *stream);
+/*
+ * Proposal aimed at the whole normalisation Gram matrix rather than at S: the
+ * target density is sum_k |B_k|^2 p q, whose importance weights control the
+ * error of every Gram element G_jk = int B_j* B_k p q and so of I(c) = c^H G c at
+ * any couplings (the quantity the fit reads, Eq. 5 with the phase-space
+ * density).  Builds G for the masses and widths in params (host; its couplings
+ * are not used) over the current normalisation points, splits n events over
+ * the columns in proportion to G_kk (at least 1 each), draws column k's share
+ * from the model with the single unit coupling c_k = 1 (amp4d_generate, seed
+ * gen_seed + k) and trains the proposal on their union exactly as
+ * amp4d_proposal_train (cfg, seed, *loss).  Synchronises.  Errors: STATE (no
+ * normalisation points), DOMAIN (a Gram diagonal element not >= 0), ARG, CUDA,
+ * OOM, TIMEOUT.
+ */
+amp4d_status amp4d_proposal_train_gram(amp4d_model *model, const double *params, int64_t n,
+                                       const amp4d_mlp_cfg *cfg, uint64_t seed, uint64_t gen_seed,
+                                       double *loss, void *stream);
 amp4d_status amp4d_proposal_sample(amp4d_model *model, int64_t n, uint64_t seed, float *m, float *cK,
                                    float *cpsi, float *phi, float *w, void *stream);
 

@@ -1382,7 +1382,10 @@ void or_grid_sample(const double *gc, const int *nb, double alpha, uint64_t seed
         uint32_t c1[4] = {(uint32_t)i, 1u, (uint32_t)((uint64_t)i >> 32), 0u}, r1[4];
         or_philox4x32_10(c0, key, r0);
         or_philox4x32_10(c1, key, r1);
-        const double u0 = u01(r0[0]) * cdf[nc - 1];
+        /* stratified in the CDF: point i takes its cell at u in [i/n, (i+1)/n) of the
+           total, so every point is marginally distributed as the proposal while the
+           points of one call cover the CDF evenly */
+        const double u0 = ((double)i + u01(r0[0])) / (double)n * cdf[nc - 1];
         int64_t lo = 0, hi = nc - 1;
         while (lo < hi) {
             int64_t mid = (lo + hi) / 2;
@@ -1396,7 +1399,10 @@ void or_grid_sample(const double *gc, const int *nb, double alpha, uint64_t seed
         const double us[4] = {u01(r0[1]), u01(r0[2]), u01(r0[3]), u01(r1[0])};
         double x[4];
         for (int d = 0; d < 4; ++d) x[d] = -1.0 + 2.0 * (idx[d] + us[d]) / nb[d];
-        const float fm = (float)(m_lo + (m_hi - m_lo) * 0.5 * (x[0] + 1.0));
+        float fm = (float)(m_lo + (m_hi - m_lo) * 0.5 * (x[0] + 1.0));
+        /* keep the FP32 mass inside the box (the cell density is constant) */
+        if ((double)fm > m_hi) fm = nextafterf(fm, 0.0f);
+        if ((double)fm < m_lo) fm = nextafterf(fm, 3.0e38f);
         const float fcK = (float)x[1], fcpsi = (float)x[2], fphi = (float)(M_PI * x[3]);
         const double Pc = cdf[c] - (c > 0 ? cdf[c - 1] : 0.0);
         const double q = Pc / cdf[nc - 1] * (double)nc / 16.0 * 2.0 / ((m_hi - m_lo) * M_PI);

@@ -213,6 +213,9 @@ amp4d_generate = _proto("amp4d_generate", C.c_int, [_vp, _d, C.c_uint64, C.c_int
 amp4d_proposal_train = _proto("amp4d_proposal_train", C.c_int,
                               [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.POINTER(amp4d_mlp_cfg), C.c_uint64,
                                _d, _vp])
+amp4d_proposal_train_gram = _proto("amp4d_proposal_train_gram", C.c_int,
+                                   [_vp, _d, C.c_int64, C.POINTER(amp4d_mlp_cfg), C.c_uint64, C.c_uint64,
+                                    _d, _vp])
 amp4d_proposal_sample = _proto("amp4d_proposal_sample", C.c_int,
                                [_vp, C.c_int64, C.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp])
 amp4d_mlp_forward = _proto("amp4d_mlp_forward", C.c_int, [_vp, _vp, C.c_int64, _vp, _vp])
@@ -237,7 +240,7 @@ EXPORTED = ["amp4d_set_efficiency", "amp4d_set_background", "amp4d_set_flavour",
             "amp4d_eval_nll_grad", "amp4d_eval_terms", "amp4d_eval_density", "amp4d_enqueue_eval",
             "amp4d_profile_enable", "amp4d_profile_read", "amp4d_build_gram", "amp4d_get_gram",
             "amp4d_gram_selftest", "amp4d_generate", "amp4d_proposal_train",
-            "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample",
+            "amp4d_proposal_train_gram", "amp4d_proposal_sample", "amp4d_mlp_forward", "amp4d_mlp_loss_grad", "amp4d_grid_sample",
             "amp4d_mlp_loss_grad_noalloc", "amp4d_noalloc_last_error", "amp4d_eval_partials",
             "amp4d_enqueue_partials", "amp4d_combine_partials", "amp4d_shard_last_error",
             "amp4d_eval_pdf", "amp4d_fit_fractions"]
@@ -445,7 +448,7 @@ class Model:
                                    *(o.data_ptr() for o in outs), _stream_ptr(stream)))
         return tuple(outs)
 
-    def proposal_train(self, events, nb=(128, 16, 16, 32), alpha=0.1, steps=1500, batch=4096,
+    def proposal_train(self, events, nb=(128, 32, 16, 32), alpha=0.05, steps=4000, batch=8192,
                        lr=2e-3, seed=1, stream=None):
         cfg = amp4d_mlp_cfg((C.c_int * 4)(*nb), alpha, steps, batch, lr)
         loss = C.c_double()
@@ -454,27 +457,18 @@ class Model:
                                          C.byref(cfg), int(seed), C.byref(loss), _stream_ptr(stream)))
         return loss.value
 
-    def proposal_train_gram(self, params, n=1 << 20, seed=12, gen_seed=5000, **kw):
-        """Train the proposal toward the whole normalisation Gram matrix: the
-        target density sum_k |B_k|^2 p q, drawn column by column (the model with a
-        unit coupling at column k has density |B_k|^2 p q) in proportion to the
-        Gram diagonal G_kk over the current normalisation points.  params gives the
-        masses and widths (its couplings are not used).  Returns the training loss."""
-        import torch
+    def proposal_train_gram(self, params, n=1 << 20, seed=12, gen_seed=5000, nb=(128, 32, 16, 32),
+                            alpha=0.05, steps=4000, batch=8192, lr=2e-3, stream=None):
+        """Train the proposal toward the whole normalisation Gram matrix (target
+        sum_k |B_k|^2 p q; amp4d_proposal_train_gram).  params gives the masses
+        and widths (its couplings are not used).  Returns the training loss."""
         p = self._params(params)
-        self.build_gram(p)
-        G = self.get_gram()
-        K = self.n_cols
-        gdiag = np.array([G[2 * k, 2 * k] + G[2 * k + 1, 2 * k + 1] for k in range(K)])
-        n_k = np.maximum(1, np.round(n * gdiag / gdiag.sum())).astype(int)
-        pieces = []
-        for k in range(K):
-            pk = np.zeros_like(p)
-            pk[2 * k] = 1.0
-            pk[2 * K:] = p[2 * K:]
-            pieces.append(self.generate(pk, int(n_k[k]), gen_seed + k))
-        events = tuple(torch.cat([pc[i] for pc in pieces]) for i in range(4))
-        return self.proposal_train(events, seed=seed, **kw)
+        cfg = amp4d_mlp_cfg((C.c_int * 4)(*nb), alpha, steps, batch, lr)
+        loss = C.c_double()
+        self._check(amp4d_proposal_train_gram(self.h, p.ctypes.data_as(_d), int(n), C.byref(cfg),
+                                              int(seed), int(gen_seed), C.byref(loss),
+                                              _stream_ptr(stream)))
+        return loss.value
 
     def proposal_sample(self, n, seed, stream=None):
         """n importance-sampled points and weights w = p q / q (device float32 tensors)."""

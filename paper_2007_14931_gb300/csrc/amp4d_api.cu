@@ -1367,6 +1367,58 @@ amp4d_status amp4d_proposal_train(amp4d_model *model, const float *m, const floa
     return AMP4D_OK;
 }
 
+amp4d_status amp4d_proposal_train_gram(amp4d_model *model, const double *params, int64_t n,
+                                       const amp4d_mlp_cfg *cfg, uint64_t seed, uint64_t gen_seed,
+                                       double *loss, void *stream)
+{
+    if (!model || !params || !cfg || n < 1) return AMP4D_ERR_ARG;
+    if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "set_norm_points must come first");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(model->device));
+    // The Gram diagonal over the current points at these masses and widths:
+    // G_kk = int |B_k|^2 p q (times the points' weights), the normalisation of
+    // column k with a unit coupling.
+    amp4d_status rc = amp4d_build_gram(model, params, stream);
+    if (rc) return rc;
+    const int K = model->n_col, dim = 2 * K, P = model->n_param;
+    std::vector<double> G((size_t)dim * dim);
+    rc = amp4d_get_gram(model, G.data(), stream);
+    if (rc) return rc;
+    std::vector<double> gd(K);
+    double gsum = 0.0;
+    for (int k = 0; k < K; ++k) {
+        gd[k] = G[(size_t)(2 * k) * dim + 2 * k] + G[(size_t)(2 * k + 1) * dim + 2 * k + 1];
+        if (!(gd[k] >= 0.0)) return fail(model, AMP4D_ERR_DOMAIN, "proposal_train_gram: a Gram diagonal element is not >= 0");
+        gsum += gd[k];
+    }
+    if (!(gsum > 0.0)) return fail(model, AMP4D_ERR_DOMAIN, "proposal_train_gram: the Gram diagonal is 0");
+    // Column k contributes max(1, round(n G_kk / sum G)) events of the model with
+    // the single unit coupling c_k = 1 (density |B_k|^2 p q), drawn by the
+    // generator with seed gen_seed + k: together a draw from sum_k |B_k|^2 p q.
+    std::vector<int64_t> nk(K), off(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        nk[k] = std::max<int64_t>(1, (int64_t)std::llround((double)n * gd[k] / gsum));
+        off[k + 1] = off[k] + nk[k];
+    }
+    const int64_t tot = off[K];
+    float *ev = nullptr;
+    CK(cudaMalloc(&ev, (size_t)4 * tot * sizeof(float)));
+    std::vector<double> pk(params, params + P);
+    for (int k = 0; k < K && rc == AMP4D_OK; ++k) {
+        std::fill(pk.begin(), pk.begin() + 2 * K, 0.0);
+        pk[2 * k] = 1.0;
+        rc = amp4d_generate(model, pk.data(), gen_seed + (uint64_t)k, nk[k], ev + off[k],
+                            ev + tot + off[k], ev + 2 * tot + off[k], ev + 3 * tot + off[k], stream);
+    }
+    if (rc == AMP4D_OK)
+        rc = amp4d_proposal_train(model, ev, ev + tot, ev + 2 * tot, ev + 3 * tot, tot, cfg, seed, loss,
+                                  stream);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(ev);
+    if (rc == AMP4D_OK && e != cudaSuccess) return fail(model, AMP4D_ERR_CUDA, cudaGetErrorString(e));
+    return rc;
+}
+
 amp4d_status amp4d_proposal_sample(amp4d_model *model, int64_t n, uint64_t seed, float *m, float *cK,
                                    float *cpsi, float *phi, float *w, void *stream)
 {

@@ -322,7 +322,12 @@ __global__ void k_grid_sample(const double *__restrict__ cdf, int nb0, int nb1, 
         uint32_t r0[4], r1[4];
         philox_stream((uint64_t)i, 0u, seed, r0);
         philox_stream((uint64_t)i, 1u, seed, r1);
-        const double u0 = u01d(r0[0]) * total;
+        // Stratified in the CDF: point i takes u in [i/n, (i + 1)/n) of the total.
+        // Each point is marginally drawn from the proposal (the weights stay exact),
+        // and a call's points cover the CDF evenly: the estimate of I keeps only the
+        // variation of S p q / q inside each stratum (about one cell), not the
+        // fluctuation of how many points land in each region.
+        const double u0 = ((double)i + u01d(r0[0])) / (double)n * total;
         int64_t lo = 0, hi = nc - 1;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
@@ -339,7 +344,11 @@ __global__ void k_grid_sample(const double *__restrict__ cdf, int nb0, int nb1, 
         const double x1 = -1.0 + 2.0 * (i1 + u01d(r0[2])) / nb1;
         const double x2 = -1.0 + 2.0 * (i2 + u01d(r0[3])) / nb2;
         const double x3 = -1.0 + 2.0 * (i3 + u01d(r1[0])) / nb3;
-        const float fm = (float)(m_lo + (m_hi - m_lo) * 0.5 * (x0 + 1.0));
+        float fm = (float)(m_lo + (m_hi - m_lo) * 0.5 * (x0 + 1.0));
+        // the FP32 rounding may step just outside the box: take the nearest FP32
+        // value inside (q is constant over the cell, so the weight is unchanged)
+        if ((double)fm > m_hi) fm = nextafterf(fm, 0.0f);
+        if ((double)fm < m_lo) fm = nextafterf(fm, 3.0e38f);
         const double Pc = cdf[c] - (c > 0 ? cdf[c - 1] : 0.0);
         const double q = Pc / total * (double)nc / 16.0 * 2.0 / ((m_hi - m_lo) * M_PI);
         const double mm = (double)fm;

@@ -51,14 +51,33 @@ def test_generator_matches_oracle_generator(A):
 
 
 def test_generator_follows_the_model(A):
-    """Mean of cos^2 theta_psi and of m over generated events vs the oracle's draw (statistics)."""
-    cfg = W.CONFIGS["kstar10_z"]
+    """GPU accept-reject events of the ten-K* model: their m_Kpi histogram against
+    the model's 1D density p q int S dOmega / I, from the exact angular closure and
+    adaptive quadrature in m (chi^2 per bin near 1)."""
+    from scipy import integrate
+    from test_oracle_pins import M_END, _kstar_angular_closed_form, _norm_1d
+    cfg = W.CONFIGS["kstar10"]
     res = cfg.resonances
-    p = W.couplings_to_params(W.draw_couplings(res, cfg.coupling_seed))
+    c = W.draw_couplings(res, cfg.coupling_seed)
+    p = W.couplings_to_params(c)
+    mo = O.Model(res)
     gm = A.Model(res)
-    ev = [t.cpu().numpy().astype(np.float64) for t in gm.generate(p, 50_000, 5)]
-    S, pq = O.Model(res).density(p, ev)
-    assert np.all(S * pq > 0)
+    m = gm.generate(p, 200_000, 5)[0].cpu().numpy().astype(np.float64)
+    I1 = _norm_1d(mo, c)
+
+    def dens(x):
+        return O.breakup(W.M_B, x, W.M_PSI) * O.breakup(x, W.M_K, W.M_PI) * \
+            _kstar_angular_closed_form(mo, c, x) / I1
+
+    edges = np.linspace(W.M_LO, M_END, 61)
+    h, _ = np.histogram(m, edges)
+    exp = len(m) * np.array([integrate.quad(dens, a, b, epsrel=1e-10)[0]
+                             for a, b in zip(edges[:-1], edges[1:])])
+    keep = exp > 10
+    chi2 = np.sum((h[keep] - exp[keep]) ** 2 / exp[keep])
+    print("generator m_Kpi: chi2 %.1f for %d bins" % (chi2, keep.sum()))
+    assert abs(exp.sum() / len(m) - 1) < 1e-6
+    assert chi2 / keep.sum() < 1.6
 
 
 @pytest.mark.parametrize("n", [1, 127, 4099])
@@ -95,39 +114,40 @@ def test_grid_sample_parity(A):
     assert np.allclose(w.cpu().numpy()[same], wo[same], rtol=2e-6)
 
 
-def test_learned_proposal_reduces_normalisation_variance(A):
-    """C4-like: train the proposal on 2^20 events generated from the 10 K* + Z model;
-    2^20 importance-sampled points vs 2^24 uniform points, 8 seeds each, judged by
-    the FP64 oracle on 2^26 uniform points."""
+def test_learned_proposal_meets_the_integral_target(A):
+    """The learned normalisation (C4): the proposal trained on 2^20 events the GPU
+    generator draws from the 10 K* + Z model; 16 independent samples of 2^20
+    importance-sampled points and 16 of 2^24 uniform points, each judged against
+    the oracle's 4D product quadrature of I (accurate to about 1e-8).  Target:
+    rms relative error <= 1e-4 for the learned estimate, which must also beat
+    the uniform one with 16 times fewer points, and no bias beyond its spread."""
+    from oracle import quadrature as Q
     cfg = W.CONFIGS["learned"]
     res = cfg.resonances
     c = W.draw_couplings(res, cfg.coupling_seed)
     p = W.couplings_to_params(c)
+    I_q = Q.normalisation_quadrature(O.Model(res), p, 24, 16)
     gm = A.Model(res)
     ev = gm.generate(p, 1 << 20, 3)
     gm.set_events(*ev)
-    loss = gm.proposal_train(ev, steps=1500, batch=4096, seed=11)
+    loss = gm.proposal_train(ev, seed=11)
+    one = np.ones(1, dtype=np.float32)
     I_is, I_un = [], []
-    for s in range(8):
+    for s in range(16):
         pts, w = gm.proposal_sample(1 << 20, 100 + s)
         gm.set_norm_points(*pts, w=w, volume=1.0)
         I_is.append(gm.eval_terms(p)[2])
-        un = W.uniform_points(1 << 24, 500 + s)
-        gm.set_norm_points(*(torch.from_numpy(a).cuda() for a in un))
+        pts, w, _ = A.grid_sample(one, (1, 1, 1, 1), 1.0, 500 + s, 1 << 24)   # uniform, w = V p q
+        gm.set_norm_points(*pts, w=w, volume=1.0)
         I_un.append(gm.eval_terms(p)[2])
-    judge_pts = W.uniform_points(1 << 26, 777)
-    S, pq = O.Model(res).density(p, judge_pts)
-    f = W.BOX_VOLUME * S * pq
-    I_ref, sig_ref = f.mean(), f.std() / math.sqrt(len(f))
-    I_is, I_un = np.array(I_is), np.array(I_un)
-    rms_is = np.sqrt(np.mean((I_is / I_ref - 1) ** 2))
-    rms_un = np.sqrt(np.mean((I_un / I_ref - 1) ** 2))
-    sd_is, sd_un = I_is.std(ddof=1) / I_ref, I_un.std(ddof=1) / I_ref
-    print("loss %.4f  rms rel error vs judge: learned 2^20 %.3e, uniform 2^24 %.3e (judge sigma %.1e); "
-          "seed spread: learned %.3e, uniform %.3e; variance reduction per point %.1f" % (
-              loss, rms_is, rms_un, sig_ref / I_ref, sd_is, sd_un, 16 * (sd_un / sd_is) ** 2))
-    assert abs(I_is.mean() / I_ref - 1) < 4 * max(I_is.std() / math.sqrt(8), sig_ref) / I_ref + 1e-4
-    assert rms_is < rms_un * 1.2
+    r_is, r_un = np.array(I_is) / I_q - 1, np.array(I_un) / I_q - 1
+    rms_is, rms_un = np.sqrt(np.mean(r_is ** 2)), np.sqrt(np.mean(r_un ** 2))
+    print("loss %.4f  rms relative error vs the quadrature: learned 2^20 %.3e (mean %+.2e), "
+          "uniform 2^24 %.3e (mean %+.2e); variance reduction per point %.0f" % (
+              loss, rms_is, r_is.mean(), rms_un, r_un.mean(), 16 * (rms_un / rms_is) ** 2))
+    assert rms_is <= 1e-4
+    assert rms_is < rms_un
+    assert abs(r_is.mean()) < 4 * r_is.std(ddof=1) / 4.0 + 1e-6
 
 
 def test_gram_targeted_proposal_is_unbiased_for_every_column(A):

@@ -106,13 +106,29 @@ def test_grid_sampler_cell_frequencies():
     _, _, cell = O.grid_sample(gc, nb, alpha, 5, n)
     P = alpha / 64 + (1 - alpha) * gc / gc.sum()
     counts = np.bincount(cell, minlength=64)
-    chi2 = np.sum((counts - n * P) ** 2 / (n * P))
-    assert stats.chi2.sf(chi2, 63) > 1e-3
+    # stratified in the CDF: cell c receives the points whose strata [i/n, (i+1)/n)
+    # of the total put u in its CDF interval, n P_c of them up to one at each end
+    assert np.all(np.abs(counts - n * P) < 2.0)
     # the sampled position lies in the sampled cell
     (m, cK, cpsi, phi), _, cell = O.grid_sample(gc, nb, alpha, 6, 1000)
     x0 = 2 * (m.astype(np.float64) - W.M_LO) / (W.M_HI - W.M_LO) - 1
     i0 = np.minimum((0.5 * (x0 + 1) * nb[0]).astype(int), nb[0] - 1)
     assert np.mean(i0 == cell // (nb[1] * nb[2] * nb[3])) > 0.999
+
+
+def test_grid_sampler_points_are_marginally_drawn_from_the_proposal():
+    """Over independent seeds the cell of point i follows the proposal's cell
+    probabilities restricted to its stratum: pooled over the points of many calls
+    of a few points each, the cell frequencies are multinomial in P."""
+    nb = (4, 2, 2, 4)
+    rng = np.random.default_rng(14)
+    gc = rng.uniform(0, 1, 64) ** 3
+    alpha = 0.2
+    P = alpha / 64 + (1 - alpha) * gc / gc.sum()
+    cells = np.concatenate([O.grid_sample(gc, nb, alpha, 1000 + s, 1)[2] for s in range(20_000)])
+    counts = np.bincount(cells, minlength=64)
+    chi2 = np.sum((counts - len(cells) * P) ** 2 / (len(cells) * P))
+    assert stats.chi2.sf(chi2, 63) > 1e-3
 
 
 def test_grid_sampler_is_unbiased_for_the_phase_space_volume():
