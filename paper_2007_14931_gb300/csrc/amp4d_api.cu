@@ -72,6 +72,7 @@ struct amp4d_model {
     int64_t prof_n[4] = {0, 0, 0, 0};
     int *d_slot_param = nullptr;
     unsigned long long *d_acc = nullptr;   // 128-bit sums: [data, points][nslot][hi, lo], R
+    double *d_guv = nullptr;               // G u and G v of the fused Gram finish (2 x 64)
     double *d_out = nullptr, *h_out = nullptr;
     unsigned *d_status = nullptr;
     unsigned long long *d_bad = nullptr;
@@ -244,7 +245,7 @@ cudaError_t enqueue_table(amp4d_model *mo, const double *d_params, cudaStream_t 
 {
     const bool fast = mo->n_float == 0 && mo->table_built;
     cudaError_t e = launch_build_table(mo->d_static, d_params, mo->d_md, mo->d_pscale, mo->d_status,
-                                       st, fast, mo->d_acc, 4 * mo->nslot + 2);
+                                       st, fast, mo->d_acc, 4 * mo->nslot + 3);
     if (e == cudaSuccess && mo->n_float == 0) mo->table_built = true;
     return e;
 }
@@ -423,8 +424,24 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
                                   model->n_param, (double)model->ev.n, lnconst, von, d_params,
                                   model->d_G, model->d_status, d_out, 0, st, (double)model->mc.n, 0,
                                   nullptr, model->d_md, model->purity));
+        // With the gradient and no background the data kernel's last CTA finishes
+        // the evaluation (no separate launch).
+        bool fused = false;
         if (with_grad) {
             LaunchArgs la = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
+            // the all-cached kernel carries the finish; its first n_col CTAs form G u, G v
+            fused = !mix && la.lcache != nullptr && la.grid >= model->n_col;
+            if (fused) {
+                FinishArgs &f = la.fin;
+                f.ad = ad; f.slot_param = model->d_slot_param; f.pscale = model->d_pscale;
+                f.nslot = model->nslot; f.ncol = model->n_col; f.nparam = model->n_param;
+                f.n_events = (double)model->ev.n; f.lnpq = lnconst; f.vol_over_n = von;
+                f.params = d_params; f.G = model->d_G; f.status = model->d_status; f.out = d_out;
+                f.with_grad = 1; f.n_points = (double)model->mc.n; f.partials = partials ? 1 : 0;
+                f.ar = ar;
+                f.ticket = reinterpret_cast<unsigned *>(model->d_acc + 4 * model->nslot + 2);
+                f.guv = model->d_guv;
+            }
             CK(launch_grad(la, false));
         } else {
             LaunchArgs la = args_for(model, model->ev, model->ev.part, nullptr, st, model->ev.grid_eval);
@@ -432,10 +449,11 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
         }
         CK(mark());
         CK(mark());
-        CK(launch_finish_gram(ad, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
-                              model->n_param, (double)model->ev.n, lnconst, von, d_params,
-                              model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st,
-                              (double)model->mc.n, partials ? 1 : 0, ar));
+        if (!fused)
+            CK(launch_finish_gram(ad, model->d_slot_param, model->d_pscale, model->nslot, model->n_col,
+                                  model->n_param, (double)model->ev.n, lnconst, von, d_params,
+                                  model->d_G, model->d_status, d_out, with_grad ? 1 : 0, st,
+                                  (double)model->mc.n, partials ? 1 : 0, ar));
         CK(mark());
         if (model->prof_on) model->prof_pending.push_back(marks);
         return AMP4D_OK;
@@ -757,7 +775,9 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
     }
     if (e == cudaSuccess) e = cudaMalloc(&model->d_slot_param, model->nslot * sizeof(int));
     // [data, points][nslot][hi, lo], then the Eq. 14 signal-probability sum
-    if (e == cudaSuccess) e = cudaMalloc(&model->d_acc, (4 * model->nslot + 2) * sizeof(unsigned long long));
+    // and the finishing ticket of the data kernel (zeroed with the sums)
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_acc, (4 * model->nslot + 3) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&model->d_guv, 128 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&model->h_out, (6 + 2 * model->n_param) * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&model->d_status, sizeof(unsigned));
@@ -800,6 +820,7 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
     for (cudaEvent_t e : model->ev_pool) cudaEventDestroy(e);
     if (model->d_slot_param) cudaFree(model->d_slot_param);
     if (model->d_acc) cudaFree(model->d_acc);
+    if (model->d_guv) cudaFree(model->d_guv);
     if (model->d_out) cudaFree(model->d_out);
     if (model->h_out) cudaFreeHost(model->h_out);
     if (model->d_status) cudaFree(model->d_status);

@@ -134,9 +134,11 @@ __device__ __forceinline__ void acc128_add(unsigned long long *a, double x, unsi
     const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
     atomicAdd(a, hi + carry);
 }
+// Read with ld.global.cg (L2): the words were written by other CTAs' atomics,
+// and a finishing CTA of the same launch must not see a stale L1 line.
 __device__ __forceinline__ double acc128_value(const unsigned long long *a)
 {
-    return (double)(long long)a[0] + (double)a[1] * 0x1p-64;
+    return (double)(long long)__ldcg(a) + (double)__ldcg(a + 1) * 0x1p-64;
 }
 
 // ----------------------------------------------------------------------------

@@ -11,11 +11,13 @@
 // reduce in FP64 and add their sums to exact 128-bit accumulators (acc128_add).
 // Instantiated per resonance-count bucket in amp4d_eval_nk*.cu.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
 
 #include "amp4d_device.cuh"
+#include "amp4d_finish.cuh"
 #include "amp4d_launch.h"
 
 namespace amp4d {
@@ -676,7 +678,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                                                          const float2 *__restrict__ lc, int nslot,
                                                          const float *__restrict__ meps,
                                                          const float *__restrict__ mhb,
-                                                         unsigned long long *__restrict__ acc_r)
+                                                         unsigned long long *__restrict__ acc_r,
+                                                         FinishArgs fin)
 {
     constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
     const ModelDev &md = c_md;
@@ -685,6 +688,10 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     const int tid = threadIdx.x;
     const int npair = (nslot - 1) >> 1;
     for (int i = 0; i < npair; ++i) gsl[i * BLOCK + tid] = make_float2(0.f, 0.f);
+    if constexpr (!NORM) {
+        // fused finish: rows of G u and G v, 4 per CTA, by warp 0 of the first CTAs
+        if (fin.ticket && tid < 32 && (int)blockIdx.x < fin.ncol) gram_rows_for_finish(fin, blockIdx.x);
+    }
     float2 *g = gsl + tid;
     Kahan acc0, rsum;
     int esum = 0;
@@ -850,6 +857,23 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     if constexpr (MIX) {
         __syncthreads();
         block_accumulate<BLOCK>(rsum.value(), red, acc_r, status);
+    }
+    if constexpr (!NORM) {
+        // Gram path: the CTA that draws the last ticket finishes the evaluation,
+        // once every CTA's sums are in the accumulators (each thread fences its
+        // atomics before its CTA takes a ticket), in the slot memory, which the
+        // block tail no longer reads.
+        if (fin.ticket) {
+            __shared__ int last;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) last = atomicAdd(fin.ticket, 1u) == gridDim.x - 1;
+            __syncthreads();
+            if (last) {
+                __threadfence();
+                finish_gram_body(fin, reinterpret_cast<double *>(gsl));
+            }
+        }
     }
 }
 
@@ -1037,7 +1061,8 @@ cudaError_t launch_eval_t(const LaunchArgs &a, int mode)
 template <int NK, int NZ, bool NORM, bool FX>
 cudaError_t launch_grad_k(const LaunchArgs &a)
 {
-    const size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
+    size_t smem = (size_t)a.nslot * GRAD_BLOCK * sizeof(float);
+    if (FX && !NORM && a.fin.ticket) smem = std::max(smem, finish_gram_smem(a.fin.ncol));
     constexpr int EPT = GRAD_EVENTS_PER_THREAD_CACHED, CPS = GRAD_CTAS_PER_SM_CACHED;
     constexpr int CPS1 = GRAD_CTAS_PER_SM_KFLOAT;
     const bool mix = !NORM && a.mix_eps != nullptr;
@@ -1070,7 +1095,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
         return with_const_table(a.md, a.stream, [&]() {
             kern<<<a.grid, GRAD_BLOCK, smem, a.stream>>>(a.rec, a.npad, a.n, a.wrec, a.acc, a.status,
                                                          a.lcache, a.nslot, a.mix_eps, a.mix_hb,
-                                                         a.acc_r);
+                                                         a.acc_r, a.fin);
             return cudaGetLastError();
         });
     } else {

@@ -6,6 +6,7 @@
 
 #include "amp4d_device.cuh"
 #include "amp4d_launch.h"
+#include "amp4d_finish.cuh"
 
 namespace amp4d {
 
@@ -88,15 +89,6 @@ __global__ void k_finish(const unsigned long long *__restrict__ ad, const unsign
 
 // Eq. 14 with a background: alpha = P / I_eps from the point sum of the pass that
 // ran first, into the device table (its hi + lo pair).
-__device__ __forceinline__ void store_alpha(ModelDev *md, double I, double purity, unsigned *status)
-{
-    double a = 0.0;
-    if (I > 0.0 && isfinite(I)) a = purity / I;
-    else atomicOr(status, 1u);
-    md->mahi = (float)a;
-    md->malo = (float)(a - (double)md->mahi);
-}
-
 __global__ void k_mix_alpha(const unsigned long long *__restrict__ an, double vol_over_n,
                             double purity, ModelDev *__restrict__ md, unsigned *__restrict__ status)
 {
@@ -151,103 +143,13 @@ __global__ void __launch_bounds__(256) k_finish_gram(
     int partials, const unsigned long long *__restrict__ ar, ModelDev *__restrict__ alpha_md,
     double purity)
 {
-    extern __shared__ double sG[];   // dim x dim, staged once with independent loads
-    __shared__ double u[96], v[96], Gu[96], Gv[96];
-    __shared__ double qsh, Ish;
-    const int dim = 2 * ncol, t = threadIdx.x;
-    for (int i = t; i < dim * dim; i += blockDim.x) sG[i] = G[i];
-    for (int k = t; k < ncol; k += blockDim.x) {
-        const double re = pscale[2 * k] * params[2 * k], im = pscale[2 * k] * params[2 * k + 1];
-        u[2 * k] = re; u[2 * k + 1] = -im;
-        v[2 * k] = im; v[2 * k + 1] = re;
-    }
-    __syncthreads();
-    // (Gu)_i and (Gv)_i: 8 lanes per row, fixed lane-strided order, reduced by
-    // shuffles over the 8 lanes; the loop count is uniform across the block.
-    const int lane8 = t & 7, rows_per_pass = blockDim.x >> 3;
-    for (int base = 0; base < dim; base += rows_per_pass) {
-        const int i = base + (t >> 3);
-        double a = 0.0, b = 0.0;
-        if (i < dim)
-            for (int j = lane8; j < dim; j += 8) {
-                a = fma(sG[i * dim + j], u[j], a);
-                b = fma(sG[i * dim + j], v[j], b);
-            }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (i < dim && lane8 == 0) { Gu[i] = a; Gv[i] = b; }
-    }
-    __syncthreads();
-    if (t < 32) {
-        double q = 0.0;
-        for (int i = t; i < dim; i += 32) q = fma(u[i], Gu[i], fma(v[i], Gv[i], q));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        if (t == 0) qsh = q;
-    }
-    __syncthreads();
-    const double q = qsh;
-    if (alpha_md) {   // Eq. 14 with a background: only alpha = P / I_eps, before the data pass
-        if (t == 0) store_alpha(alpha_md, vol_over_n * q, purity, const_cast<unsigned *>(status));
-        return;
-    }
-    if (partials) {
-        // Shard partials (layout of k_partials) with T = V (u^T G u + v^T G v).
-        const double volume = vol_over_n * n_points;
-        if (t == 0) {
-            out[0] = acc128_value(ad);
-            out[1] = lnpq;
-            out[2] = n_events;
-            out[3] = volume * q;
-            out[4] = n_points;
-            out[5] = (double)*status;
-        }
-        if (!with_grad) return;
-        for (int p = t; p < 2 * nparam; p += blockDim.x) out[6 + p] = 0.0;
-        __syncthreads();
-        for (int s = 1 + t; s < nslot; s += blockDim.x) {
-            const int p = slot_param[s];
-            if (p < 0) continue;
-            out[6 + p] = pscale[p] * acc128_value(ad + 2 * s);
-            if (p < dim) {
-                const int k = p >> 1;
-                const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1])
-                                          : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
-                out[6 + nparam + p] = volume * pscale[p] * dq;
-            }
-        }
-        return;
-    }
-    if (t == 0) {
-        const double I = vol_over_n * q;
-        unsigned st = *status;
-        const double rd0 = acc128_value(ad);
-        const double nll = ar ? -2.0 * (rd0 + lnpq) : -2.0 * (rd0 + lnpq - n_events * log(I));
-        if (!(I > 0.0) || !isfinite(nll)) st |= 1u;
-        out[0] = st ? INFINITY : nll;
-        out[1] = rd0;
-        out[2] = lnpq;
-        out[3] = I;
-        out[4] = n_events;
-        out[5] = (double)st;
-        Ish = st ? 0.0 : I;
-    }
-    if (!with_grad) return;
-    __syncthreads();
-    const double Iv = Ish;
-    const double nI = ar ? acc128_value(ar) : n_events;   // coefficient of dI / I
-    for (int p = t; p < nparam; p += blockDim.x) out[6 + p] = 0.0;
-    __syncthreads();
-    for (int s = 1 + t; s < nslot; s += blockDim.x) {
-        const int p = slot_param[s];
-        if (p < 0 || p >= dim || Iv == 0.0) continue;
-        const int k = p >> 1;
-        const double dq = (p & 1) ? 2.0 * (Gv[2 * k] - Gu[2 * k + 1]) : 2.0 * (Gu[2 * k] + Gv[2 * k + 1]);
-        out[6 + p] = -2.0 * pscale[p] * (acc128_value(ad + 2 * s) - nI * vol_over_n * dq / Iv);
-    }
+    extern __shared__ double sG[];   // dim x dim, then u, v, Gu, Gv (96 each)
+    FinishArgs f;
+    f.ad = ad; f.slot_param = slot_param; f.pscale = pscale; f.nslot = nslot; f.ncol = ncol;
+    f.nparam = nparam; f.n_events = n_events; f.lnpq = lnpq; f.vol_over_n = vol_over_n;
+    f.params = params; f.G = G; f.status = status; f.out = out; f.with_grad = with_grad;
+    f.n_points = n_points; f.partials = partials; f.ar = ar; f.alpha_md = alpha_md; f.purity = purity;
+    finish_gram_body(f, sG);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,7 +546,7 @@ cudaError_t launch_finish_gram(const unsigned long long *ad, const int *slot_par
                                double n_points, int partials, const unsigned long long *ar,
                                ModelDev *alpha_md, double purity)
 {
-    const size_t smem = (size_t)4 * ncol * ncol * sizeof(double);   // dim x dim
+    const size_t smem = finish_gram_smem(ncol);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_finish_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -10,6 +10,28 @@ namespace amp4d {
 struct ModelDev;
 struct ModelStatic;
 
+// Inputs of the Gram-path finishing step (finish_gram_body in amp4d_finish.cuh).
+struct FinishArgs {
+    const unsigned long long *ad = nullptr;  // the data pass's 128-bit sums
+    const int *slot_param = nullptr;
+    const double *pscale = nullptr;
+    int nslot = 0, ncol = 0, nparam = 0;
+    double n_events = 0.0, lnpq = 0.0, vol_over_n = 0.0;
+    const double *params = nullptr, *G = nullptr;
+    const unsigned *status = nullptr;
+    double *out = nullptr;
+    int with_grad = 0;
+    double n_points = 0.0;
+    int partials = 0;
+    const unsigned long long *ar = nullptr;
+    ModelDev *alpha_md = nullptr;
+    double purity = 1.0;
+    // fused into the data kernel: the CTA that draws the last ticket finishes, and
+    // CTAs 0 .. dim/2 - 1 write the rows of G u and G v (2 dim doubles) to guv
+    unsigned *ticket = nullptr;
+    double *guv = nullptr;
+};
+
 struct LaunchArgs {
     const float *rec;        // event records, REC_* x npad
     int64_t npad, n;         // padded and true event counts
@@ -31,6 +53,8 @@ struct LaunchArgs {
     const float *mix_eps = nullptr, *mix_hb = nullptr;
     unsigned long long *acc_r = nullptr;
     bool mt = false;                 // data sets with a flavour mistag: S and S(-phi) per event
+    // Gram path: the data kernel's last CTA finishes the evaluation (fin.ticket set)
+    FinishArgs fin;
 };
 
 // Resident CTAs per SM of the adjoint kernels (their __launch_bounds__).  The

@@ -508,25 +508,50 @@ __global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_grad(const __nv_bfloat16
 }
 
 // grad = sum over data blocks + (sum over uniform blocks) / S_u; loss terms.
-// out: grad[MLP_P] (FP64), then [MLP_P] = loss.
-__global__ void k_mlp_grad_finish(const float *__restrict__ part, int nblk_d, int nblk_u,
-                                  int64_t nd, int64_t nu, double *__restrict__ out)
+// out: grad[MLP_P] (FP64), then [MLP_P] = loss.  CTA b takes the 32 parameters
+// 32 b .. 32 b + 31 (lane = parameter, coalesced rows); its 8 warps sum every
+// 8th partial row in FP64 and the warps' sums are added in a fixed order, so
+// the result does not depend on timing.  Every CTA forms S_u itself from the
+// uniform blocks' last column (one warp, shuffle reduction); CTA 0 writes the loss.
+constexpr int FIN_WARPS = 8;
+__global__ void __launch_bounds__(32 * FIN_WARPS) k_mlp_grad_finish(const float *__restrict__ part, int nblk_d,
+                                                                   int nblk_u, int64_t nd, int64_t nu,
+                                                                   double *__restrict__ out)
 {
+    __shared__ double sa[FIN_WARPS][32], sb[FIN_WARPS][32];
     __shared__ double su_sh;
-    if (threadIdx.x == 0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 32 + lane;
+    if (warp == 0) {
         double su = 0.0, sl = 0.0;
-        for (int b = 0; b < nblk_u; ++b) su += part[(int64_t)(nblk_d + b) * (MLP_P + 1) + MLP_P];
-        for (int b = 0; b < nblk_d; ++b) sl += part[(int64_t)b * (MLP_P + 1) + MLP_P];
-        su_sh = su;
-        out[MLP_P] = -sl / (double)nd + log(16.0 * su / (double)nu);
+        for (int b = lane; b < nblk_u; b += 32) su += part[(int64_t)(nblk_d + b) * (MLP_P + 1) + MLP_P];
+        for (int b = lane; b < nblk_d; b += 32) sl += part[(int64_t)b * (MLP_P + 1) + MLP_P];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        }
+        if (lane == 0) {
+            su_sh = su;
+            if (blockIdx.x == 0) out[MLP_P] = -sl / (double)nd + log(16.0 * su / (double)nu);
+        }
     }
+    double a = 0.0, b = 0.0;
+    if (q < MLP_P) {
+        for (int k = warp; k < nblk_d; k += FIN_WARPS) a += part[(int64_t)k * (MLP_P + 1) + q];
+        for (int k = warp; k < nblk_u; k += FIN_WARPS) b += part[(int64_t)(nblk_d + k) * (MLP_P + 1) + q];
+    }
+    sa[warp][lane] = a;
+    sb[warp][lane] = b;
     __syncthreads();
-    const double su = su_sh;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < MLP_P; q += gridDim.x * blockDim.x) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < nblk_d; ++k) a += part[(int64_t)k * (MLP_P + 1) + q];
-        for (int k = 0; k < nblk_u; ++k) b += part[(int64_t)(nblk_d + k) * (MLP_P + 1) + q];
-        out[q] = a + b / su;
+    if (warp == 0 && q < MLP_P) {
+        double ta = 0.0, tb = 0.0;
+#pragma unroll
+        for (int w = 0; w < FIN_WARPS; ++w) {
+            ta += sa[w][lane];
+            tb += sb[w][lane];
+        }
+        out[q] = ta + tb / su_sh;
     }
 }
 
@@ -566,7 +591,7 @@ cudaError_t launch_mlp_grad(const __nv_bfloat16 *wb, const float *xd, int64_t nd
     cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_mlp_grad<<<nbd + nbu, MLP_THREADS, smem, st>>>(wb, xd, nd, xu, nu, nbd, part);
-    k_mlp_grad_finish<<<(MLP_P + 255) / 256, 256, 0, st>>>(part, nbd, nbu, nd, nu, out);
+    k_mlp_grad_finish<<<(MLP_P + 31) / 32, 32 * FIN_WARPS, 0, st>>>(part, nbd, nbu, nd, nu, out);
     return cudaGetLastError();
 }
 
