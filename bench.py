@@ -168,12 +168,13 @@ def kernel_sources_sha16():
 def bytes_per_event(res_list, cached=True, float_names=(), norm=False):
     """Algorithmic bytes read per event (or normalisation point) by the adjoint
     kernel: the FP32 records it reads and, on the cached path, one complex FP32
-    lineshape per fixed resonance.  Records: 17 with a Z, 8 without.  The cached
-    kernel reads cos/sin phi instead of phi, the K pi mass and momenta only when a
-    K* lineshape is computed per event, and the J/psi pi mass and momenta only
-    when a Z lineshape is; normalisation points add their weight."""
-    has_z = any(r.chain == W.CHAIN_Z for r in res_list)
-    nrec = 17 if has_z else 8
+    lineshape per fixed resonance and the four complex Z-chain angular factors of
+    each Z.  Records: 17 with a Z, 8 without.  The cached kernel reads cos/sin phi
+    instead of phi, none of the six Z-chain angle records, the K pi mass and
+    momenta only when a K* lineshape is computed per event, and the J/psi pi mass
+    and momenta only when a Z lineshape is; normalisation points add their weight."""
+    n_z = sum(1 for r in res_list if r.chain == W.CHAIN_Z)
+    nrec = 17 if n_z else 8
     n_fixed = len(res_list)
     if cached:
         fl = [r for r in res_list if r.name in float_names]
@@ -181,9 +182,11 @@ def bytes_per_event(res_list, cached=True, float_names=(), norm=False):
         nrec -= 1                                                  # phi
         if not any(r.chain == W.CHAIN_KSTAR for r in fl):
             nrec -= 3                                              # m, p, q
-        if has_z and not any(r.chain == W.CHAIN_Z for r in fl):
-            nrec -= 3                                              # m_psi pi, p_Z, q_Z
-    return 4 * (nrec + (1 if norm else 0)) + (8 * n_fixed if cached else 0)
+        if n_z:
+            nrec -= 6                                              # the Z angles (cached factors)
+            if not any(r.chain == W.CHAIN_Z for r in fl):
+                nrec -= 3                                          # m_psi pi, p_Z, q_Z
+    return 4 * (nrec + (1 if norm else 0)) + ((8 * n_fixed + 32 * n_z) if cached else 0)
 
 
 def make_workload(cfg, rank=0):
@@ -280,13 +283,21 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
     # couplings near the kinematic edge) whose errors are not meaningful.
     lam, V = r.well_constrained()
     pulls = (V.T @ d) * np.sqrt(lam / 2.0)
+    # The normalisations are compared from one reference minimum: the fit with the
+    # first uniform sample started at the generating point.  The likelihood of this
+    # 50-parameter model has secondary minima, and a fit from the perturbed start can
+    # reach one of them depending on the normalisation sample, which says nothing
+    # about the accuracy of the normalisation itself (chi2 measure below:
+    # perturbed_start_vs_reference).
+    r_t = F.fit(m.eval_nll_grad, par, p_true, tol=tol)
+    p_u = par.to_params(r_t.theta)
     # The same fit with an independent uniform normalisation sample: the spread
     # between the two minima, in the same units, is the statistical error of the
     # Monte Carlo normalisation integral (N/M = events / points).
     nm2 = W.uniform_points(cfg.n_norm, cfg.norm_seed + 7919)
     m.set_norm_points(*(torch.from_numpy(a).cuda() for a in nm2))
-    r2 = F.fit(m.eval_nll_grad, par, p0, tol=tol)
-    d2 = r2.theta - r.theta
+    r2 = F.fit(m.eval_nll_grad, par, p_u, tol=tol)
+    d2 = r2.theta - r_t.theta
     d2[1:nph:2] = (d2[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
     spread = (V.T @ d2) * np.sqrt(lam / 2.0)
     # The same fit normalised by the learned proposal: the MLP density trained on
@@ -297,12 +308,7 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
     m.proposal_train(tuple(t[:1 << 20] for t in ev), seed=11)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    # The learned-normalisation fits start from the uniform-points minimum: the
-    # likelihood of this 50-parameter model has secondary minima, and a fit from the
-    # perturbed start can reach one of them depending on the normalisation sample
-    # (measured below: from_perturbed_start), which says nothing about the accuracy
-    # of the normalisation itself.
-    p_u = par.to_params(r.theta)
+    # The learned-normalisation fits start from the reference minimum.
     learned = []
     for sd in (101, 102):
         pts, w = m.proposal_sample(cfg.n_norm, sd)
@@ -339,7 +345,7 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
     dp = rp.theta - par.from_params(p_true)
     dp[1:nph:2] = (dp[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
     zp = (V.T @ dp) * np.sqrt(lam / 2.0)
-    du = rp.theta - r.theta
+    du = rp.theta - r_t.theta
     du[1:nph:2] = (du[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
     zu = (V.T @ du) * np.sqrt(lam / 2.0)
     dgg = gram_t[1][0].theta - gram_t[0][0].theta
@@ -347,7 +353,7 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
     spread_g = (V.T @ dgg) * np.sqrt(lam / 2.0)
     shift_u = []
     for rg, _ in gram_t:
-        dd = rg.theta - r.theta
+        dd = rg.theta - r_t.theta
         dd[1:nph:2] = (dd[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
         shift_u.append(float(np.sqrt(np.mean(((V.T @ dd) * np.sqrt(lam / 2.0)) ** 2))))
     gram_out = {"proposal_train_s": t_train_g,
@@ -362,7 +368,7 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
                                          "fval_minus_uniform_fit_fval_on_this_sample":
                                              float(rp.fval - gram_t[0][0].fval)},
                 "note": "proposal trained on sum_k |B_k|^2 p q (per-column samples mixed by G_kk); "
-                        "fits start from the uniform-points minimum"}
+                        "fits start from the reference minimum"}
     # Hessian-free measures on the likelihood of the first uniform sample (f = -2 ln L):
     # the sum of squared pulls of a minimum against the truth is f(truth) - f(min),
     # and the squared distance between two minima a, b in units of the errors is
@@ -383,12 +389,28 @@ def full_fit(cfg, A, seed=2718, tol=0.1):
         return 2.0 * (f_at(a) + f_at(b) - 2.0 * f_at(midpoint(a, b))) / par.n_free
 
     th_true = par.from_params(p_true)
-    chi2 = {"truth_vs_uniform_fit": (f_at(th_true) - f_at(r.theta)) / par.n_free,
-            "uniform_sample_shift": shift_chi2(r.theta, r2.theta),
+    f_ref = f_at(r_t.theta)
+
+    def loss(th):
+        return (f_at(th) - f_ref) / par.n_free
+
+    chi2 = {"loss_vs_reference": {
+                "note": "[f(theta) - f(reference)] / n_free on the first uniform sample's "
+                        "likelihood: the mean squared shift in standard deviations for a "
+                        "quadratic f; needs neither a Hessian nor convexity between minima",
+                "perturbed_start": loss(r.theta), "uniform_sample_2": loss(r2.theta),
+                "learned_S": [loss(x.theta) for x, _ in learned],
+                "gram_targeted": [loss(x.theta) for x, _ in gram_t]},
+            "truth_vs_uniform_fit": (f_at(th_true) - f_at(r.theta)) / par.n_free,
+            "perturbed_start_vs_reference": shift_chi2(r.theta, r_t.theta),
+            "uniform_sample_shift": shift_chi2(r_t.theta, r2.theta),
+            "learned_S_vs_reference": [shift_chi2(r_t.theta, x.theta) for x, _ in learned],
             "learned_S_sample_shift": shift_chi2(learned[0][0].theta, learned[1][0].theta),
+            "gram_targeted_vs_reference": [shift_chi2(r_t.theta, x.theta) for x, _ in gram_t],
             "gram_targeted_sample_shift": shift_chi2(gram_t[0][0].theta, gram_t[1][0].theta),
             "note": "per free parameter, on the first uniform sample's likelihood; 1 is one "
-                    "standard deviation per parameter"}
+                    "standard deviation per parameter, negative means another valley; the "
+                    "reference is the first uniform sample's fit from the generating point"}
     learned_out = {"proposal_train_s": t_train,
                    "converged": [bool(rl.converged) for rl, _ in learned],
                    "rms_pull_vs_truth": [float(np.sqrt(np.mean(x ** 2))) for x in pl],

@@ -295,7 +295,9 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
 amp4d_status ensure_lcache(amp4d_model *model, EventSet &s, cudaStream_t st)
 {
     if (s.lcache_valid || s.n == 0) return AMP4D_OK;
-    if (!s.lcache) CK(cudaMalloc(&s.lcache, (size_t)model->res.size() * s.npad * sizeof(float2)));
+    // lineshape rows, then the four angular-factor rows of each Z
+    const size_t rows = model->res.size() + 4 * (size_t)model->nZ;
+    if (!s.lcache) CK(cudaMalloc(&s.lcache, rows * s.npad * sizeof(float2)));
     LaunchArgs a = args_for(model, s, nullptr, nullptr, st, model->nsm * 8);
     CK(launch_lcache(a, s.lcache));
     s.lcache_valid = true;
@@ -913,6 +915,8 @@ amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mist
             if (nt) cudaFree(nt);
             return fail(model, AMP4D_ERR_CUDA, std::string("set_flavour: ") + cudaGetErrorString(e));
         }
+        // the cached Z-chain angular factors follow the rewritten phi-odd records
+        if (model->nZ > 0) s.lcache_valid = false;
     }
     if (s.tag) cudaFree(s.tag);
     s.tag = nt;

@@ -390,19 +390,6 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             }
         }
     if constexpr (NZ > 0) {
-        float2 ephz[NE];
-        float cZ[NE], sZ[NE], ca[NE], sa[NE];
-        float d1t[NE][3][2];
-#pragma unroll
-        for (int j = 0; j < NE; ++j) {
-            cZ[j] = r[j][REC_CZ];
-            const float ctz = r[j][REC_CTZ];
-            ephz[j] = make_float2(r[j][REC_CPZ], r[j][REC_SPZ]);
-            ca[j] = r[j][REC_CA]; sa[j] = r[j][REC_SA];
-            sZ[j] = sqrtf(fmaxf(0.0f, fmaf(-cZ[j], cZ[j], 1.0f)));
-            const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
-            wigner_1(ctz, stz, d1t[j]);
-        }
         if constexpr (LFM >= 1) {
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
@@ -415,25 +402,37 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
             const ResDev &rs = md.zr[z];
+            // the angular factors from the basis cache: rows n_res + 4 z + (Om0 x=0, Om0 x=1,
+            // Om1 x=0, Om1 x=1)
+            const float2 *zr = lc + (int64_t)(md.n_res + 4 * z) * lcn;
+            if constexpr (NE == 2) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 t = __ldcs(reinterpret_cast<const float4 *>(zr + q * lcn + e[0]));
+                    float2 *dst0 = q < 2 ? &ev[0].Om0[z][q] : &ev[0].Om1[z][q - 2];
+                    float2 *dst1 = q < 2 ? &ev[1].Om0[z][q] : &ev[1].Om1[z][q - 2];
+                    *dst0 = make_float2(t.x, t.y);
+                    *dst1 = make_float2(t.z, t.w);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NE; ++j)
+#pragma unroll
+                    for (int x = 0; x < 2; ++x) {
+                        ev[j].Om0[z][x] = __ldg(zr + x * lcn + e[j]);
+                        ev[j].Om1[z][x] = __ldg(zr + (2 + x) * lcn + e[j]);
+                    }
+            }
 #pragma unroll
             for (int j = 0; j < NE; ++j) {
                 float2 LA = LZ[j][z];
                 if constexpr (LFM >= 1) {
                     if (rs.fpos >= 0) LA = lineshape(rs, ev[j].mZ, ev[j].invmZ, ev[j].pZ, ev[j].qZ).A;
                 }
-                float dz0, dz1;
-                wigner_l0(rs, make_float2(cZ[j], cZ[j]), sZ[j], dz0, dz1);
                 ev[j].AZ[z] = LA;
 #pragma unroll
                 for (int x = 0; x < 2; ++x) {
-                    const float2 eal = make_float2(ca[j], x == 0 ? sa[j] : -sa[j]);
-                    float2 o0 = cscale(eal, dz0 * d1t[j][1][x]);
-                    float2 t = cscale(ephz[j], -dz1 * d1t[j][2][x]);
-                    const float2 ephm = make_float2(ephz[j].x, -ephz[j].y);
-                    t = cadd(t, cscale(ephm, (float)rs.eta * dz1 * d1t[j][0][x]));
-                    float2 o1 = cmul(t, eal);
-                    ev[j].Om0[z][x] = o0;
-                    ev[j].Om1[z][x] = o1;
+                    const float2 o0 = ev[j].Om0[z][x], o1 = ev[j].Om1[z][x];
                     float2 s = make_float2(0.f, 0.f);
                     if (rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
                     if (rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
@@ -536,12 +535,41 @@ enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
 
 // Records read by the all-cached kernels (FX): all but phi (its cosine and sine
 // are records); the K* (Z) masses and momenta only when floated K* (Z)
-// lineshapes are computed per event (LFM 2, LFM >= 1).
-template <bool FX, int LFM = 0>
+// lineshapes are computed per event (LFM 2, LFM >= 1); the Z-chain angles only
+// when their angular factors are not read from the basis cache (ZC).
+template <bool FX, int LFM = 0, bool ZC = false>
 __device__ __forceinline__ constexpr bool record_used(int k)
 {
     return !FX || !(k == REC_PHI || (LFM < 2 && (k == REC_M || k == REC_P || k == REC_Q)) ||
-                    (LFM < 1 && (k == REC_MZ || k == REC_PZ || k == REC_QZ)));
+                    (LFM < 1 && (k == REC_MZ || k == REC_PZ || k == REC_QZ)) ||
+                    (ZC && k >= REC_CZ && k <= REC_SA));
+}
+
+// Z-chain angular factors of one event (Eq. 10-11) for each muon helicity xi
+// (x = 0: +1, x = 1: -1): with the Z's own d^J and its parity factor eta,
+//   Om0 = e^{i xi alpha} d^J_00(theta_Z) d^1_{0 xi}(theta~_psi)            (l' = 0),
+//   Om1 = e^{i xi alpha} [-d^J_{01} e^{i phi~} d^1_{1 xi} + eta d^J_{01} e^{-i phi~} d^1_{-1 xi}]
+// in the kernels' normalisation (d1 = -sin P_J' stands for sqrt(J (J+1)) d^J_{10}).
+// They do not depend on any parameter: the all-cached kernels read them from the
+// basis cache, built with this same arithmetic.
+__device__ __forceinline__ void z_angular(const ResDev &rs, float cZ, float ctz, float2 ephz, float ca,
+                                          float sa, float2 (&o0)[2], float2 (&o1)[2])
+{
+    const float sZ = sqrtf(fmaxf(0.0f, fmaf(-cZ, cZ, 1.0f)));
+    const float stz = sqrtf(fmaxf(0.0f, fmaf(-ctz, ctz, 1.0f)));
+    float d1t[3][2];
+    wigner_1(ctz, stz, d1t);
+    float dz0, dz1;
+    wigner_l0(rs, make_float2(cZ, cZ), sZ, dz0, dz1);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        const float2 eal = make_float2(ca, x == 0 ? sa : -sa);
+        o0[x] = cscale(eal, dz0 * d1t[1][x]);
+        float2 t = cscale(ephz, -dz1 * d1t[2][x]);
+        const float2 ephm = make_float2(ephz.x, -ephz.y);
+        t = cadd(t, cscale(ephm, (float)rs.eta * dz1 * d1t[0][x]));
+        o1[x] = cmul(t, eal);
+    }
 }
 
 template <int NK, int NZ, int MODE, int BLOCK, bool FX, bool MIX = false, bool MT = false>
@@ -715,7 +743,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             valid[1] = e0 + 1 < n;
 #pragma unroll
             for (int k = 0; k < NREC; ++k) {
-                const float2 t = record_used<true, LFM>(k)
+                const float2 t = record_used<true, LFM, true>(k)
                                      ? __ldcs(reinterpret_cast<const float2 *>(rec + k * npad + e0))
                                      : make_float2(0.f, 0.f);
                 v[0][k] = t.x;
@@ -729,7 +757,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
                 e[j] = valid[j] ? ej : e0;
 #pragma unroll
                 for (int k = 0; k < NREC; ++k)
-                    v[j][k] = record_used<true, LFM>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
+                    v[j][k] = record_used<true, LFM, true>(k) ? __ldg(rec + k * npad + e[j]) : 0.f;
             }
         }
         EvState<NK, NZ> ev[NE];
@@ -1127,9 +1155,11 @@ cudaError_t launch_grad_t(const LaunchArgs &a, bool norm)
 }
 
 // Basis cache: A'_R (Eq. 2-3 without its column constant) of every resonance for
-// every event of a set, [internal resonance][npad] complex FP32.  The per-event
-// angular factors (Eq. 4, 10) stay per evaluation: they are cheap polynomials,
-// while the lineshapes carry the square roots and reciprocals.
+// every event of a set, [internal resonance][npad] complex FP32, then for each Z
+// its four angular factors (z_angular: Om0 and Om1 for xi = +1, -1), rows
+// n_res + 4 z .. n_res + 4 z + 3.  The K* angular factors (Eq. 4) stay per
+// evaluation: they are cheap polynomials, while the lineshapes carry the square
+// roots and reciprocals and the Z-chain factors about 45 instructions per event.
 template <int NK, int NZ>
 __global__ void __launch_bounds__(256) k_build_lcache(const float *__restrict__ rec, int64_t npad,
                                                       const ModelDev *__restrict__ gmd,
@@ -1148,9 +1178,20 @@ __global__ void __launch_bounds__(256) k_build_lcache(const float *__restrict__ 
         if constexpr (NZ > 0) {
             const float mZ = rec[REC_MZ * npad + e], pZ = rec[REC_PZ * npad + e];
             const float qZ = rec[REC_QZ * npad + e], invmZ = __frcp_rn(mZ);
+            const float cZ = rec[REC_CZ * npad + e], ctz = rec[REC_CTZ * npad + e];
+            const float2 ephz = make_float2(rec[REC_CPZ * npad + e], rec[REC_SPZ * npad + e]);
+            const float ca = rec[REC_CA * npad + e], sa = rec[REC_SA * npad + e];
 #pragma unroll
-            for (int z = 0; z < NZ; ++z)
+            for (int z = 0; z < NZ; ++z) {
                 lc[(nK + z) * npad + e] = lineshape(md.res[nK + z], mZ, invmZ, pZ, qZ).A;
+                float2 o0[2], o1[2];
+                z_angular(md.zr[z], cZ, ctz, ephz, ca, sa, o0, o1);
+                float2 *zr = lc + (int64_t)(md.n_res + 4 * z) * npad;
+                zr[e] = o0[0];
+                zr[npad + e] = o0[1];
+                zr[2 * npad + e] = o1[0];
+                zr[3 * npad + e] = o1[1];
+            }
         }
     }
 }

@@ -190,15 +190,18 @@ def test_z_sensitivity(A):
 
 def test_learned_normalisation_reproduces_the_uniform_minimum(A):
     """The learned normalisation serves the fit: 10 K* + Z(4430), 10^6 events the GPU
-    generator draws from the model.  The fit with 2^24 uniform normalisation points
-    starts from a perturbed point; the fits with two independent 2^20-point samples
-    of the proposal aimed at the Gram matrix (target sum_k |B_k|^2 p q) start from its
-    minimum, so that all three minimise in the same basin (the likelihood of this
-    50-parameter model has secondary minima, which a fit from the perturbed start can
-    reach depending on the normalisation sample).  Every fit converges, and along
-    the directions the data constrain (the uniform fit's Hessian, eigenvalues above
-    1e-6 of the largest) the minima agree within one standard deviation per
-    direction (rms), pairwise."""
+    generator draws from the model.  The reference likelihood f = -2 ln L uses 2^26
+    uniform normalisation points; its minimum is fitted from the generating point.
+    From that minimum, fits with 2^24 uniform points and with two independent
+    2^20-point samples of the proposal aimed at the Gram matrix (target
+    sum_k |B_k|^2 p q) all converge, and each of their minima lies within one
+    standard deviation per free parameter of the reference: on the reference
+    likelihood, [f(theta) - f(theta_ref)] / n_free < 1 (for a quadratic f this is
+    the mean squared shift in standard deviations).  The measure needs neither a
+    Hessian, which finite differences give poorly along this model's nearly flat
+    directions, nor convexity between the minima: the likelihood has several nearby
+    valleys of almost equal depth, and a fit started at one minimum with another
+    normalisation sample can end in a neighbouring one."""
     cfg = W.CONFIGS["learned"]
     res = cfg.resonances
     cols = W.columns(res)
@@ -209,31 +212,28 @@ def test_learned_normalisation_reproduces_the_uniform_minimum(A):
     m = A.Model(res, path=A.AMP4D_PATH_CACHED)
     ev = m.generate(p_true, 1_000_000, 77)
     m.set_events(*ev)
-    nm = W.uniform_points(1 << 24, 4321)
-    m.set_norm_points(*(torch.from_numpy(a).cuda() for a in nm))
+    one = np.ones(1, dtype=np.float32)
+
+    def uniform(n, seed):     # uniform points, w = V p q (one-cell grid)
+        pts, w, _ = A.grid_sample(one, (1, 1, 1, 1), 1.0, seed, n)
+        m.set_norm_points(*pts, w=w, volume=1.0)
+
     par = F.Parametrization(len(c), 0, fixed_col=fixed, polar=True)
-    c0 = W.perturbed_start(c)
-    c0[fixed] = 1.0
-    r_u = F.fit(m.eval_nll_grad, par, W.couplings_to_params(c0), tol=0.1)
+    uniform(1 << 26, 9000)
+    r_ref = F.fit(m.eval_nll_grad, par, p_true, tol=0.1)
+    start = par.to_params(r_ref.theta)
+    uniform(1 << 24, 9101)
+    fits = {"uniform 2^24": F.fit(m.eval_nll_grad, par, start, tol=0.1)}
     m.proposal_train_gram(p_true, n=1 << 20, seed=12)
-    r_l = []
-    for sd in (201, 202):
+    for k, sd in enumerate((201, 202)):
         pts, w = m.proposal_sample(1 << 20, sd)
         m.set_norm_points(*pts, w=w, volume=1.0)
-        r_l.append(F.fit(m.eval_nll_grad, par, par.to_params(r_u.theta), tol=0.1))
-    lam, V = r_u.well_constrained()
-    nph = 2 * (len(c) - 1)
-
-    def shift(a, b):
-        d = b - a
-        d[1:nph:2] = (d[1:nph:2] + math.pi) % (2 * math.pi) - math.pi
-        z = (V.T @ d) * np.sqrt(lam / 2.0)
-        return float(np.sqrt(np.mean(z * z)))
-
-    s12 = shift(r_l[0].theta, r_l[1].theta)
-    s1u, s2u = shift(r_u.theta, r_l[0].theta), shift(r_u.theta, r_l[1].theta)
-    print("learned-normalisation minima (rms over %d constrained directions, in sigma): between "
-          "samples %.3f, to the uniform minimum %.3f %.3f; converged %s" % (
-              len(lam), s12, s1u, s2u, [bool(r.converged) for r in [r_u] + r_l]))
-    assert r_u.converged and all(r.converged for r in r_l)
-    assert s12 < 1 and s1u < 1 and s2u < 1
+        fits["learned %d" % (k + 1)] = F.fit(m.eval_nll_grad, par, start, tol=0.1)
+    uniform(1 << 26, 9000)
+    f_ref = m.eval_nll(par.to_params(r_ref.theta))
+    loss = {k: (m.eval_nll(par.to_params(r.theta)) - f_ref) / par.n_free for k, r in fits.items()}
+    print("reference-likelihood loss per free parameter: " +
+          ", ".join("%s %.3f (edm %.1e)" % (k, loss[k], fits[k].edm) for k in fits) +
+          "; converged %s" % [bool(r.converged) for r in [r_ref] + list(fits.values())])
+    assert r_ref.converged and all(r.converged for r in fits.values())
+    assert all(v < 1 for v in loss.values())
