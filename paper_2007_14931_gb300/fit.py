@@ -99,15 +99,26 @@ class MinResult:
     history: list = field(default_factory=list)
 
 
-def migrad(fg, x0, tol=0.1, errordef=1.0, maxiter=500, init_step=None, V0=None):
+def migrad(fg, x0, tol=0.1, errordef=1.0, maxiter=500, init_step=None, V0=None, f_noise=None):
     """Minimise f with gradient: fg(x) -> (f, g).  Returns a MinResult.  V0: an
-    initial inverse-Hessian estimate (positive definite), e.g. from HESSE."""
+    initial inverse-Hessian estimate (positive definite), e.g. from HESSE.
+
+    f_noise: the absolute rounding noise of f (default 1e-9 |f(x0)|).  A sum of
+    millions of single-precision log-likelihood terms carries noise of order
+    1e-3, as large as the decreases left near the minimum, where the sufficient-
+    decrease test on f alone then fails at random.  A step whose expected
+    decrease is below 10 f_noise is therefore also accepted when f has not risen
+    by more than the noise and the directional derivative has shrunk,
+    |g(x + a dx) . dx| < |g(x) . dx|: the gradient is accurate where f is not.
+    """
     x = np.array(x0, dtype=np.float64)
     n = len(x)
     f, g = fg(x)
     nfcn = 1
     if not math.isfinite(f):
         raise ValueError("starting point has a non-finite function value")
+    if f_noise is None:
+        f_noise = 1e-9 * max(abs(f), 1.0)
     if V0 is not None:
         V = np.array(V0, dtype=np.float64)
         diag = 1.0 / np.maximum(np.diag(V), 1e-300)
@@ -147,6 +158,10 @@ def migrad(fg, x0, tol=0.1, errordef=1.0, maxiter=500, init_step=None, V0=None):
             nfcn += 1
             if math.isfinite(fn) and fn <= f + 1e-4 * alpha * slope:
                 f_new, g_new = fn, gn
+                break
+            if (math.isfinite(fn) and -alpha * slope < 10.0 * f_noise and fn <= f + 10.0 * f_noise
+                    and abs(gn @ dx) < abs(slope)):
+                f_new, g_new = fn, gn   # within the noise of f: decided by the gradient
                 break
             if math.isfinite(fn):
                 # minimum of the parabola through f(0), f'(0) = slope, f(alpha)

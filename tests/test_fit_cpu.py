@@ -34,6 +34,37 @@ def test_migrad_rosenbrock():
     assert np.allclose(r.x, [1, 1], atol=1e-3)
 
 
+def _noisy_quadratic(seed, n=30, amp=1e-2):
+    """0.5 d^T H d (condition number 1e5) plus 5e7 and a non-smooth deterministic
+    term of amplitude amp, with the exact gradient: f carries rounding-like noise
+    comparable to the decreases left near the minimum, g does not."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    H = U @ np.diag(np.logspace(0, 5, n)) @ U.T
+    xmin = rng.normal(size=n)
+    w = rng.normal(size=n)
+
+    def fg(x):
+        d = x - xmin
+        return 0.5 * d @ H @ d + 5e7 + amp * math.sin(1e7 * float(x @ w)), H @ d
+
+    return fg, xmin + 0.3 * rng.normal(size=n), xmin
+
+
+def test_migrad_converges_when_f_is_noisier_than_the_last_decreases():
+    """Near the minimum the line search decides on the directional derivative
+    where f's noise hides the decrease; with that fallback switched off
+    (f_noise = 0) most of these minimisations stop before the EDM criterion."""
+    failed_without = 0
+    for seed in range(5):
+        fg, x0, xmin = _noisy_quadratic(seed)
+        r = F.migrad(fg, x0, tol=0.1)
+        assert r.converged and r.edm < 2e-4
+        r0 = F.migrad(fg, x0, tol=0.1, f_noise=0.0)
+        failed_without += not r0.converged
+    assert failed_without >= 3
+
+
 def test_polar_parametrisation_round_trip_and_chain_rule():
     par = F.Parametrization(n_cols=4, n_mg=2, fixed_col=1, polar=True)
     rng = np.random.default_rng(3)
