@@ -323,10 +323,14 @@ const char *amp4d_shard_last_error(void);
  * x = (Re B_0, Im B_0, Re B_1, ...) over the normalisation points (State-of-
  * the-art section: numerical normalisation; Eq. 5, 12 for B), so that
  * I = (V / N_mc) (u^T G u + v^T G v) with u = (Re c_0, -Im c_0, ...),
- * v = (Im c_0, Re c_0, ...).  Built on the tensor cores (tcgen05) from exact
- * BF16 digit slices of fixed-point columns, accumulated in INT64.
- * amp4d_build_gram builds it for the masses and widths in params (host; the
- * couplings are not used) and synchronises; K <= 32 columns.  Models created
+ * v = (Im c_0, Re c_0, ...).  Built in two passes: the basis of every point is
+ * evaluated once into an FP32 basis matrix (with its column maxima), then the
+ * tensor cores (tcgen05) accumulate exact BF16 digit slices of its fixed-point
+ * columns in INT64.  The basis matrix is device scratch owned by the model:
+ * 16 K bytes per normalisation point (rounded up to 512 points), allocated by
+ * the first build and kept for rebuilds at new masses until the model is
+ * destroyed.  amp4d_build_gram builds G for the masses and widths in params
+ * (host; the couplings are not used) and synchronises; K <= 32 columns.  Models created
  * with AMP4D_PATH_CACHED and no floated masses/widths build it on their first
  * evaluation (which then synchronises) and use it for I and dI/dc thereafter;
  * amp4d_set_norm_points discards it.  amp4d_get_gram copies G (host, 2K x 2K,

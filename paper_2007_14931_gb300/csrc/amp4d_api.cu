@@ -81,6 +81,8 @@ struct amp4d_model {
     // normalisation Gram matrix (cached path)
     double *d_G = nullptr;           // 2K x 2K, folded basis
     long long *d_gram_part = nullptr;
+    float *d_gram_x = nullptr;       // basis matrix of the points (Gram build scratch)
+    size_t gram_x_cap = 0;           // its size in floats
     unsigned *d_colmax = nullptr;
     float *d_gscale = nullptr;
     int *d_gram_err = nullptr;
@@ -352,6 +354,15 @@ amp4d_status build_gram(amp4d_model *model, cudaStream_t st)
         CK(cudaMalloc(&model->d_gscale, 64 * sizeof(float)));
         CK(cudaMalloc(&model->d_gram_err, sizeof(int)));
     }
+    // the basis matrix: 2 dim floats per point (kept for later builds at new masses)
+    const size_t nx = (size_t)gram_basis_points(model->mc.n) * 2 * (2 * model->n_col);
+    if (nx > model->gram_x_cap) {
+        if (model->d_gram_x) CK(cudaFree(model->d_gram_x));
+        model->d_gram_x = nullptr;
+        model->gram_x_cap = 0;
+        CK(cudaMalloc(&model->d_gram_x, nx * sizeof(float)));
+        model->gram_x_cap = nx;
+    }
     CK(cudaMemsetAsync(model->d_gram_err, 0, sizeof(int), st));
     CK(enqueue_table(model, model->d_params, st));
     GramArgs g{};
@@ -360,13 +371,14 @@ amp4d_status build_gram(amp4d_model *model, cudaStream_t st)
     g.n = model->mc.n;
     g.wrec = model->mc.wrec;
     g.md = model->d_md;
+    g.xb = model->d_gram_x;
     g.colmax = model->d_colmax;
     g.gscale = model->d_gscale;
     g.part = model->d_gram_part;
     g.err = model->d_gram_err;
     g.G = model->d_G;
     g.dim = 2 * model->n_col;
-    g.grid_colmax = model->nsm * 4;
+    g.nsm = model->nsm;
     const int64_t nchunks = (model->mc.n + gram_chunk_points() - 1) / gram_chunk_points();
     g.grid_tc = (int)std::max<int64_t>(1, std::min<int64_t>(model->gram_grid, nchunks));
     g.nk_max = model->nk_max;
@@ -830,6 +842,7 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
     if (model->d_tmp) cudaFree(model->d_tmp);
     if (model->d_G) cudaFree(model->d_G);
     if (model->d_gram_part) cudaFree(model->d_gram_part);
+    if (model->d_gram_x) cudaFree(model->d_gram_x);
     if (model->d_colmax) cudaFree(model->d_colmax);
     if (model->d_gscale) cudaFree(model->d_gscale);
     if (model->d_gram_err) cudaFree(model->d_gram_err);
@@ -1165,21 +1178,18 @@ amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, 
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, nchunks));
     int *d_X = nullptr, *d_err = nullptr;
     long long *d_part = nullptr, *d_out = nullptr;
-    ModelDev *d_md = nullptr;
     cudaError_t e = cudaMalloc(&d_X, (size_t)n * 128 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&d_part, (size_t)grid * 4096 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&d_out, 4096 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&d_md, sizeof(ModelDev));
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_md, 0, sizeof(ModelDev), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_X, X, (size_t)n * 128 * sizeof(int), cudaMemcpyDefault, st);
-    if (e == cudaSuccess) e = launch_gram_selftest(d_X, n, d_md, d_part, grid, d_err, d_out, st);
+    if (e == cudaSuccess) e = launch_gram_selftest(d_X, n, d_part, grid, d_err, d_out, st);
     int err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(G_int, d_out, 4096 * sizeof(long long), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_X); cudaFree(d_part); cudaFree(d_out); cudaFree(d_err); cudaFree(d_md);
+    cudaFree(d_X); cudaFree(d_part); cudaFree(d_out); cudaFree(d_err);
     if (e != cudaSuccess) return fail(nullptr, AMP4D_ERR_CUDA, std::string("gram self-test: ") + cudaGetErrorString(e));
     if (err) return fail(nullptr, AMP4D_ERR_TIMEOUT, "gram self-test: a bounded wait expired");
     return AMP4D_OK;

@@ -119,20 +119,23 @@ struct GramArgs {
     int64_t npad, n;
     int wrec;
     const ModelDev *md;
+    float *xb;               // basis matrix (scratch): 2 dim x gram_basis_points(n) floats
     unsigned *colmax;        // 64 (scratch)
     float *gscale;           // 64 (scratch): fixed-point scale per real column
     long long *part;         // grid_tc x 4096 INT64 partials (scratch)
     int *err;                // set to 1 if a bounded wait expired
     double *G;               // dim x dim output
     int dim;                 // 2 K
-    int grid_colmax, grid_tc;
+    int nsm, grid_tc;
     int nk_max, nz;
     cudaStream_t stream;
 };
 cudaError_t launch_gram(const GramArgs &a);
-cudaError_t launch_gram_selftest(const int *synth, int64_t n, const ModelDev *md, long long *part,
-                                 int grid, int *err, long long *out, cudaStream_t st);
+cudaError_t launch_gram_selftest(const int *synth, int64_t n, long long *part, int grid, int *err,
+                                 long long *out, cudaStream_t st);
 int gram_chunk_points();
+// Points the basis matrix holds for n points: n rounded up to whole chunks.
+int64_t gram_basis_points(int64_t n);
 
 // Generator and learned proposal (amp4d_proposal.cu).
 cudaError_t launch_gen_candidates(float *rec, int64_t npad, int64_t n, uint64_t first,
