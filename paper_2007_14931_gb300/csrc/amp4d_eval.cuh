@@ -272,13 +272,57 @@ __device__ __forceinline__ float2 z_adj_y(const ModelDev &md, const ResDev &rs, 
     return y;
 }
 
+// Shared-memory staging of the all-cached kernel's inputs (k_grad_fx, STG): each
+// thread copies the records and cache rows of its next event pair into its own
+// shared-memory slots with cp.async while it evaluates the current pair, then
+// reads them with ld.shared.  Only the copying thread reads a slot, so a
+// cp.async.wait_group of that thread is the only synchronisation.
+__device__ __forceinline__ uint32_t shared_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(shared_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(shared_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ float4 lds4(const void *p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(shared_u32(p)));
+    return v;
+}
+__device__ __forceinline__ float2 lds2(const void *p)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(shared_u32(p)));
+    return v;
+}
+// The cached values of an adjacent event pair: from global memory (evict-first)
+// or, SM, from the thread's staging slots.
+template <bool SM>
+__device__ __forceinline__ float4 ld_pair(const float2 *p)
+{
+    if constexpr (SM) return lds4(p);
+    else return __ldcs(reinterpret_cast<const float4 *>(p));
+}
+
 // Evaluation of NE events at once with the lineshapes of fixed resonances from
 // the basis cache: the per-resonance constants are read once for all NE events.
+// SM (NE = 2 only): lc points to the staging slots (row stride lcn, e[0] the
+// thread's slot) instead of the cache.
 // r[j] holds the records of event e[j]; lc is the basis cache [resonance][lcn].
 // LFM: which floated resonances have their lineshape computed per event (Eq.
 // 2-3) from the mass and momentum records instead of the cache: 0 none, 1 the
 // floated Z, 2 every floated resonance (K* and Z).
-template <int NK, int NZ, int NE, int LFM = 0, bool MT = false>
+template <int NK, int NZ, int NE, int LFM = 0, bool MT = false, bool SM = false>
 __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
                                                EvState<NK, NZ> (&ev)[NE],
                                                const float2 *__restrict__ lc, int64_t lcn,
@@ -293,14 +337,13 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
         // events e[0] and e[0] + 1 (even e[0]): one 16-byte load per resonance
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
-            const float4 t = k < nK ? __ldcs(reinterpret_cast<const float4 *>(lc + k * lcn + e[0]))
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 t = k < nK ? ld_pair<SM>(lc + k * lcn + e[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
             LK[0][k] = make_float2(t.x, t.y);
             LK[1][k] = make_float2(t.z, t.w);
         }
 #pragma unroll
         for (int z = 0; z < NZ; ++z) {
-            const float4 t = __ldcs(reinterpret_cast<const float4 *>(lc + (nK + z) * lcn + e[0]));
+            const float4 t = ld_pair<SM>(lc + (nK + z) * lcn + e[0]);
             LZ[0][z] = make_float2(t.x, t.y);
             LZ[1][z] = make_float2(t.z, t.w);
         }
@@ -408,7 +451,7 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
             if constexpr (NE == 2) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 t = __ldcs(reinterpret_cast<const float4 *>(zr + q * lcn + e[0]));
+                    const float4 t = ld_pair<SM>(zr + q * lcn + e[0]);
                     float2 *dst0 = q < 2 ? &ev[0].Om0[z][q] : &ev[0].Om1[z][q - 2];
                     float2 *dst1 = q < 2 ? &ev[1].Om0[z][q] : &ev[1].Om1[z][q - 2];
                     *dst0 = make_float2(t.x, t.y);
@@ -538,11 +581,20 @@ enum { MODE_SUM_LNS = 0, MODE_SUM_WS = 1, MODE_WRITE = 2 };
 // lineshapes are computed per event (LFM 2, LFM >= 1); the Z-chain angles only
 // when their angular factors are not read from the basis cache (ZC).
 template <bool FX, int LFM = 0, bool ZC = false>
-__device__ __forceinline__ constexpr bool record_used(int k)
+__host__ __device__ __forceinline__ constexpr bool record_used(int k)
 {
     return !FX || !(k == REC_PHI || (LFM < 2 && (k == REC_M || k == REC_P || k == REC_Q)) ||
                     (LFM < 1 && (k == REC_MZ || k == REC_PZ || k == REC_QZ)) ||
                     (ZC && k >= REC_CZ && k <= REC_SA));
+}
+
+// Number of records the all-cached kernels read (record_used<true, LFM, true>).
+template <int NREC, int LFM>
+__host__ __device__ constexpr int records_used_fx()
+{
+    int c = 0;
+    for (int k = 0; k < NREC; ++k) c += record_used<true, LFM, true>(k) ? 1 : 0;
+    return c;
 }
 
 // Z-chain angular factors of one event (Eq. 10-11) for each muon helicity xi
@@ -698,7 +750,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // gets zero weight.  LFM selects which floated lineshapes are computed per event
 // (eval_events_fx), MIX the Eq. 14 background, MT the flavour mistag.
 template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, int LFM, bool MIX = false,
-          bool MT = false>
+          bool MT = false, bool STG = false>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
                                                          unsigned long long *__restrict__ acc,
@@ -732,6 +784,27 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     // (ld.global.cs) keep them from displacing the small per-evaluation data in L2.
     const int64_t estride = (int64_t)gridDim.x * BLOCK;
     const int64_t first = NE == 2 ? 2 * (blockIdx.x * (int64_t)BLOCK + tid) : blockIdx.x * (int64_t)BLOCK + tid;
+    // STG (NE = 2): after the slot pairs, the staging slots of the records read
+    // ([NRU][BLOCK] pairs) and of the cache rows ([nrow][BLOCK] pairs of float2)
+    static_assert(!STG || NE == 2, "staging takes adjacent event pairs");
+    constexpr int NRU = records_used_fx<NREC, LFM>();
+    float2 *stg_rec = gsl + npair * BLOCK;
+    float4 *stg_lc = reinterpret_cast<float4 *>(stg_rec + NRU * BLOCK);
+    const int nrow = md.n_res + 4 * NZ;
+    auto stage = [&](int64_t es) {
+        int ru = 0;
+#pragma unroll
+        for (int k = 0; k < NREC; ++k) {
+            if (!record_used<true, LFM, true>(k)) continue;
+            cp_async_8(stg_rec + ru * BLOCK + tid, rec + k * npad + es);
+            ++ru;
+        }
+        for (int r = 0; r < nrow; ++r) cp_async_16(stg_lc + r * BLOCK + tid, lc + (int64_t)r * npad + es);
+        cp_async_commit();
+    };
+    if constexpr (STG) {
+        if (first < n) stage(first);
+    }
     for (int64_t e0 = first; e0 < n; e0 += NE * estride) {
         int64_t e[NE];
         bool valid[NE];
@@ -741,11 +814,16 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             e[1] = e0 + 1;
             valid[0] = true;
             valid[1] = e0 + 1 < n;
+            if constexpr (STG) cp_async_wait_all();   // this pair's slots have landed
+            int ru = 0;
 #pragma unroll
             for (int k = 0; k < NREC; ++k) {
-                const float2 t = record_used<true, LFM, true>(k)
-                                     ? __ldcs(reinterpret_cast<const float2 *>(rec + k * npad + e0))
-                                     : make_float2(0.f, 0.f);
+                float2 t = make_float2(0.f, 0.f);
+                if (record_used<true, LFM, true>(k)) {
+                    if constexpr (STG) t = lds2(stg_rec + ru * BLOCK + tid);
+                    else t = __ldcs(reinterpret_cast<const float2 *>(rec + k * npad + e0));
+                    ++ru;
+                }
                 v[0][k] = t.x;
                 v[1][k] = t.y;
             }
@@ -761,7 +839,17 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             }
         }
         EvState<NK, NZ> ev[NE];
-        eval_events_fx<NK, NZ, NE, LFM, MT>(md, v, ev, lc, npad, e);
+        if constexpr (STG) {
+            const int64_t es[NE] = {2 * tid, 2 * tid + 1};   // the thread's slot (in float2)
+            eval_events_fx<NK, NZ, NE, LFM, MT, true>(md, v, ev, reinterpret_cast<const float2 *>(stg_lc),
+                                                      2 * BLOCK, es);
+            // S depends on every staged value, so once both are computed every
+            // ld.shared of the slots has completed: restage them for the next pair
+            asm volatile("" ::"f"(ev[0].S), "f"(ev[1].S));
+            if (e0 + NE * estride < n) stage(e0 + NE * estride);
+        } else {
+            eval_events_fx<NK, NZ, NE, LFM, MT>(md, v, ev, lc, npad, e);
+        }
         float2 as[NE][2], asb[NE][2];
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
@@ -1102,8 +1190,21 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
         KernT kern = lfm == 0 ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0>
                    : lfm == 1 ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1>
                               : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, 1, CPS1, 2>;
+        // Staging of the next event pair in shared memory (STG) for the all-cached
+        // mode, where the slots and the staging still leave room for CPS CTAs per SM.
+        // (With the floated Z computed per event the staged form measured 3 % slower.)
+        constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
+        const size_t stg = (size_t)((a.nslot - 1) / 2) * GRAD_BLOCK * sizeof(float2) +
+                           (size_t)records_used_fx<NREC, 0>() * GRAD_BLOCK * sizeof(float2) +
+                           (size_t)a.nrow * GRAD_BLOCK * sizeof(float4);
+        const bool use_stg = lfm == 0 && !mix && !a.mt && EPT == 2 &&
+                             (size_t)CPS * (std::max(stg, smem) + 1024) <= 228 * 1024;
+        if (use_stg) {
+            smem = std::max(smem, stg);
+            kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
+        }
         if constexpr (!NORM) {
-            switch (lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
+            switch (use_stg ? -1 : lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
             case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, true>; break;
             case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false>; break;
             case 3: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, true>; break;
