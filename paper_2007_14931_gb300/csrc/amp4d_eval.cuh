@@ -790,7 +790,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     constexpr int NRU = records_used_fx<NREC, LFM>();
     float2 *stg_rec = gsl + npair * BLOCK;
     float4 *stg_lc = reinterpret_cast<float4 *>(stg_rec + NRU * BLOCK);
-    const int nrow = md.n_res + 4 * NZ;
+    // cache rows: the nK K* lineshapes, then NZ Z lineshapes and 4 NZ Z factors
+    float4 *stg_z = stg_lc + nK * BLOCK + tid;
     auto stage = [&](int64_t es) {
         int ru = 0;
 #pragma unroll
@@ -799,7 +800,13 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             cp_async_8(stg_rec + ru * BLOCK + tid, rec + k * npad + es);
             ++ru;
         }
-        for (int r = 0; r < nrow; ++r) cp_async_16(stg_lc + r * BLOCK + tid, lc + (int64_t)r * npad + es);
+        const float2 *src = lc + es;
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            if (k < nK) cp_async_16(stg_lc + k * BLOCK + tid, src + (int64_t)k * npad);
+        src += (int64_t)nK * npad;
+#pragma unroll
+        for (int r = 0; r < 5 * NZ; ++r) cp_async_16(stg_z + r * BLOCK, src + (int64_t)r * npad);
         cp_async_commit();
     };
     if constexpr (STG) {
