@@ -255,15 +255,21 @@ class Amp4dError(RuntimeError):
 
 
 _torch_cuda = None
+_raw_stream = None
 
 
 def _stream_ptr(stream):
-    """cudaStream_t of a torch stream, an int, or (None) torch's current stream."""
-    global _torch_cuda
+    """cudaStream_t of a torch stream, an int, or (None) torch's current stream.
+    The current stream's handle is read with torch's raw getter where it exists
+    (it builds no Stream object: 0.06 us against about 3-8 us per call)."""
+    global _torch_cuda, _raw_stream
     if stream is None:
         if _torch_cuda is None:
             import torch
             _torch_cuda = torch.cuda
+            _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if _raw_stream is not None:
+            return _raw_stream(_torch_cuda.current_device())
         return _torch_cuda.current_stream().cuda_stream
     return stream if isinstance(stream, int) else stream.cuda_stream
 

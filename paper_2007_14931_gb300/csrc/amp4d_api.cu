@@ -74,6 +74,20 @@ struct amp4d_model {
     unsigned long long *d_acc = nullptr;   // 128-bit sums: [data, points][nslot][hi, lo], R
     double *d_guv = nullptr;               // G u and G v of the fused Gram finish (2 x 64)
     double *d_out = nullptr, *h_out = nullptr;
+    // Replay of the synchronous evaluations (run_eval) as CUDA graphs of the
+    // parameter copy, the evaluation's launches and the result copy, captured on a
+    // private stream.  state_gen counts the calls that may change what an
+    // evaluation enqueues; a graph is captured on the second call at one
+    // generation (the first may build the table, the caches or the Gram) and
+    // replayed while the generation holds.
+    uint64_t state_gen = 0;
+    cudaStream_t cap_stream = nullptr;
+    struct EvalGraph {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t gen = ~0ull;
+        int calls = 0;
+        bool failed = false;
+    } graphs[2][2];   // [with_grad][partials]
     unsigned *d_status = nullptr;
     unsigned long long *d_bad = nullptr;
     double *d_tmp = nullptr;     // scratch for set-up reductions
@@ -513,6 +527,52 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
 }
 
 // Synchronous evaluation from host parameters; leaves the output block in h_out.
+// The copy-in, the evaluation and the copy-out of run_eval on stream st.
+amp4d_status enqueue_sync_eval(amp4d_model *model, bool with_grad, bool partials, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    amp4d_status rc = enqueue(model, with_grad, model->d_params, model->d_out, st, partials);
+    if (rc) return rc;
+    const size_t nout = 6 + (with_grad ? (partials ? 2 : 1) * model->n_param : 0);
+    CK(cudaMemcpyAsync(model->h_out, model->d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return AMP4D_OK;
+}
+
+void drop_graph(amp4d_model::EvalGraph &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = amp4d_model::EvalGraph{};
+}
+
+// Capture enqueue_sync_eval into g.exec; false if the sequence cannot be
+// captured (the call then runs it directly).
+bool capture_eval_graph(amp4d_model *model, bool with_grad, bool partials, amp4d_model::EvalGraph &g)
+{
+    if (!model->cap_stream &&
+        cudaStreamCreateWithFlags(&model->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        model->cap_stream = nullptr;
+        return false;
+    }
+    cudaStream_t cs = model->cap_stream;
+    const std::string saved_err = model->err;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const amp4d_status rc = enqueue_sync_eval(model, with_grad, partials, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    bool ok = rc == AMP4D_OK && e == cudaSuccess && graph != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        g.exec = nullptr;
+        cudaGetLastError();   // a failed capture leaves no sticky error; clear the last one
+        model->err = saved_err;
+    }
+    return ok;
+}
+
+// Synchronous evaluation from host parameters; leaves the output block in h_out.
+// Repeated calls at one state generation replay a CUDA graph of the sequence.
 amp4d_status run_eval(amp4d_model *model, const double *params, bool with_grad, cudaStream_t st,
                       bool partials = false)
 {
@@ -520,12 +580,20 @@ amp4d_status run_eval(amp4d_model *model, const double *params, bool with_grad, 
     if (rc) return rc;
     CK(cudaSetDevice(model->device));
     std::memcpy(model->h_params, params, model->n_param * sizeof(double));
-    CK(cudaMemcpyAsync(model->d_params, model->h_params, model->n_param * sizeof(double),
-                       cudaMemcpyHostToDevice, st));
-    rc = enqueue(model, with_grad, model->d_params, model->d_out, st, partials);
-    if (rc) return rc;
-    const size_t nout = 6 + (with_grad ? (partials ? 2 : 1) * model->n_param : 0);
-    CK(cudaMemcpyAsync(model->h_out, model->d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+    amp4d_model::EvalGraph &g = model->graphs[with_grad ? 1 : 0][partials ? 1 : 0];
+    if (g.gen != model->state_gen) {
+        drop_graph(g);
+        g.gen = model->state_gen;
+    }
+    ++g.calls;
+    if (!g.exec && !g.failed && !model->prof_on && g.calls >= 2)
+        g.failed = !capture_eval_graph(model, with_grad, partials, g);
+    if (g.exec && !model->prof_on) {
+        CK(cudaGraphLaunch(g.exec, st));
+    } else {
+        rc = enqueue_sync_eval(model, with_grad, partials, st);
+        if (rc) return rc;
+    }
     CK(cudaStreamSynchronize(st));
     if (((unsigned)model->h_out[5]) & 2u) return fail(model, AMP4D_ERR_ARG, "invalid parameters");
     return AMP4D_OK;
@@ -842,6 +910,9 @@ amp4d_status amp4d_model_destroy(amp4d_model *model)
     if (model->d_bad) cudaFree(model->d_bad);
     if (model->d_tmp) cudaFree(model->d_tmp);
     if (model->d_G) cudaFree(model->d_G);
+    for (auto &row : model->graphs)
+        for (auto &g : row) drop_graph(g);
+    if (model->cap_stream) cudaStreamDestroy(model->cap_stream);
     if (model->d_gram_part) cudaFree(model->d_gram_part);
     if (model->d_gram_x) cudaFree(model->d_gram_x);
     if (model->d_colmax) cudaFree(model->d_colmax);
@@ -865,6 +936,7 @@ int amp4d_num_params(const amp4d_model *model) { return model ? model->n_param :
 amp4d_status amp4d_set_events(amp4d_model *model, const float *m, const float *cK,
                               const float *cpsi, const float *phi, int64_t n, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model) return AMP4D_ERR_ARG;
     amp4d_status rc = load_set(model, model->ev, m, cK, cpsi, phi, nullptr, n, false, (cudaStream_t)stream);
     if (rc == AMP4D_OK) rc = apply_templates(model, model->ev, false, (cudaStream_t)stream);
@@ -874,6 +946,7 @@ amp4d_status amp4d_set_events(amp4d_model *model, const float *m, const float *c
 amp4d_status amp4d_set_efficiency(amp4d_model *model, const amp4d_hist2d *mass,
                                   const amp4d_hist2d *angle, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || (!mass) != (!angle)) return model ? fail(model, AMP4D_ERR_ARG, "give both templates or neither") : AMP4D_ERR_ARG;
     CK(cudaSetDevice(model->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -895,6 +968,7 @@ amp4d_status amp4d_set_efficiency(amp4d_model *model, const amp4d_hist2d *mass,
 
 amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mistag, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model) return AMP4D_ERR_ARG;
     if (!(mistag >= 0.0 && mistag <= 0.5)) return fail(model, AMP4D_ERR_ARG, "mistag must lie in [0, 0.5]");
     EventSet &s = model->ev;
@@ -943,6 +1017,7 @@ amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mist
 amp4d_status amp4d_set_background(amp4d_model *model, const amp4d_hist2d *mass,
                                   const amp4d_hist2d *angle, double purity, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || (!mass) != (!angle)) return model ? fail(model, AMP4D_ERR_ARG, "give both templates or neither") : AMP4D_ERR_ARG;
     if (mass && !(purity >= 0.0 && purity <= 1.0)) return fail(model, AMP4D_ERR_ARG, "purity must lie in [0, 1]");
     CK(cudaSetDevice(model->device));
@@ -960,6 +1035,7 @@ amp4d_status amp4d_set_norm_points(amp4d_model *model, const float *m, const flo
                                    const float *cpsi, const float *phi, const float *w,
                                    int64_t n, double volume, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model) return AMP4D_ERR_ARG;
     if (!(volume > 0.0)) return fail(model, AMP4D_ERR_ARG, "volume must be > 0");
     model->gram_valid = false;
@@ -1013,6 +1089,7 @@ amp4d_status amp4d_eval_terms(amp4d_model *model, const double *params, double *
 amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int which,
                                 float *S_out, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !params || !S_out || (which != 0 && which != 1)) return AMP4D_ERR_ARG;
     EventSet &s = which == 0 ? model->ev : model->mc;
     if (s.n == 0) return fail(model, AMP4D_ERR_STATE, "no events loaded");
@@ -1032,6 +1109,7 @@ amp4d_status amp4d_eval_density(amp4d_model *model, const double *params, int wh
 
 amp4d_status amp4d_eval_pdf(amp4d_model *model, const double *params, float *pdf_out, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !params || !pdf_out) return AMP4D_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     amp4d_status rc = run_eval(model, params, false, st);   // I over the current points
@@ -1053,6 +1131,7 @@ amp4d_status amp4d_eval_pdf(amp4d_model *model, const double *params, float *pdf
 amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *params, double *out,
                                 void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !params || !out || (what != AMP4D_EVAL_NLL && what != AMP4D_EVAL_NLL_GRAD))
         return model ? fail(model, AMP4D_ERR_ARG, "bad enqueue arguments") : AMP4D_ERR_ARG;
     CK(cudaSetDevice(model->device));
@@ -1062,6 +1141,7 @@ amp4d_status amp4d_enqueue_eval(amp4d_model *model, int what, const double *para
 amp4d_status amp4d_enqueue_partials(amp4d_model *model, int what, const double *params,
                                     double *out, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !params || !out || (what != AMP4D_EVAL_NLL && what != AMP4D_EVAL_NLL_GRAD))
         return model ? fail(model, AMP4D_ERR_ARG, "bad enqueue arguments") : AMP4D_ERR_ARG;
     CK(cudaSetDevice(model->device));
@@ -1082,6 +1162,7 @@ amp4d_status amp4d_eval_partials(amp4d_model *model, int what, const double *par
 
 amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model) return AMP4D_ERR_ARG;
     amp4d_status rc = check_params(model, params);
     if (rc) return rc;
@@ -1095,6 +1176,7 @@ amp4d_status amp4d_build_gram(amp4d_model *model, const double *params, void *st
 
 amp4d_status amp4d_fit_fractions(amp4d_model *model, const double *params, double *ff, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !params || !ff) return AMP4D_ERR_ARG;
     if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "set_norm_points must come first");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1199,6 +1281,7 @@ amp4d_status amp4d_gram_selftest(const int32_t *X, int64_t n, long long *G_int, 
 amp4d_status amp4d_generate(amp4d_model *model, const double *params, uint64_t seed, int64_t n,
                             float *m, float *cK, float *cpsi, float *phi, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !m || !cK || !cpsi || !phi || n < 1) return AMP4D_ERR_ARG;
     amp4d_status rc = check_params(model, params);
     if (rc) return rc;
@@ -1340,6 +1423,7 @@ amp4d_status amp4d_proposal_train(amp4d_model *model, const float *m, const floa
                                   const float *cpsi, const float *phi, int64_t n,
                                   const amp4d_mlp_cfg *cfg, uint64_t seed, double *loss, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !m || !cK || !cpsi || !phi || !cfg || n < 1 || cfg->batch < 1 || cfg->steps < 1)
         return AMP4D_ERR_ARG;
     for (int d = 0; d < 4; ++d)
@@ -1407,6 +1491,7 @@ amp4d_status amp4d_proposal_train_gram(amp4d_model *model, const double *params,
                                        const amp4d_mlp_cfg *cfg, uint64_t seed, uint64_t gen_seed,
                                        double *loss, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !params || !cfg || n < 1) return AMP4D_ERR_ARG;
     if (model->mc.n == 0) return fail(model, AMP4D_ERR_STATE, "set_norm_points must come first");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1458,6 +1543,7 @@ amp4d_status amp4d_proposal_train_gram(amp4d_model *model, const double *params,
 amp4d_status amp4d_proposal_sample(amp4d_model *model, int64_t n, uint64_t seed, float *m, float *cK,
                                    float *cpsi, float *phi, float *w, void *stream)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model || !m || !cK || !cpsi || !phi || !w || n < 1) return AMP4D_ERR_ARG;
     if (!model->proposal_ready) return fail(model, AMP4D_ERR_STATE, "proposal not trained");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1545,6 +1631,7 @@ amp4d_status amp4d_grid_sample(const float *gcell, const int *nb, double alpha, 
 
 amp4d_status amp4d_profile_enable(amp4d_model *model, int on)
 {
+    if (model) ++model->state_gen;   // may change what an evaluation enqueues
     if (!model) return AMP4D_ERR_ARG;
     model->prof_on = on != 0;
     return AMP4D_OK;

@@ -42,7 +42,9 @@ static ConstTableSync &const_table_sync()
 // Copies the device table gmd (written by k_build_table on the same stream)
 // into c_md and enqueues launch().  There is one c_md per device, so launches
 // from different streams are serialised: each waits for the previous user's
-// kernels before overwriting the table.
+// kernels before overwriting the table.  Under stream capture (a CUDA graph of
+// an evaluation) the wait and the record become external event nodes, so every
+// replay of the graph takes part in the same serialisation.
 template <typename Launch>
 static cudaError_t with_const_table(const ModelDev *gmd, cudaStream_t st, Launch &&launch)
 {
@@ -50,16 +52,21 @@ static cudaError_t with_const_table(const ModelDev *gmd, cudaStream_t st, Launch
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
+    const bool capturing = cap == cudaStreamCaptureStatusActive;
     ConstTableSync &sy = const_table_sync();
     std::lock_guard<std::mutex> lock(sy.mu);
     if (!sy.done[dev]) e = cudaEventCreateWithFlags(&sy.done[dev], cudaEventDisableTiming);
-    else e = cudaStreamWaitEvent(st, sy.done[dev], 0);
+    else e = cudaStreamWaitEvent(st, sy.done[dev], capturing ? cudaEventWaitExternal : 0);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyToSymbolAsync(c_md, gmd, sizeof(ModelDev), 0, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
     e = launch();
     if (e != cudaSuccess) return e;
-    return cudaEventRecord(sy.done[dev], st);
+    return capturing ? cudaEventRecordWithFlags(sy.done[dev], st, cudaEventRecordExternal)
+                     : cudaEventRecord(sy.done[dev], st);
 }
 
 
@@ -1198,8 +1205,9 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                    : lfm == 1 ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1>
                               : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, 1, CPS1, 2>;
         // Staging of the next event pair in shared memory (STG) for the all-cached
-        // mode, where the slots and the staging still leave room for CPS CTAs per SM.
-        // (With the floated Z computed per event the staged form measured 3 % slower.)
+        // mode, where the slots and the staging still leave room for CPS CTAs per SM
+        // (with the floated Z computed per event, 168 registers, it measured 4 %
+        // slower).
         constexpr int NREC = NZ > 0 ? REC_NZ : REC_NK;
         const size_t stg = (size_t)((a.nslot - 1) / 2) * GRAD_BLOCK * sizeof(float2) +
                            (size_t)records_used_fx<NREC, 0>() * GRAD_BLOCK * sizeof(float2) +
