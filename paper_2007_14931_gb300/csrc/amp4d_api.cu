@@ -294,6 +294,7 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.stream = st;
     a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
     a.nrow = (int)mo->res.size() + 4 * mo->nZ;
+    a.nk = (int)mo->res.size() - mo->nZ;
     a.nslot = mo->nslot;
     a.all_fixed = mo->n_float == 0;
     a.kstar_fixed = mo->kstar_fixed;

@@ -329,13 +329,13 @@ __device__ __forceinline__ float4 ld_pair(const float2 *p)
 // LFM: which floated resonances have their lineshape computed per event (Eq.
 // 2-3) from the mass and momentum records instead of the cache: 0 none, 1 the
 // floated Z, 2 every floated resonance (K* and Z).
-template <int NK, int NZ, int NE, int LFM = 0, bool MT = false, bool SM = false>
+template <int NK, int NZ, int NE, int LFM = 0, bool MT = false, bool SM = false, bool FULL = false>
 __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
                                                EvState<NK, NZ> (&ev)[NE],
                                                const float2 *__restrict__ lc, int64_t lcn,
                                                const int64_t (&e)[NE])
 {
-    const int nK = md.n_res - NZ;
+    const int nK = FULL ? NK : md.n_res - NZ;   // FULL: the model fills the K* bucket
     float2 cc[NE];
     float sK[NE];
     float2 u[NE][3];
@@ -757,7 +757,7 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // gets zero weight.  LFM selects which floated lineshapes are computed per event
 // (eval_events_fx), MIX the Eq. 14 background, MT the flavour mistag.
 template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, int LFM, bool MIX = false,
-          bool MT = false, bool STG = false>
+          bool MT = false, bool STG = false, bool FULL = false>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
                                                          unsigned long long *__restrict__ acc,
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
     Kahan acc0, rsum;
     int esum = 0;
     bool bad = false;
-    const int nK = md.n_res - NZ;
+    const int nK = FULL ? NK : md.n_res - NZ;   // FULL: the model fills the K* bucket
     // NE = 2: thread t takes the adjacent events 2t and 2t + 1 of its stride
     // (8-byte record loads; e0 is even and npad a multiple of 4, so e0 + 1 < npad
     // holds a real or a padding event); otherwise events e0 + j * stride.  The
@@ -855,8 +855,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
         EvState<NK, NZ> ev[NE];
         if constexpr (STG) {
             const int64_t es[NE] = {2 * tid, 2 * tid + 1};   // the thread's slot (in float2)
-            eval_events_fx<NK, NZ, NE, LFM, MT, true>(md, v, ev, reinterpret_cast<const float2 *>(stg_lc),
-                                                      2 * BLOCK, es);
+            eval_events_fx<NK, NZ, NE, LFM, MT, true, FULL>(md, v, ev, reinterpret_cast<const float2 *>(stg_lc),
+                                                            2 * BLOCK, es);
             // S depends on every staged value, so once both are computed every
             // ld.shared of the slots has completed: restage them for the next pair
             asm volatile("" ::"f"(ev[0].S), "f"(ev[1].S));
@@ -1216,7 +1216,9 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                              (size_t)CPS * (std::max(stg, smem) + 1024) <= 228 * 1024;
         if (use_stg) {
             smem = std::max(smem, stg);
-            kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
+            // the model fills its K* bucket: no run-time test of the K* count
+            kern = a.nk == NK ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true>
+                              : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
         }
         if constexpr (!NORM) {
             switch (use_stg ? -1 : lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
