@@ -1214,11 +1214,14 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                            (size_t)a.nrow * GRAD_BLOCK * sizeof(float4);
         const bool use_stg = lfm == 0 && !mix && !a.mt && EPT == 2 &&
                              (size_t)CPS * (std::max(stg, smem) + 1024) <= 228 * 1024;
+        // FULL: the model fills its K* bucket, so no run-time test of the K* count
+        const bool full = a.nk == NK;
         if (use_stg) {
             smem = std::max(smem, stg);
-            // the model fills its K* bucket: no run-time test of the K* count
-            kern = a.nk == NK ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true>
-                              : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
+            kern = full ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true>
+                        : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
+        } else if (lfm == 1 && full && !mix && !a.mt) {
+            kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true>;
         }
         if constexpr (!NORM) {
             switch (use_stg ? -1 : lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
