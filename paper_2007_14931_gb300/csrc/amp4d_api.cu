@@ -295,6 +295,9 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.lcache = (mo->path == AMP4D_PATH_CACHED && s.lcache_valid) ? s.lcache : nullptr;
     a.nrow = (int)mo->res.size() + 4 * mo->nZ;
     a.nk = (int)mo->res.size() - mo->nZ;
+    a.nj0 = 0;
+    for (int u : mo->internal)
+        if (mo->res[u].chain == AMP4D_CHAIN_KSTAR && mo->res[u].J == 0) ++a.nj0;
     a.nslot = mo->nslot;
     a.all_fixed = mo->n_float == 0;
     a.kstar_fixed = mo->kstar_fixed;
@@ -837,8 +840,14 @@ amp4d_status amp4d_model_create(const amp4d_particle_masses *masses, const amp4d
             if (r.J >= 1) { model->col_res.push_back(i); model->col_lam.push_back(1); }
         }
         model->n_col = (int)model->col_res.size();
-        if (r.chain == AMP4D_CHAIN_KSTAR) model->internal.push_back(i);
     }
+    // Internal order: the K* of spin > 0, then the scalar K* (J = 0), then the Z,
+    // each in the caller's order.  With the scalars last, a kernel specialised
+    // for the number of scalars knows each K*'s class at compile time.
+    for (int i = 0; i < n_res; ++i)
+        if (res[i].chain == AMP4D_CHAIN_KSTAR && res[i].J != 0) model->internal.push_back(i);
+    for (int i = 0; i < n_res; ++i)
+        if (res[i].chain == AMP4D_CHAIN_KSTAR && res[i].J == 0) model->internal.push_back(i);
     for (int i = 0; i < n_res; ++i)
         if (res[i].chain == AMP4D_CHAIN_Z) model->internal.push_back(i);
     model->nZ = nz;

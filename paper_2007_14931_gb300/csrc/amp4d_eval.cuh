@@ -329,7 +329,8 @@ __device__ __forceinline__ float4 ld_pair(const float2 *p)
 // LFM: which floated resonances have their lineshape computed per event (Eq.
 // 2-3) from the mass and momentum records instead of the cache: 0 none, 1 the
 // floated Z, 2 every floated resonance (K* and Z).
-template <int NK, int NZ, int NE, int LFM = 0, bool MT = false, bool SM = false, bool FULL = false>
+template <int NK, int NZ, int NE, int LFM = 0, bool MT = false, bool SM = false, bool FULL = false,
+          int NJ0 = -1>
 __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (&r)[NE][NZ > 0 ? REC_NZ : REC_NK],
                                                EvState<NK, NZ> (&ev)[NE],
                                                const float2 *__restrict__ lc, int64_t lcn,
@@ -398,7 +399,7 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
                 if constexpr (LFM == 2) {
                     if (rs.fpos >= 0) LK[j][k] = lineshape(rs, ev[j].m, ev[j].invm, ev[j].p, ev[j].q).A;
                 }
-                if (NE == 2 && rs.J == 0) {
+                if (NE == 2 && (NJ0 >= 0 ? k >= NK - NJ0 : rs.J == 0)) {
                     // d^0_00 = 1, no l = +-1 terms: the same bits as the general form
                     // (with one event per thread the branch costs more than it saves)
                     const float2 b0 = LK[j][k];
@@ -756,8 +757,10 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // events.  An event index at or beyond n holds a padding or repeated event that
 // gets zero weight.  LFM selects which floated lineshapes are computed per event
 // (eval_events_fx), MIX the Eq. 14 background, MT the flavour mistag.
+// FULL: the model's K* count equals the bucket NK.  NJ0 >= 0 (with FULL): the last
+// NJ0 K* of the internal order are the scalars (J = 0), the others have J > 0.
 template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, int LFM, bool MIX = false,
-          bool MT = false, bool STG = false, bool FULL = false>
+          bool MT = false, bool STG = false, bool FULL = false, int NJ0 = -1>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
                                                          int64_t n, int wrec,
                                                          unsigned long long *__restrict__ acc,
@@ -855,8 +858,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
         EvState<NK, NZ> ev[NE];
         if constexpr (STG) {
             const int64_t es[NE] = {2 * tid, 2 * tid + 1};   // the thread's slot (in float2)
-            eval_events_fx<NK, NZ, NE, LFM, MT, true, FULL>(md, v, ev, reinterpret_cast<const float2 *>(stg_lc),
-                                                            2 * BLOCK, es);
+            eval_events_fx<NK, NZ, NE, LFM, MT, true, FULL, NJ0>(
+                md, v, ev, reinterpret_cast<const float2 *>(stg_lc), 2 * BLOCK, es);
             // S depends on every staged value, so once both are computed every
             // ld.shared of the slots has completed: restage them for the next pair
             asm volatile("" ::"f"(ev[0].S), "f"(ev[1].S));
@@ -900,7 +903,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             if (k >= nK) continue;
-            const bool j0 = NE == 2 && md.res[k].J == 0;   // only the l = 0 slot moves (B1 = 0)
+            // a scalar: only the l = 0 slot moves (B1 = 0)
+            const bool j0 = NE == 2 && (NJ0 >= 0 ? k >= NK - NJ0 : md.res[k].J == 0);
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
                 if (j0 && l != 1) continue;
@@ -1220,6 +1224,16 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
             smem = std::max(smem, stg);
             kern = full ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true>
                         : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
+            if constexpr (!NORM) {
+                // the data kernel also with the scalars' positions fixed (up to three)
+                if (full) switch (a.nj0) {
+                    case 0: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 0>; break;
+                    case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 1>; break;
+                    case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 2>; break;
+                    case 3: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 3>; break;
+                    default: break;
+                    }
+            }
         } else if (lfm == 1 && full && !mix && !a.mt) {
             kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true>;
         }
