@@ -296,8 +296,13 @@ LaunchArgs args_for(amp4d_model *mo, EventSet &s, double *part, float *out, cuda
     a.nrow = (int)mo->res.size() + 4 * mo->nZ;
     a.nk = (int)mo->res.size() - mo->nZ;
     a.nj0 = 0;
-    for (int u : mo->internal)
-        if (mo->res[u].chain == AMP4D_CHAIN_KSTAR && mo->res[u].J == 0) ++a.nj0;
+    a.zboth = true;
+    for (int u : mo->internal) {
+        const amp4d_resonance &r = mo->res[u];
+        if (r.chain == AMP4D_CHAIN_KSTAR && r.J == 0) ++a.nj0;
+        // a Z has the l' = 0 column when its parity factor is +1, l' = +-1 when J >= 1
+        if (r.chain == AMP4D_CHAIN_Z && (-r.P * ((r.J % 2) ? -1 : 1) != 1 || r.J < 1)) a.zboth = false;
+    }
     a.nslot = mo->nslot;
     a.all_fixed = mo->n_float == 0;
     a.kstar_fixed = mo->kstar_fixed;

@@ -485,14 +485,15 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
                 for (int x = 0; x < 2; ++x) {
                     const float2 o0 = ev[j].Om0[z][x], o1 = ev[j].Om1[z][x];
                     float2 s = make_float2(0.f, 0.f);
-                    if (rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
-                    if (rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
+                    // NJ0 >= 0: every Z has both columns (the host checks)
+                    if (NJ0 >= 0 || rs.zcol0 >= 0) cfma2p(s, md.zp[z][0], o0, make_float2(o0.y, o0.x));
+                    if (NJ0 >= 0 || rs.zcol1 >= 0) cfma2p(s, md.zp[z][1], o1, make_float2(o1.y, o1.x));
                     cfma(ev[j].a[x], LA, s);
                     if constexpr (MT) {
                         const float2 c0 = make_float2(o0.x, -o0.y), c1 = make_float2(o1.x, -o1.y);
                         float2 sb = make_float2(0.f, 0.f);
-                        if (rs.zcol0 >= 0) cfma2p(sb, md.zp[z][0], c0, make_float2(c0.y, c0.x));
-                        if (rs.zcol1 >= 0) cfma2p(sb, md.zp[z][1], c1, make_float2(c1.y, c1.x));
+                        if (NJ0 >= 0 || rs.zcol0 >= 0) cfma2p(sb, md.zp[z][0], c0, make_float2(c0.y, c0.x));
+                        if (NJ0 >= 0 || rs.zcol1 >= 0) cfma2p(sb, md.zp[z][1], c1, make_float2(c1.y, c1.x));
                         cfma(ev[j].ab[x], LA, sb);
                     }
                 }
@@ -758,7 +759,8 @@ __device__ __forceinline__ void grad_block_tail(const Kahan &acc0, int esum, boo
 // gets zero weight.  LFM selects which floated lineshapes are computed per event
 // (eval_events_fx), MIX the Eq. 14 background, MT the flavour mistag.
 // FULL: the model's K* count equals the bucket NK.  NJ0 >= 0 (with FULL): the last
-// NJ0 K* of the internal order are the scalars (J = 0), the others have J > 0.
+// NJ0 K* of the internal order are the scalars (J = 0), the others have J > 0, and
+// every Z has both columns (l' = 0 and l' = +-1).
 template <int NK, int NZ, bool NORM, int BLOCK, int NE, int CTAS, int LFM, bool MIX = false,
           bool MT = false, bool STG = false, bool FULL = false, int NJ0 = -1>
 __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict__ rec, int64_t npad,
@@ -1226,7 +1228,8 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                         : k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true>;
             if constexpr (!NORM) {
                 // the data kernel also with the scalars' positions fixed (up to three)
-                if (full) switch (a.nj0) {
+                // when every Z has both columns
+                if (full && a.zboth) switch (a.nj0) {
                     case 0: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 0>; break;
                     case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 1>; break;
                     case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true, 2>; break;

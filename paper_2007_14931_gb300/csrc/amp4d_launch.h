@@ -48,6 +48,7 @@ struct LaunchArgs {
     int nrow = 0;                    // rows of the basis cache: lineshapes, then 4 per Z
     int nk = -1;                     // K* resonances of the model (at most the bucket nk_max)
     int nj0 = 0;                     // of which scalar (J = 0): the last nj0 in internal order
+    bool zboth = false;              // every Z has both columns (l' = 0 and l' = +-1)
     int nslot = 0;                   // gradient slots (grad_num_slots)
     bool all_fixed = false;          // no mass or width floats (with lcache: all lineshapes cached)
     bool kstar_fixed = false;        // no K* mass or width floats
