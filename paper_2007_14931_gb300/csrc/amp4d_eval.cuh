@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
             asm volatile("" ::"f"(ev[0].S), "f"(ev[1].S));
             if (e0 + NE * estride < n) stage(e0 + NE * estride);
         } else {
-            eval_events_fx<NK, NZ, NE, LFM, MT>(md, v, ev, lc, npad, e);
+            eval_events_fx<NK, NZ, NE, LFM, MT, false, FULL, NJ0>(md, v, ev, lc, npad, e);
         }
         float2 as[NE][2], asb[NE][2];
 #pragma unroll
@@ -1239,6 +1239,14 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
             }
         } else if (lfm == 1 && full && !mix && !a.mt) {
             kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true>;
+            // and with the scalars' positions and the Z columns fixed
+            if (a.zboth) switch (a.nj0) {
+                case 0: kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true, 0>; break;
+                case 1: kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true, 1>; break;
+                case 2: kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true, 2>; break;
+                case 3: kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true, 3>; break;
+                default: break;
+                }
         }
         if constexpr (!NORM) {
             switch (use_stg ? -1 : lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
