@@ -1222,6 +1222,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                              (size_t)CPS * (std::max(stg, smem) + 1024) <= 228 * 1024;
         // FULL: the model fills its K* bucket, so no run-time test of the K* count
         const bool full = a.nk == NK;
+        bool structured = false;   // a structure variant of an unstaged data kernel
         if (use_stg) {
             smem = std::max(smem, stg);
             kern = full ? k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 0, false, false, true, true>
@@ -1237,6 +1238,24 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                     default: break;
                     }
             }
+        } else if (!NORM && lfm == 0 && full && a.zboth && a.nj0 <= 3 && !a.mt) {
+            // unstaged data kernel (the slots and staging of two Z exceed 3 CTAs/SM, or the
+            // Eq. 14 background) with the model's structure fixed
+            if constexpr (!NORM) {
+            if (mix) switch (a.nj0) {
+                case 0: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false, false, true, 0>; break;
+                case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false, false, true, 1>; break;
+                case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false, false, true, 2>; break;
+                default: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false, false, true, 3>; break;
+                }
+            else switch (a.nj0) {
+                case 0: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, false, true, 0>; break;
+                case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, false, true, 1>; break;
+                case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, false, true, 2>; break;
+                default: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, false, false, true, 3>; break;
+                }
+            structured = true;
+            }
         } else if (lfm == 1 && full && !mix && !a.mt) {
             kern = k_grad_fx<NK, NZ, NORM, GRAD_BLOCK, EPT, CPS, 1, false, false, false, true>;
             // and with the scalars' positions and the Z columns fixed
@@ -1249,7 +1268,7 @@ cudaError_t launch_grad_k(const LaunchArgs &a)
                 }
         }
         if constexpr (!NORM) {
-            switch (use_stg ? -1 : lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
+            switch (use_stg || structured ? -1 : lfm * 4 + (mix ? 2 : 0) + (a.mt ? 1 : 0)) {
             case 1: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, false, true>; break;
             case 2: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, false>; break;
             case 3: kern = k_grad_fx<NK, NZ, false, GRAD_BLOCK, EPT, CPS, 0, true, true>; break;
