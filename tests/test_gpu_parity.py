@@ -392,3 +392,65 @@ def test_lass_density_near_threshold_and_pole(A, R):
         nll, g = g2.eval_nll_grad(p)
         assert abs(nll - nll_o) < 1e-4 + 1e-9 * abs(nll_o)
         assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
+
+
+def _structure_case(case):
+    """Resonance lists that select each compiled variant of the all-cached data
+    kernel: the K* count filling its bucket with 0-3 scalars (their positions
+    compile-time), with four scalars (run-time spin tests), and with a Z that has
+    a single column (run-time column tests)."""
+    T = {r.name: r for r in W.KSTAR_TABLE}
+    extra_vec = W.Resonance("K*(1550)", W.CHAIN_KSTAR, 1, -1, 1.55, 0.25)
+    extra_scalar = W.Resonance("K0*(1200)", W.CHAIN_KSTAR, 0, +1, 1.20, 0.30)
+    if case == "bucket2_one_scalar":
+        return [T["K*(892)"], T["K0*(1430)"]]
+    if case == "bucket10_two_scalars_z":
+        return [extra_vec if r.name == "K0*(800)" else r for r in W.KSTAR_TABLE] + [W.Z4430]
+    if case == "bucket10_one_scalar_z":
+        return [extra_vec if r.name in ("K0*(800)", "K0*(1950)") else r
+                for r in W.KSTAR_TABLE[:9]] + [T["K2*(1980)"], W.Z4430]
+    if case == "bucket10_four_scalars_z":
+        return [extra_scalar if r.name == "K*(1410)" else r for r in W.KSTAR_TABLE] + [W.Z4430]
+    if case == "z_one_column":   # J^P = 1^-: no l' = 0 column
+        return list(W.KSTAR_TABLE) + [W.Resonance("Z(1-)", W.CHAIN_Z, 1, -1, 4.43, 0.18)]
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["bucket2_one_scalar", "bucket10_two_scalars_z", "bucket10_one_scalar_z",
+                                  "bucket10_four_scalars_z", "z_one_column"])
+def test_structure_variants_match_oracle(A, case):
+    """Cached path (the benchmarked data kernel and its variants) against the
+    oracle: NLL within 1e-3, every gradient component within 1e-6 of the
+    gradient scale; also with the Eq. 14 efficiency and background (the unstaged
+    variants), within 1e-6 of |g|_inf as in the Eq. 14 parity tests."""
+    res = _structure_case(case)
+    nsc = sum(1 for r in res if r.chain == W.CHAIN_KSTAR and r.J == 0)
+    c = W.draw_couplings(res, 23)
+    p = W.couplings_to_params(c)
+    om = O.Model(res)
+    ev = W.peaked_points(8_000, 24, res)
+    nm = W.uniform_points(40_000, 25)
+    gm = A.Model(res, path=A.AMP4D_PATH_CACHED)
+    gm.set_events(*_dev(ev))
+    gm.set_norm_points(*_dev(nm))
+    nll_o, g_o, _, rc = om.nll(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    scale = max(np.max(np.abs(g_o)), _gradient_scale(om, p, ev))
+    print("%s (%d scalars): dNLL %.2e, max |dg| / scale %.3e" % (
+        case, nsc, nll - nll_o, np.max(np.abs(g - g_o)) / scale))
+    assert abs(nll - nll_o) < 1e-3
+    assert np.all(np.abs(g - g_o) <= np.maximum(1e-6 * np.abs(g_o), GRAD_TOL * scale))
+    # the same model with the Eq. 14 efficiency and background
+    em, ea, bm, ba, _ = W.eq14_templates(26)
+    gm.set_efficiency(em, ea)
+    gm.set_background(bm, ba, W.PURITY)
+    om.set_template(0, em, ea)
+    om.set_template(1, bm, ba, purity=W.PURITY)
+    nll_o, g_o, _, rc = om.nll_eq14(p, ev, nm, grad=True)
+    nll, g = gm.eval_nll_grad(p)
+    print("%s with Eq. 14: dNLL %.2e, max |dg| / |g|inf %.3e" % (
+        case, nll - nll_o, np.max(np.abs(g - g_o)) / np.max(np.abs(g_o))))
+    assert rc == 0
+    assert abs(nll - nll_o) < 1e-3
+    assert np.max(np.abs(g - g_o)) <= GRAD_TOL * np.max(np.abs(g_o))
+    gm.close()
