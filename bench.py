@@ -889,9 +889,10 @@ def main():
         "events_per_s": value * cfg.n_events,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * P,
                 "d2h_bytes_per_step": 8 * (6 + P)},
-        # per step: table update, data adjoint, finish (Gram path); with floated
-        # masses also the point adjoint (per-point normalisation)
-        "gpu_launches": int(K * (3 if not cfg.float_mg else 4)),
+        # per step on the Gram path: the table update and the data adjoint, whose
+        # last CTA finishes the evaluation; with floated masses the table build, the
+        # data adjoint, the point adjoint and the finish
+        "gpu_launches": int(K * (2 if not cfg.float_mg else 4)),
         "phases_ms_per_step": {n: float(prof_ms[i] / max(1, prof_n[i])) for i, n in enumerate(names)},
         "roofline": roof,
         "clocks": clk,
