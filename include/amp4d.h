@@ -223,9 +223,10 @@ amp4d_status amp4d_set_flavour(amp4d_model *model, const float *tag, double mist
  * The synchronous evaluations (amp4d_eval_nll, amp4d_eval_nll_grad,
  * amp4d_eval_terms, amp4d_eval_partials) copy params in, enqueue the evaluation
  * on `stream`, copy the result out and synchronise the stream.  From the second
- * call of one kind at an unchanged model state the sequence runs as a CUDA graph
- * (captured once on a private stream of the model, then launched on `stream`),
- * with the same results bit for bit.  Every other call that takes the model may
+ * call of one kind at an unchanged model state the evaluation runs as a CUDA graph
+ * (captured once on a private stream of the model, then launched on `stream`)
+ * whose kernels read the parameters from and write the result to the model's
+ * pinned host buffers directly, with the same results bit for bit.  Every other call that takes the model may
  * change what an evaluation enqueues and makes the next call capture afresh.
  * The first call may build the constant table, the basis caches or the Gram
  * matrix, and so takes longer.

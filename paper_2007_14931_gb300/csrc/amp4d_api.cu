@@ -554,8 +554,9 @@ void drop_graph(amp4d_model::EvalGraph &g)
     g = amp4d_model::EvalGraph{};
 }
 
-// Capture enqueue_sync_eval into g.exec; false if the sequence cannot be
-// captured (the call then runs it directly).
+// Capture the evaluation into g.exec, on the pinned parameter and result
+// buffers; false if it cannot be captured (the call then runs
+// enqueue_sync_eval directly).
 bool capture_eval_graph(amp4d_model *model, bool with_grad, bool partials, amp4d_model::EvalGraph &g)
 {
     if (!model->cap_stream &&
@@ -565,8 +566,18 @@ bool capture_eval_graph(amp4d_model *model, bool with_grad, bool partials, amp4d
     }
     cudaStream_t cs = model->cap_stream;
     const std::string saved_err = model->err;
+    // The graph's kernels read the parameters from, and write the result block to,
+    // the model's pinned host buffers directly (their device-side addresses), so it
+    // holds no copy nodes.  Every call writes h_params before the launch and reads
+    // h_out after the synchronisation.
+    double *dp = nullptr, *dout = nullptr;
+    if (cudaHostGetDevicePointer(reinterpret_cast<void **>(&dp), model->h_params, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&dout), model->h_out, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
-    const amp4d_status rc = enqueue_sync_eval(model, with_grad, partials, cs);
+    const amp4d_status rc = enqueue(model, with_grad, dp, dout, cs, partials);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);
     bool ok = rc == AMP4D_OK && e == cudaSuccess && graph != nullptr;
