@@ -462,13 +462,15 @@ amp4d_status enqueue(amp4d_model *model, bool with_grad, const double *d_params,
                                   model->n_param, (double)model->ev.n, lnconst, von, d_params,
                                   model->d_G, model->d_status, d_out, 0, st, (double)model->mc.n, 0,
                                   nullptr, model->d_md, model->purity));
-        // With the gradient and no background the data kernel's last CTA finishes
+        // With the gradient the data kernel's last CTA finishes
         // the evaluation (no separate launch).
         bool fused = false;
         if (with_grad) {
             LaunchArgs la = args_for(model, model->ev, model->ev.part, nullptr, st, grad_grid(model, model->ev));
-            // the all-cached kernel carries the finish; its first n_col CTAs form G u, G v
-            fused = !mix && la.lcache != nullptr && la.grid >= model->n_col;
+            // the all-cached kernel carries the finish (with a background too: alpha was
+            // set before the data pass, and the signal-probability sum is added before
+            // the CTA takes its ticket); its first n_col CTAs form G u, G v
+            fused = la.lcache != nullptr && la.grid >= model->n_col;
             if (fused) {
                 FinishArgs &f = la.fin;
                 f.ad = ad; f.slot_param = model->d_slot_param; f.pscale = model->d_pscale;
