@@ -66,7 +66,7 @@ def test_quadrature_of_a_z_alone_matches_its_rotation_invariant_form():
     # the outer integrand varies fastest where the Z band meets the box edge
     edges = sorted(set(Q._z_band_edges(mo, W.M_LO, m_end)))
     ref, _ = integrate.quad(inner, W.M_LO, m_end, points=edges, epsabs=0, epsrel=1e-12, limit=400)
-    # the judge needs 1e-6 (its target is 1e-4); the rule reaches about 1e-8 here
+    # as the reference for a 1e-4 target the rule needs 1e-6; it reaches about 1e-8 here
     assert Q.normalisation_quadrature(mo, p, 24, 16) / ref == pytest.approx(1.0, abs=1e-7)
 
 
