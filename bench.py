@@ -155,8 +155,8 @@ K_GRAD_SOURCES = ("paper_2007_14931_gb300/csrc/amp4d_eval.cuh",
                   "paper_2007_14931_gb300/csrc/amp4d_device.cuh",
                   "paper_2007_14931_gb300/csrc/amp4d_finish.cuh")
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_grad_fx launch on 4e6
-# events of `large` (544.12 MB + 3.82 MB), per event; valid for these sources only
-K_GRAD_TRAFFIC = {"bytes_per_event": (544.120832e6 + 3.820032e6) / 4e6, "sources_sha16": "38851d7d54f30b4f"}
+# events of `large` (544.12 MB + 3.27 MB), per event; valid for these sources only
+K_GRAD_TRAFFIC = {"bytes_per_event": (544.121856e6 + 3.26912e6) / 4e6, "sources_sha16": "af101cab03cc6bf9"}
 
 
 def kernel_sources_sha16():

@@ -238,6 +238,28 @@ __device__ __forceinline__ float observed_S(const ModelDev &md, const EvState<NK
     return fmaf(md.mwhi, d, fmaf(md.mwlo, d, ev.S));
 }
 
+// w_0 for the real Psi_{0 xi} (p = Psi_{0 xi}.x): the bits of adj_w, whose zero
+// products leave the FMA chain unchanged, in half the FMAs.
+template <bool MT>
+__device__ __forceinline__ float2 adj_w_real(const float2 (&as)[2], const float2 (&asb)[2],
+                                             const float2 (&psi)[2])
+{
+    float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        t.x = fmaf(as[x].x, psi[x].x, t.x);
+        t.y = fmaf(-as[x].y, psi[x].x, t.y);
+    }
+    if constexpr (MT) {
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            t.x = fmaf(asb[x].x, psi[x].x, t.x);
+            t.y = fmaf(-asb[x].y, psi[x].x, t.y);
+        }
+    }
+    return t;
+}
+
 // Adjoint vectors w_l = sum_xi conj(as_xi) Psi_{l xi} of the scaled amplitudes,
 // with the mistag term conj(asb_xi Psi_{l xi}) for the mirrored amplitudes.
 template <bool MT>
@@ -429,13 +451,18 @@ __device__ __forceinline__ void eval_events_fx(const ModelDev &md, const float (
         for (int x = 0; x < 2; ++x) {
             float2 a = make_float2(0.f, 0.f);
             cfma(a, ev[j].Psi[0][x], u[j][0]);
-            cfma(a, ev[j].Psi[1][x], u[j][1]);
+            // Psi_{0 xi} is real: the same bits as the complex form (whose zero term
+            // enters its FMA chain first) in half the FMAs
+            const float p1 = ev[j].Psi[1][x].x;
+            a.x = fmaf(p1, u[j][1].x, a.x);
+            a.y = fmaf(p1, u[j][1].y, a.y);
             cfma(a, ev[j].Psi[2][x], u[j][2]);
             ev[j].a[x] = a;
             if constexpr (MT) {
                 float2 b = make_float2(0.f, 0.f);
                 cfma_conj(b, ev[j].Psi[0][x], u[j][0]);
-                cfma_conj(b, ev[j].Psi[1][x], u[j][1]);
+                b.x = fmaf(p1, u[j][1].x, b.x);
+                b.y = fmaf(p1, u[j][1].y, b.y);
                 cfma_conj(b, ev[j].Psi[2][x], u[j][2]);
                 ev[j].ab[x] = b;
             }
@@ -901,7 +928,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS) k_grad_fx(const float *__restrict
 #pragma unroll
         for (int j = 0; j < NE; ++j)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) wl[j][l] = adj_w<MT>(as[j], asb[j], ev[j].Psi[l]);
+            for (int l = 0; l < 3; ++l)
+                wl[j][l] = l == 1 ? adj_w_real<MT>(as[j], asb[j], ev[j].Psi[l]) : adj_w<MT>(as[j], asb[j], ev[j].Psi[l]);
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             if (k >= nK) continue;
